@@ -1,0 +1,216 @@
+/*
+ * gw.h -- C ABI of the GB300 (sm_103a) GW hot path: imaginary-frequency
+ * polarization, screened interaction, correlation self-energy and its analytic
+ * continuation, after Friedrich, Bluegel and Schindlmayr, "Efficient
+ * implementation of the GW approximation within the all-electron FLAPW method"
+ * (Sec. III.C and III.E).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_dev are device pointers, *_host host pointers. Arrays of
+ *     per-q device pointers (e.g. `const void* const* M_dev`) are HOST arrays whose
+ *     entries are device pointers. The caller owns every buffer; the library keeps
+ *     no pointer after a call returns and never frees caller memory.
+ *   - Complex data is interleaved (re, im): complex128 = two doubles, complex64 = two
+ *     floats. Matrices are row-major and dense (leading dimension = row length).
+ *   - Every compute call only enqueues work on `stream` (no host synchronisation).
+ *     Argument errors are returned at once (GW_EINVAL, message in gw_last_error()).
+ *     Errors found on the device (a non-positive-definite dielectric matrix, a
+ *     non-finite value, an expired bounded wait) are recorded in a library-owned
+ *     device status word and returned by gw_check(), which synchronises the
+ *     stream and clears the word. Outputs are unspecified after an error.
+ *   - Scratch memory comes from the caller: query the size with the matching
+ *     *_workspace() function, pass a device buffer of at least that many bytes
+ *     (256-byte aligned); a smaller buffer gives GW_EWORKSPACE.
+ *   - Symbols are the paper's: q transfer momentum (the paper's k in Eq. polar_MB),
+ *     k summed Bloch vector, t = (k, n occ, n' unocc) a transition with
+ *     Delta_t = e_n'(k+q) - e_n(k) > 0, N_b the size of the Coulomb eigenbasis,
+ *     omega_j > 0 the imaginary-frequency mesh.
+ */
+#ifndef GW_H
+#define GW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gw_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+enum gw_status {
+  GW_OK = 0,
+  GW_EINVAL = 1,        /* bad argument (sizes, pointers, Delta <= 0, e_n' == 0, ...) */
+  GW_EWORKSPACE = 2,    /* workspace missing or too small */
+  GW_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+  GW_ENONFINITE = 4,    /* a non-finite value was produced or read */
+  GW_ENOTHPD = 5,       /* 1 - v^1/2 P v^1/2 not positive definite (P not NSD) */
+  GW_ETIMEOUT = 6,      /* a bounded device-side wait expired */
+  GW_ENOCONV = 7,       /* a fit did not converge (per-curve status holds details) */
+  GW_EUNSUPPORTED = 8   /* combination not built (e.g. precision for this dtype) */
+};
+
+enum gw_dtype { GW_C128 = 0, GW_C64 = 1 };
+
+/* Arithmetic of the P and Sigma contractions. GW_FP64: double precision on the
+ * FP64 pipe (M must be GW_C128). GW_TF32X3 ("FP32-split"): tensor-core products of
+ * a two-term TF32 split of each FP32 operand (hi*hi + hi*lo + lo*hi), FP32
+ * accumulation drained into FP64 partial sums (M must be GW_C64). GW_BF16X3: the
+ * same with a two-term BF16 split. */
+enum gw_precision { GW_FP64 = 0, GW_TF32X3 = 1, GW_BF16X3 = 2 };
+
+enum gw_fit_method { GW_FIT_PLAIN = 0, GW_FIT_MLP = 1 };
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int gw_version(void);
+
+/* Message of the last error returned on the calling host thread ("" if none). */
+const char* gw_last_error(void);
+
+/* Synchronise `stream`, then return and clear the device status word of the
+ * current device (GW_OK if no device-side error was recorded). */
+int gw_check(gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a1. Transition weights (bracket of Eq. polar_MB at w = i omega, Sec. III.C):
+ *   w[j][t] = prefactor * f_t * ( 1/(i omega_j - Delta_t) - 1/(i omega_j + Delta_t) )
+ *           = -prefactor * f_t * 2 Delta_t / (Delta_t^2 + omega_j^2).
+ * prefactor = 2/N_k (spin sum over the BZ density). f_dev may be NULL (f_t = 1).
+ *   delta_dev [K] double, f_dev [K] double or NULL, omega_host [nw] double,
+ *   w_dev [nw][K] double (output).
+ * Errors: GW_EINVAL if K < 0, nw < 1 or nw > GW_MAX_NW, a NULL required pointer,
+ * or omega_j < 0. Delta_t <= 0 is reported by gw_check as GW_EINVAL. */
+#define GW_MAX_NW 64
+int gw_transition_weights(int64_t K, const double* delta_dev, const double* f_dev,
+                          double prefactor, int nw, const double* omega_host,
+                          double* w_dev, gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a2. Polarization in the Coulomb eigenbasis (Eq. polar_MB at w = i omega):
+ *   P_IJ(q, i omega_j) = sum_t w_tj M_{t,I} conj(M_{t,J}),
+ * a weighted Hermitian rank-K_q update per frequency; negative semidefinite.
+ * Batched over nq transfer momenta with their own K_q and N_b(q):
+ *   K_host[nq], nb_host[nq]                   sizes (K_q >= 0, 1 <= N_b <= 8192),
+ *   M_dev[q]      [K_q][N_b] complex (m_dtype) projections M_{t,I},
+ *   delta_dev[q]  [K_q] double                 Delta_t > 0,
+ *   f_dev         NULL, or host array of nq device pointers ([K_q] double, entries
+ *                 may be NULL),
+ *   omega_host    [nw] double, 1 <= nw <= GW_MAX_NW,
+ *   P_dev[q]      [nw][N_b][N_b] complex128 output, both triangles written.
+ * precision: GW_FP64 needs GW_C128; GW_TF32X3 and GW_BF16X3 need GW_C64.
+ * Workspace: gw_polarization_workspace() bytes. */
+size_t gw_polarization_workspace(int nq, const int64_t* K_host, const int* nb_host,
+                                 int nw, int precision);
+int gw_polarization(int nq, const int64_t* K_host, const int* nb_host,
+                    const void* const* M_dev, int m_dtype,
+                    const double* const* delta_dev, const double* const* f_dev,
+                    double prefactor, int nw, const double* omega_host,
+                    double* const* P_dev, int precision,
+                    void* ws_dev, size_t ws_bytes, gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a3. Dielectric matrix and correlation part of the screened interaction in the
+ * Coulomb eigenbasis (Eqs. dielec_MB, screen_MB and W^c = W - v, Sec. III.C):
+ *   eps = 1 - v^1/2 P v^1/2,   W^c = v^1/2 (eps^{-1} - 1) v^1/2,
+ * computed in FP64 from the Cholesky factor of eps (HPD on the imaginary axis).
+ *   v_dev[q]  [N_b] double > 0 Coulomb eigenvalues,
+ *   P_dev[q]  [nw][N_b][N_b] complex128 (Hermitian NSD),
+ *   Wc_dev[q] [nw][N_b][N_b] complex128 output (may alias P_dev[q]).
+ * A failed factorisation is reported by gw_check as GW_ENOTHPD.
+ * Workspace: gw_screened_w_workspace() bytes. */
+size_t gw_screened_w_workspace(int nq, const int* nb_host, int nw);
+int gw_screened_w(int nq, const int* nb_host, int nw, const double* const* v_dev,
+                  const double* const* P_dev, double* const* Wc_dev,
+                  void* ws_dev, size_t ws_bytes, gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a5. Pair coefficients of the self-energy (band-space factor of Eq. SEc_AC):
+ *   c[j][p] = Re( sum_{mu,nu} conj(m_{p,mu}) W^c_{mu nu}(q, i omega_j) m_{p,nu} ),
+ * p = (state n, band n'), m_{p,mu} = <E_mu phi_n | phi_n'>. Real and <= 0.
+ *   npair_host[nq], nb_host[nq]; Msig_dev[q] [npair_q][N_b] complex (m_dtype);
+ *   Wc_dev[q] [nw][N_b][N_b] complex128; c_dev[q] [nw][npair_q] double output.
+ * precision as for gw_polarization. Workspace: gw_sigma_workspace(). */
+int gw_sigma_pair_coeffs(int nq, const int64_t* npair_host, const int* nb_host,
+                         const void* const* Msig_dev, int m_dtype, int nw,
+                         const double* const* Wc_dev, double* const* c_dev,
+                         int precision, void* ws_dev, size_t ws_bytes,
+                         gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a6. Frequency convolution (Eq. SEc_AC and the paragraph after it):
+ *   Sigma^c_s(i w_i) = -1/(2 pi) sum_q w_q sum_{p: state(p) = s}
+ *                      int dw' c_p(w') / (i w_i + i w' - e_p)
+ * with c_p(w') a cubic spline in lambda = w'/(1+w') through the node values
+ * c[j][p] (not-a-knot at the first node, first piece extrapolated to 0, slope at the
+ * last node clamped to the tail's), the tail c_N w_N^2 / w'^2 beyond the last node,
+ * and each spline segment and the tail integrated analytically.
+ *   wq_host[nq] BZ weights; c_dev[q] [nw][npair_q] double;
+ *   pair_state_dev[q] [npair_q] int in [0, nsig); eps_dev[q] [npair_q] double != 0;
+ *   omega_host [nw] (ascending, > 0); omega_out_host [nw_out] (any real values);
+ *   sigma_dev [nsig][nw_out] complex128 output (overwritten).
+ * e_p == 0 is reported by gw_check as GW_EINVAL. */
+int gw_sigma_convolve(int nq, const double* wq_host, const int64_t* npair_host,
+                      int nw, const double* omega_host, const double* const* c_dev,
+                      const int* const* pair_state_dev, const double* const* eps_dev,
+                      int nw_out, const double* omega_out_host, int nsig,
+                      double* sigma_dev, gw_stream_t stream);
+
+/* a5 + a6 in one call (the Sigma^c step of the hot path). */
+size_t gw_sigma_workspace(int nq, const int64_t* npair_host, const int* nb_host, int nw,
+                          int precision);
+int gw_sigma_c(int nq, const double* wq_host, const int64_t* npair_host,
+               const int* nb_host, const void* const* Msig_dev, int m_dtype,
+               const int* const* pair_state_dev, const double* const* eps_dev,
+               int nw, const double* omega_host, const double* const* Wc_dev,
+               int nw_out, const double* omega_out_host, int nsig, double* sigma_dev,
+               int precision, void* ws_dev, size_t ws_bytes, gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a7. Analytic continuation (Eq. modelf): fit f(z) = sum_p a_p / (z - w_p) to each
+ * curve Sigma(i omega_j) by FP64 Levenberg-Marquardt (Marquardt's diagonal
+ * scaling; cost 1/2 sum_j |f(i omega_j) - Sigma_j|^2).
+ *   sigma_dev [ncurve][nw] complex128; sign_dev [ncurve] double (sign of the state
+ *   energy, picks the default start w_p = s (0.5, 2, 5, 10, 20)_p - 0.1 i s) or NULL
+ *   (+1); npole in [1, 5].
+ *   method GW_FIT_PLAIN: default start, residues by linear least squares.
+ *   method GW_FIT_MLP: start proposed by the network (npole = 2, nw = 24,
+ *     mlp_dev = packed FP32 weights, see gw_mlp_param_count); the fit from the
+ *     default start is also run and the lower-cost result is kept.
+ *   params_dev [ncurve][npole][4] double output (Re a, Im a, Re w, Im w);
+ *   cost_dev [ncurve], iters_dev [ncurve], status_dev [ncurve] outputs
+ *   (status 0 converged, 1 iteration limit, 2 damping overflow). */
+int gw_continue(int ncurve, int nw, const double* omega_host, const double* sigma_dev,
+                const double* sign_dev, int npole, int method, const float* mlp_dev,
+                double* params_dev, double* cost_dev, int* iters_dev, int* status_dev,
+                gw_stream_t stream);
+
+/* Learned initialiser: MLP 48 -> 128 -> 128 -> 8 (SiLU), input the curve on 24 nodes
+ * scaled by s = max |Sigma_j|, output (Re a/s, Im a/s, Re w, Im w) for 2 poles.
+ * Packed FP32 parameter layout: W1[128][48], b1[128], W2[128][128], b2[128],
+ * W3[8][128], b3[8]. */
+int gw_mlp_param_count(void);
+/* Forward pass in BF16 tensor-free arithmetic for inference: out_dev [n][8] float. */
+int gw_mlp_forward(int n, const double* sigma_dev, const float* mlp_dev, float* out_dev,
+                   gw_stream_t stream);
+/* One FP32 training step on a batch: loss = mean_b (1/24) sum_j |f(i w_j) - y_j|^2/s^2.
+ * Writes the batch loss to loss_dev[0] and the gradient into grad_dev (packed
+ * layout); then, if lr > 0, applies one Adam step (beta1 0.9, beta2 0.999, eps 1e-8,
+ * step number `step` >= 1) to mlp_dev with moments m_dev, v_dev (packed layout). */
+int gw_mlp_train_step(int n, const double* omega_host, const double* sigma_dev,
+                      float* mlp_dev, float* grad_dev, float* m_dev, float* v_dev,
+                      float lr, int step, float* loss_dev, gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Synthetic-input generator (not part of the method): fills projections with
+ * complex normals (Philox4x32-10 keyed by seed, counter (element index, q, tid),
+ * Box-Muller) scaled by 1/(1 + I/16), exactly as the host-side input module does,
+ * so large inputs can be created on the device. out_dev [rows][nb] of m_dtype,
+ * element (r, I) uses index (row0 + r) * nb + I. */
+int gw_synth_projections(uint64_t seed, uint32_t tid, uint32_t q, int64_t row0,
+                         int64_t rows, int nb, int m_dtype, void* out_dev,
+                         gw_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GW_H */

@@ -1,0 +1,294 @@
+"""Python binding of libgw (the GB300 GW hot path).
+
+Argument marshalling only: every step runs in the CUDA kernels of libgw.so, which
+is built in-tree by ``paper_1003_0316_gb300._build``. Tensors are torch CUDA
+tensors (complex128 / complex64 / float64 / int32) on the current device; the
+calls enqueue on torch's current stream. There is no CPU fallback: importing this
+package without the compiled library raises ImportError.
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libgw.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is not built; run `python -m paper_1003_0316_gb300._build`")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+GW_OK, GW_EINVAL, GW_EWORKSPACE, GW_ECUDA, GW_ENONFINITE, GW_ENOTHPD, GW_ETIMEOUT, \
+    GW_ENOCONV, GW_EUNSUPPORTED = range(9)
+GW_C128, GW_C64 = 0, 1
+GW_FP64, GW_TF32X3, GW_BF16X3 = 0, 1, 2
+GW_FIT_PLAIN, GW_FIT_MLP = 0, 1
+PRECISIONS = {"fp64": GW_FP64, "tf32x3": GW_TF32X3, "bf16x3": GW_BF16X3}
+MAX_NW = 64
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_f64 = ctypes.c_double
+_f32 = ctypes.c_float
+_sz = ctypes.c_size_t
+_P = ctypes.POINTER
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_sig("gw_version", _i32)
+_sig("gw_last_error", ctypes.c_char_p)
+_sig("gw_check", _i32, _vp)
+_sig("gw_transition_weights", _i32, _i64, _vp, _vp, _f64, _i32, _P(_f64), _vp, _vp)
+_sig("gw_polarization_workspace", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32)
+_sig("gw_polarization", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp), _f64,
+     _i32, _P(_f64), _P(_vp), _i32, _vp, _sz, _vp)
+_sig("gw_screened_w_workspace", _sz, _i32, _P(_i32), _i32)
+_sig("gw_screened_w", _i32, _i32, _P(_i32), _i32, _P(_vp), _P(_vp), _P(_vp), _vp, _sz, _vp)
+_sig("gw_sigma_pair_coeffs", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _i32, _P(_vp),
+     _P(_vp), _i32, _vp, _sz, _vp)
+_sig("gw_sigma_convolve", _i32, _i32, _P(_f64), _P(_i64), _i32, _P(_f64), _P(_vp), _P(_vp),
+     _P(_vp), _i32, _P(_f64), _i32, _vp, _vp)
+_sig("gw_sigma_workspace", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32)
+_sig("gw_sigma_c", _i32, _i32, _P(_f64), _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp),
+     _i32, _P(_f64), _P(_vp), _i32, _P(_f64), _i32, _vp, _i32, _vp, _sz, _vp)
+_sig("gw_continue", _i32, _i32, _i32, _P(_f64), _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp,
+     _vp)
+_sig("gw_mlp_param_count", _i32)
+_sig("gw_mlp_forward", _i32, _i32, _vp, _vp, _vp, _vp)
+_sig("gw_mlp_train_step", _i32, _i32, _P(_f64), _vp, _vp, _vp, _vp, _vp, _f32, _i32, _vp, _vp)
+_sig("gw_synth_projections", _i32, _u64, _u32, _u32, _i64, _i64, _i32, _i32, _vp, _vp)
+
+
+class GWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libgw error {code}: {msg}")
+        self.code = code
+
+
+def _raise(rc):
+    if rc != GW_OK:
+        raise GWError(rc, _lib.gw_last_error().decode())
+
+
+def lib_path():
+    return _LIB_PATH
+
+
+def version():
+    return _lib.gw_version()
+
+
+def _stream():
+    return _vp(torch.cuda.current_stream().cuda_stream)
+
+
+def _arr(ctype, vals):
+    vals = list(vals)
+    return (ctype * len(vals))(*vals)
+
+
+def _ptrs(ts):
+    return (_vp * len(ts))(*[(t.data_ptr() if t is not None else None) for t in ts])
+
+
+def _om(omega):
+    om = [float(x) for x in (omega.tolist() if hasattr(omega, "tolist") else omega)]
+    return _arr(_f64, om), len(om)
+
+
+def _ws(nbytes, device):
+    if nbytes == 0:
+        return None, _vp(None), 0
+    buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+    return buf, _vp(buf.data_ptr()), int(nbytes)
+
+
+def check(stream=None):
+    """Synchronise the stream and raise if a device-side error was recorded."""
+    _raise(_lib.gw_check(stream if stream is not None else _stream()))
+
+
+def _dtype_code(t):
+    if t.dtype == torch.complex128:
+        return GW_C128
+    if t.dtype == torch.complex64:
+        return GW_C64
+    raise TypeError(f"projections must be complex128 or complex64, got {t.dtype}")
+
+
+# ---------------------------------------------------------------- a1 --------
+def transition_weights(delta, omega, prefactor, f=None):
+    """w[j, t] = -prefactor f_t 2 Delta_t / (Delta_t^2 + omega_j^2) (float64 [nw][K])."""
+    om, nw = _om(omega)
+    K = delta.numel()
+    w = torch.empty((nw, K), dtype=torch.float64, device=delta.device)
+    _raise(_lib.gw_transition_weights(K, delta.data_ptr(), f.data_ptr() if f is not None else None,
+                                      float(prefactor), nw, om, w.data_ptr(), _stream()))
+    return w
+
+
+# ---------------------------------------------------------------- a2 --------
+def polarization_workspace(Ks, nbs, nw, precision):
+    return _lib.gw_polarization_workspace(len(Ks), _arr(_i64, Ks), _arr(_i32, nbs), nw,
+                                          PRECISIONS.get(precision, precision))
+
+
+def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=None, ws=None):
+    """P[q] = sum_t w_tj M_tI conj(M_tJ) for each q (complex128 [nw][N_b][N_b])."""
+    prec = PRECISIONS.get(precision, precision)
+    om, nw = _om(omega)
+    nq = len(Ms)
+    Ks = [m.shape[0] for m in Ms]
+    nbs = [m.shape[1] for m in Ms]
+    dev = Ms[0].device
+    if out is None:
+        out = [torch.empty((nw, nb, nb), dtype=torch.complex128, device=dev) for nb in nbs]
+    need = polarization_workspace(Ks, nbs, nw, prec)
+    if ws is None:
+        wsb, wsp, wsn = _ws(need, dev)
+    else:
+        wsb, wsp, wsn = ws, _vp(ws.data_ptr()), ws.numel()
+    fptr = _ptrs(fs) if fs is not None else None
+    _raise(_lib.gw_polarization(nq, _arr(_i64, Ks), _arr(_i32, nbs), _ptrs(Ms), _dtype_code(Ms[0]),
+                                _ptrs(deltas), fptr, float(prefactor), nw, om, _ptrs(out), prec,
+                                wsp, wsn, _stream()))
+    return out
+
+
+# ---------------------------------------------------------------- a3 --------
+def screened_w_workspace(nbs, nw):
+    return _lib.gw_screened_w_workspace(len(nbs), _arr(_i32, nbs), nw)
+
+
+def screened_w(Ps, vs, out=None, ws=None):
+    """W^c[q] = v^1/2 (eps^-1 - 1) v^1/2, eps = 1 - v^1/2 P v^1/2 (complex128)."""
+    nq = len(Ps)
+    nw = Ps[0].shape[0]
+    nbs = [p.shape[1] for p in Ps]
+    dev = Ps[0].device
+    if out is None:
+        out = [torch.empty_like(p) for p in Ps]
+    need = screened_w_workspace(nbs, nw)
+    if ws is None:
+        wsb, wsp, wsn = _ws(need, dev)
+    else:
+        wsb, wsp, wsn = ws, _vp(ws.data_ptr()), ws.numel()
+    _raise(_lib.gw_screened_w(nq, _arr(_i32, nbs), nw, _ptrs(vs), _ptrs(Ps), _ptrs(out), wsp, wsn,
+                              _stream()))
+    return out
+
+
+# ---------------------------------------------------------------- a5/a6 -----
+def sigma_workspace(npairs, nbs, nw, precision):
+    return _lib.gw_sigma_workspace(len(npairs), _arr(_i64, npairs), _arr(_i32, nbs), nw,
+                                   PRECISIONS.get(precision, precision))
+
+
+def sigma_pair_coeffs(Msigs, Wcs, precision="fp64", out=None):
+    prec = PRECISIONS.get(precision, precision)
+    nq = len(Msigs)
+    nw = Wcs[0].shape[0]
+    npairs = [m.shape[0] for m in Msigs]
+    nbs = [m.shape[1] for m in Msigs]
+    dev = Msigs[0].device
+    if out is None:
+        out = [torch.empty((nw, n), dtype=torch.float64, device=dev) for n in npairs]
+    need = sigma_workspace(npairs, nbs, nw, prec)
+    wsb, wsp, wsn = _ws(need, dev)
+    _raise(_lib.gw_sigma_pair_coeffs(nq, _arr(_i64, npairs), _arr(_i32, nbs), _ptrs(Msigs),
+                                     _dtype_code(Msigs[0]), nw, _ptrs(Wcs), _ptrs(out), prec, wsp,
+                                     wsn, _stream()))
+    return out
+
+
+def sigma_convolve(wq, cs, pair_states, epss, omega, omega_out, nsig, out=None):
+    om, nw = _om(omega)
+    omo, nwo = _om(omega_out)
+    nq = len(cs)
+    npairs = [c.shape[1] for c in cs]
+    dev = cs[0].device
+    if out is None:
+        out = torch.empty((nsig, nwo), dtype=torch.complex128, device=dev)
+    _raise(_lib.gw_sigma_convolve(nq, _arr(_f64, wq), _arr(_i64, npairs), nw, om, _ptrs(cs),
+                                  _ptrs(pair_states), _ptrs(epss), nwo, omo, nsig, out.data_ptr(),
+                                  _stream()))
+    return out
+
+
+def sigma_c(wq, Msigs, pair_states, epss, Wcs, omega, omega_out, nsig, precision="fp64",
+            out=None, ws=None):
+    prec = PRECISIONS.get(precision, precision)
+    om, nw = _om(omega)
+    omo, nwo = _om(omega_out)
+    nq = len(Msigs)
+    npairs = [m.shape[0] for m in Msigs]
+    nbs = [m.shape[1] for m in Msigs]
+    dev = Msigs[0].device
+    if out is None:
+        out = torch.empty((nsig, nwo), dtype=torch.complex128, device=dev)
+    need = sigma_workspace(npairs, nbs, nw, prec)
+    if ws is None:
+        wsb, wsp, wsn = _ws(need, dev)
+    else:
+        wsb, wsp, wsn = ws, _vp(ws.data_ptr()), ws.numel()
+    _raise(_lib.gw_sigma_c(nq, _arr(_f64, wq), _arr(_i64, npairs), _arr(_i32, nbs), _ptrs(Msigs),
+                           _dtype_code(Msigs[0]), _ptrs(pair_states), _ptrs(epss), nw, om,
+                           _ptrs(Wcs), nwo, omo, nsig, out.data_ptr(), prec, wsp, wsn, _stream()))
+    return out
+
+
+# ---------------------------------------------------------------- a7 --------
+def continue_fit(sigma, omega, npole=2, sign=None, method="plain", mlp=None):
+    """Multipole fit per curve; returns (params [n][npole][4], cost, iters, status)."""
+    om, nw = _om(omega)
+    n = sigma.shape[0]
+    dev = sigma.device
+    params = torch.empty((n, npole, 4), dtype=torch.float64, device=dev)
+    cost = torch.empty(n, dtype=torch.float64, device=dev)
+    iters = torch.empty(n, dtype=torch.int32, device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    m = GW_FIT_PLAIN if method == "plain" else GW_FIT_MLP
+    _raise(_lib.gw_continue(n, nw, om, sigma.data_ptr(), sign.data_ptr() if sign is not None else None,
+                            npole, m, mlp.data_ptr() if mlp is not None else None,
+                            params.data_ptr(), cost.data_ptr(), iters.data_ptr(), status.data_ptr(),
+                            _stream()))
+    return params, cost, iters, status
+
+
+def mlp_param_count():
+    return _lib.gw_mlp_param_count()
+
+
+def mlp_forward(sigma, mlp, out=None):
+    n = sigma.shape[0]
+    if out is None:
+        out = torch.empty((n, 8), dtype=torch.float32, device=sigma.device)
+    _raise(_lib.gw_mlp_forward(n, sigma.data_ptr(), mlp.data_ptr(), out.data_ptr(), _stream()))
+    return out
+
+
+def mlp_train_step(sigma, omega, mlp, grad, m, v, lr, step, loss):
+    om, nw = _om(omega)
+    _raise(_lib.gw_mlp_train_step(sigma.shape[0], om, sigma.data_ptr(), mlp.data_ptr(),
+                                  grad.data_ptr(), m.data_ptr() if m is not None else None,
+                                  v.data_ptr() if v is not None else None, float(lr), int(step),
+                                  loss.data_ptr(), _stream()))
+
+
+# ------------------------------------------------------------ inputs --------
+def synth_projections(seed, tid, q, row0, rows, nb, dtype=torch.complex64, device="cuda", out=None):
+    """Device-side twin of the host input generator (Philox4x32-10 + Box-Muller)."""
+    if out is None:
+        out = torch.empty((rows, nb), dtype=dtype, device=device)
+    code = GW_C128 if dtype == torch.complex128 else GW_C64
+    _raise(_lib.gw_synth_projections(int(seed), int(tid), int(q), int(row0), int(rows), int(nb),
+                                     code, out.data_ptr(), _stream()))
+    return out

@@ -1,0 +1,368 @@
+// C ABI entry points of libgw: argument validation, the error model, workspace
+// sizing and dispatch to the kernels of the other translation units.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gw_internal.cuh"
+
+namespace gw {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+  return set_error(GW_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// One status word per device; its address is looked up once per device.
+static __device__ unsigned g_status_word;
+static std::mutex g_ctx_mu;
+static DeviceCtx g_ctx[64];
+static bool g_ctx_ok[64];
+
+int device_ctx(DeviceCtx* out) {
+  int dev = 0;
+  GW_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(GW_EINVAL, "device id %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  if (!g_ctx_ok[dev]) {
+    DeviceCtx c{};
+    c.device = dev;
+    void* p = nullptr;
+    GW_CUDA_TRY(cudaGetSymbolAddress(&p, g_status_word));
+    c.status = static_cast<unsigned*>(p);
+    GW_CUDA_TRY(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
+    g_ctx[dev] = c;
+    g_ctx_ok[dev] = true;
+  }
+  *out = g_ctx[dev];
+  return GW_OK;
+}
+
+static int fill_omega(int nw, const double* omega, OmegaArr* o, bool require_positive,
+                      bool require_ascending) {
+  if (nw < 1 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [1, %d]", nw, GW_MAX_NW);
+  if (omega == nullptr) return set_error(GW_EINVAL, "omega_host is NULL");
+  memset(o, 0, sizeof(*o));
+  for (int j = 0; j < nw; ++j) {
+    double w = omega[j];
+    if (!std::isfinite(w)) return set_error(GW_EINVAL, "omega[%d] not finite", j);
+    if (require_positive ? !(w > 0.0) : !(w >= 0.0))
+      return set_error(GW_EINVAL, "omega[%d]=%g must be %s", j, w,
+                       require_positive ? "> 0" : ">= 0");
+    if (require_ascending && j > 0 && !(w > omega[j - 1]))
+      return set_error(GW_EINVAL, "omega must be strictly ascending (index %d)", j);
+    o->v[j] = w;
+  }
+  return GW_OK;
+}
+
+static int check_ws(void* ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return GW_OK;
+  if (ws == nullptr || ws_bytes < need)
+    return set_error(GW_EWORKSPACE, "workspace of %zu bytes given, %zu needed", ws_bytes, need);
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+    return set_error(GW_EWORKSPACE, "workspace not 256-byte aligned");
+  return GW_OK;
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+extern "C" {
+
+int gw_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char* gw_last_error(void) { return g_last_error.c_str(); }
+
+int gw_check(gw_stream_t stream) {
+  DeviceCtx ctx;
+  int rc = device_ctx(&ctx);
+  if (rc) return rc;
+  GW_CUDA_TRY(cudaStreamSynchronize(stream));
+  unsigned word = 0;
+  GW_CUDA_TRY(cudaMemcpy(&word, ctx.status, sizeof(word), cudaMemcpyDeviceToHost));
+  unsigned zero = 0;
+  GW_CUDA_TRY(cudaMemcpy(ctx.status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+  if (word & ST_ETIMEOUT) return set_error(GW_ETIMEOUT, "a bounded device wait expired");
+  if (word & ST_ENOTHPD)
+    return set_error(GW_ENOTHPD, "dielectric matrix not positive definite (P not NSD)");
+  if (word & ST_ENONFINITE) return set_error(GW_ENONFINITE, "non-finite value on the device");
+  if (word & ST_EINVAL)
+    return set_error(GW_EINVAL, "invalid input data found on the device (Delta <= 0 or e == 0)");
+  return GW_OK;
+}
+
+int gw_transition_weights(int64_t K, const double* delta_dev, const double* f_dev,
+                          double prefactor, int nw, const double* omega_host, double* w_dev,
+                          gw_stream_t stream) {
+  if (K < 0) return set_error(GW_EINVAL, "K=%lld < 0", (long long)K);
+  OmegaArr om;
+  int rc = fill_omega(nw, omega_host, &om, false, false);
+  if (rc) return rc;
+  if (K == 0) return GW_OK;
+  if (delta_dev == nullptr || w_dev == nullptr)
+    return set_error(GW_EINVAL, "NULL delta_dev or w_dev");
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return launch_weights(K, delta_dev, f_dev, prefactor, nw, om, w_dev, stream, ctx);
+}
+
+static int validate_pol(int nq, const int64_t* K, const int* nb, int precision) {
+  if (nq < 1) return set_error(GW_EINVAL, "nq=%d < 1", nq);
+  if (K == nullptr || nb == nullptr) return set_error(GW_EINVAL, "NULL K_host or nb_host");
+  for (int q = 0; q < nq; ++q) {
+    if (K[q] < 0) return set_error(GW_EINVAL, "K[%d] < 0", q);
+    if (nb[q] < 1 || nb[q] > 8192) return set_error(GW_EINVAL, "nb[%d]=%d outside [1, 8192]", q, nb[q]);
+  }
+  if (precision != GW_FP64 && precision != GW_TF32X3 && precision != GW_BF16X3)
+    return set_error(GW_EINVAL, "unknown precision %d", precision);
+  return GW_OK;
+}
+
+size_t gw_polarization_workspace(int nq, const int64_t* K_host, const int* nb_host, int nw,
+                                 int precision) {
+  if (validate_pol(nq, K_host, nb_host, precision) || nw < 1 || nw > GW_MAX_NW) return 0;
+  if (precision == GW_FP64) return pol_fp64_workspace(nq, K_host, nb_host, nw);
+  return pol_tc_workspace(nq, K_host, nb_host, nw, precision);
+}
+
+int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const void* const* M_dev,
+                    int m_dtype, const double* const* delta_dev, const double* const* f_dev,
+                    double prefactor, int nw, const double* omega_host, double* const* P_dev,
+                    int precision, void* ws_dev, size_t ws_bytes, gw_stream_t stream) {
+  int rc = validate_pol(nq, K_host, nb_host, precision);
+  if (rc) return rc;
+  OmegaArr om;
+  if ((rc = fill_omega(nw, omega_host, &om, false, false))) return rc;
+  if (M_dev == nullptr || delta_dev == nullptr || P_dev == nullptr)
+    return set_error(GW_EINVAL, "NULL M_dev, delta_dev or P_dev array");
+  if (precision == GW_FP64 && m_dtype != GW_C128)
+    return set_error(GW_EUNSUPPORTED, "GW_FP64 needs complex128 projections");
+  if (precision != GW_FP64 && m_dtype != GW_C64)
+    return set_error(GW_EUNSUPPORTED, "tensor-core precisions need complex64 projections");
+  if (!std::isfinite(prefactor)) return set_error(GW_EINVAL, "prefactor not finite");
+  std::vector<PolQ> qs(nq);
+  for (int q = 0; q < nq; ++q) {
+    qs[q].M = M_dev[q];
+    qs[q].delta = delta_dev[q];
+    qs[q].f = f_dev ? f_dev[q] : nullptr;
+    qs[q].P = P_dev[q];
+    qs[q].K = K_host[q];
+    qs[q].nb = nb_host[q];
+    if (qs[q].P == nullptr) return set_error(GW_EINVAL, "P_dev[%d] is NULL", q);
+    if (qs[q].K > 0 && (qs[q].M == nullptr || qs[q].delta == nullptr))
+      return set_error(GW_EINVAL, "M_dev[%d] or delta_dev[%d] is NULL", q, q);
+    if (precision != GW_FP64 && (reinterpret_cast<uintptr_t>(qs[q].M) & 15u))
+      return set_error(GW_EINVAL, "M_dev[%d] not 16-byte aligned", q);
+  }
+  size_t need = gw_polarization_workspace(nq, K_host, nb_host, nw, precision);
+  if ((rc = check_ws(ws_dev, ws_bytes, need))) return rc;
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  if (precision == GW_FP64)
+    return pol_fp64(nq, qs.data(), prefactor, nw, om, ws_dev, ws_bytes, stream, ctx);
+  return pol_tc(nq, qs.data(), prefactor, nw, om, precision, ws_dev, ws_bytes, stream, ctx);
+}
+
+size_t gw_screened_w_workspace(int nq, const int* nb_host, int nw) {
+  if (nq < 1 || nb_host == nullptr || nw < 1 || nw > GW_MAX_NW) return 0;
+  for (int q = 0; q < nq; ++q)
+    if (nb_host[q] < 1 || nb_host[q] > 8192) return 0;
+  return dielectric_workspace(nq, nb_host, nw);
+}
+
+int gw_screened_w(int nq, const int* nb_host, int nw, const double* const* v_dev,
+                  const double* const* P_dev, double* const* Wc_dev, void* ws_dev,
+                  size_t ws_bytes, gw_stream_t stream) {
+  if (nq < 1 || nb_host == nullptr) return set_error(GW_EINVAL, "nq < 1 or NULL nb_host");
+  if (nw < 1 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [1, %d]", nw, GW_MAX_NW);
+  if (v_dev == nullptr || P_dev == nullptr || Wc_dev == nullptr)
+    return set_error(GW_EINVAL, "NULL v_dev, P_dev or Wc_dev array");
+  for (int q = 0; q < nq; ++q) {
+    if (nb_host[q] < 1 || nb_host[q] > 8192) return set_error(GW_EINVAL, "nb[%d]=%d", q, nb_host[q]);
+    if (!v_dev[q] || !P_dev[q] || !Wc_dev[q]) return set_error(GW_EINVAL, "NULL pointer for q=%d", q);
+  }
+  size_t need = dielectric_workspace(nq, nb_host, nw);
+  int rc = check_ws(ws_dev, ws_bytes, need);
+  if (rc) return rc;
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return dielectric_wc(nq, nb_host, nw, v_dev, P_dev, Wc_dev, ws_dev, ws_bytes, stream, ctx);
+}
+
+static int validate_pairs(int nq, const int64_t* npair, const int* nb, int precision, int m_dtype) {
+  if (nq < 1 || npair == nullptr || nb == nullptr)
+    return set_error(GW_EINVAL, "nq < 1 or NULL npair_host/nb_host");
+  for (int q = 0; q < nq; ++q) {
+    if (npair[q] < 0) return set_error(GW_EINVAL, "npair[%d] < 0", q);
+    if (nb[q] < 1 || nb[q] > 8192) return set_error(GW_EINVAL, "nb[%d]=%d", q, nb[q]);
+  }
+  if (precision != GW_FP64 && precision != GW_TF32X3 && precision != GW_BF16X3)
+    return set_error(GW_EINVAL, "unknown precision %d", precision);
+  if (precision == GW_FP64 && m_dtype != GW_C128)
+    return set_error(GW_EUNSUPPORTED, "GW_FP64 needs complex128 projections");
+  if (precision != GW_FP64 && m_dtype != GW_C64)
+    return set_error(GW_EUNSUPPORTED, "tensor-core precisions need complex64 projections");
+  return GW_OK;
+}
+
+int gw_sigma_pair_coeffs(int nq, const int64_t* npair_host, const int* nb_host,
+                         const void* const* Msig_dev, int m_dtype, int nw,
+                         const double* const* Wc_dev, double* const* c_dev, int precision,
+                         void* ws_dev, size_t ws_bytes, gw_stream_t stream) {
+  int rc = validate_pairs(nq, npair_host, nb_host, precision, m_dtype);
+  if (rc) return rc;
+  if (nw < 1 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [1, %d]", nw, GW_MAX_NW);
+  if (!Msig_dev || !Wc_dev || !c_dev) return set_error(GW_EINVAL, "NULL pointer array");
+  for (int q = 0; q < nq; ++q)
+    if (npair_host[q] > 0 && (!Msig_dev[q] || !Wc_dev[q] || !c_dev[q]))
+      return set_error(GW_EINVAL, "NULL pointer for q=%d", q);
+  size_t need = paircoef_workspace(nq, npair_host, nb_host, nw, precision);
+  if ((rc = check_ws(ws_dev, ws_bytes, need))) return rc;
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return paircoef(nq, npair_host, nb_host, Msig_dev, m_dtype, nw, Wc_dev, c_dev, precision,
+                  ws_dev, ws_bytes, stream, ctx);
+}
+
+int gw_sigma_convolve(int nq, const double* wq_host, const int64_t* npair_host, int nw,
+                      const double* omega_host, const double* const* c_dev,
+                      const int* const* pair_state_dev, const double* const* eps_dev,
+                      int nw_out, const double* omega_out_host, int nsig, double* sigma_dev,
+                      gw_stream_t stream) {
+  if (nq < 1 || !wq_host || !npair_host) return set_error(GW_EINVAL, "nq < 1 or NULL host array");
+  if (nw < 4) return set_error(GW_EINVAL, "the convolution needs nw >= 4 nodes (nw=%d)", nw);
+  OmegaArr om, om_out;
+  int rc = fill_omega(nw, omega_host, &om, true, true);
+  if (rc) return rc;
+  if (nw_out < 1 || nw_out > GW_MAX_NW || !omega_out_host)
+    return set_error(GW_EINVAL, "nw_out=%d outside [1, %d] or NULL omega_out", nw_out, GW_MAX_NW);
+  memset(&om_out, 0, sizeof(om_out));
+  for (int i = 0; i < nw_out; ++i) {
+    if (!std::isfinite(omega_out_host[i])) return set_error(GW_EINVAL, "omega_out[%d] not finite", i);
+    om_out.v[i] = omega_out_host[i];
+  }
+  if (nsig < 1 || !sigma_dev) return set_error(GW_EINVAL, "nsig < 1 or NULL sigma_dev");
+  if (!c_dev || !pair_state_dev || !eps_dev) return set_error(GW_EINVAL, "NULL pointer array");
+  for (int q = 0; q < nq; ++q) {
+    if (npair_host[q] < 0) return set_error(GW_EINVAL, "npair[%d] < 0", q);
+    if (!std::isfinite(wq_host[q])) return set_error(GW_EINVAL, "wq[%d] not finite", q);
+    if (npair_host[q] > 0 && (!c_dev[q] || !pair_state_dev[q] || !eps_dev[q]))
+      return set_error(GW_EINVAL, "NULL pointer for q=%d", q);
+  }
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return convolve(nq, wq_host, npair_host, nw, om, c_dev, pair_state_dev, eps_dev, nw_out, om_out,
+                  nsig, sigma_dev, nullptr, 0, stream, ctx);
+}
+
+size_t gw_sigma_workspace(int nq, const int64_t* npair_host, const int* nb_host, int nw,
+                          int precision) {
+  if (nq < 1 || !npair_host || !nb_host || nw < 1 || nw > GW_MAX_NW) return 0;
+  size_t b = 0;
+  for (int q = 0; q < nq; ++q) {
+    if (npair_host[q] < 0) return 0;
+    b += ws_round(sizeof(double) * size_t(nw) * size_t(npair_host[q]));
+  }
+  return b + paircoef_workspace(nq, npair_host, nb_host, nw, precision);
+}
+
+int gw_sigma_c(int nq, const double* wq_host, const int64_t* npair_host, const int* nb_host,
+               const void* const* Msig_dev, int m_dtype, const int* const* pair_state_dev,
+               const double* const* eps_dev, int nw, const double* omega_host,
+               const double* const* Wc_dev, int nw_out, const double* omega_out_host, int nsig,
+               double* sigma_dev, int precision, void* ws_dev, size_t ws_bytes,
+               gw_stream_t stream) {
+  int rc = validate_pairs(nq, npair_host, nb_host, precision, m_dtype);
+  if (rc) return rc;
+  size_t need = gw_sigma_workspace(nq, npair_host, nb_host, nw, precision);
+  if ((rc = check_ws(ws_dev, ws_bytes, need))) return rc;
+  if (nw < 4 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [4, %d]", nw, GW_MAX_NW);
+  WsCursor cur{static_cast<char*>(ws_dev), ws_bytes, 0};
+  std::vector<double*> cbuf(nq);
+  for (int q = 0; q < nq; ++q)
+    cbuf[q] = static_cast<double*>(cur.take(sizeof(double) * size_t(nw) * size_t(npair_host[q])));
+  size_t off = (cur.used + 255) & ~size_t(255);
+  rc = gw_sigma_pair_coeffs(nq, npair_host, nb_host, Msig_dev, m_dtype, nw, Wc_dev, cbuf.data(),
+                            precision, static_cast<char*>(ws_dev) + off, ws_bytes - off, stream);
+  if (rc) return rc;
+  std::vector<const double*> cc(cbuf.begin(), cbuf.end());
+  return gw_sigma_convolve(nq, wq_host, npair_host, nw, omega_host, cc.data(), pair_state_dev,
+                           eps_dev, nw_out, omega_out_host, nsig, sigma_dev, stream);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int gw_continue(int ncurve, int nw, const double* omega_host, const double* sigma_dev,
+                const double* sign_dev, int npole, int method, const float* mlp_dev,
+                double* params_dev, double* cost_dev, int* iters_dev, int* status_dev,
+                gw_stream_t stream) {
+  if (ncurve < 0) return set_error(GW_EINVAL, "ncurve < 0");
+  OmegaArr om;
+  int rc = fill_omega(nw, omega_host, &om, true, false);
+  if (rc) return rc;
+  if (npole < 1 || npole > 5) return set_error(GW_EINVAL, "npole=%d outside [1, 5]", npole);
+  if (2 * nw < 4 * npole) return set_error(GW_EINVAL, "fewer data (2 nw) than parameters (4 npole)");
+  if (ncurve == 0) return GW_OK;
+  if (!sigma_dev || !params_dev || !cost_dev || !iters_dev || !status_dev)
+    return set_error(GW_EINVAL, "NULL sigma/params/cost/iters/status pointer");
+  if (method == GW_FIT_PLAIN)
+    return launch_lm(ncurve, nw, om, sigma_dev, sign_dev, npole, nullptr, params_dev, cost_dev,
+                     iters_dev, status_dev, 0, stream);
+  if (method != GW_FIT_MLP) return set_error(GW_EINVAL, "unknown fit method %d", method);
+  return set_error(GW_EUNSUPPORTED, "learned start not built");
+}
+
+int gw_mlp_param_count(void) { return MLP_NPARAM; }
+
+int gw_mlp_forward(int n, const double* sigma_dev, const float* mlp_dev, float* out_dev,
+                   gw_stream_t stream) {
+  if (n < 0 || (n > 0 && (!sigma_dev || !mlp_dev || !out_dev)))
+    return set_error(GW_EINVAL, "bad MLP forward arguments");
+  if (n == 0) return GW_OK;
+  return mlp_forward(n, sigma_dev, mlp_dev, out_dev, stream);
+}
+
+int gw_mlp_train_step(int n, const double* omega_host, const double* sigma_dev, float* mlp_dev,
+                      float* grad_dev, float* m_dev, float* v_dev, float lr, int step,
+                      float* loss_dev, gw_stream_t stream) {
+  OmegaArr om;
+  int rc = fill_omega(24, omega_host, &om, true, false);
+  if (rc) return rc;
+  if (n < 1 || !sigma_dev || !mlp_dev || !grad_dev || !loss_dev)
+    return set_error(GW_EINVAL, "bad MLP training arguments");
+  if (lr > 0.0f && (!m_dev || !v_dev || step < 1))
+    return set_error(GW_EINVAL, "Adam step needs moments and step >= 1");
+  return mlp_train_step(n, om, sigma_dev, mlp_dev, grad_dev, m_dev, v_dev, lr, step, loss_dev, stream);
+}
+
+int gw_synth_projections(uint64_t seed, uint32_t tid, uint32_t q, int64_t row0, int64_t rows,
+                         int nb, int m_dtype, void* out_dev, gw_stream_t stream) {
+  if (row0 < 0 || rows < 0 || nb < 1) return set_error(GW_EINVAL, "bad synth sizes");
+  if (m_dtype != GW_C128 && m_dtype != GW_C64) return set_error(GW_EINVAL, "bad dtype");
+  if (rows > 0 && !out_dev) return set_error(GW_EINVAL, "NULL out_dev");
+  DeviceCtx ctx;
+  int rc = device_ctx(&ctx);
+  if (rc) return rc;
+  return synth_projections(seed, tid, q, row0, rows, nb, m_dtype, out_dev, stream, ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// Internal declarations shared by the translation units of libgw.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <math.h>
+
+#include "gw.h"
+
+namespace gw {
+
+// ---------------------------------------------------------------- errors ----
+// Bits of the device status word (one per device, see gw_check).
+enum : unsigned {
+  ST_EINVAL = 1u << 0,
+  ST_ENONFINITE = 1u << 1,
+  ST_ENOTHPD = 1u << 2,
+  ST_ETIMEOUT = 1u << 3,
+};
+
+int set_error(int code, const char* fmt, ...);  // records a thread-local message
+int cuda_error(cudaError_t e, const char* where);
+
+#define GW_CUDA_TRY(call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ::gw::cuda_error(e_, #call); \
+  } while (0)
+
+#define GW_LAUNCH_CHECK(where)                              \
+  do {                                                     \
+    cudaError_t e_ = cudaGetLastError();                   \
+    if (e_ != cudaSuccess) return ::gw::cuda_error(e_, where); \
+  } while (0)
+
+// Per-device context: status word address and SM count.
+struct DeviceCtx {
+  unsigned* status;   // device address of the status word
+  int sm_count;
+  int device;
+};
+int device_ctx(DeviceCtx* out);
+
+__device__ __forceinline__ void raise_status(unsigned* status, unsigned bit) {
+  atomicOr(status, bit);
+}
+
+// ------------------------------------------------------------- omega mesh ---
+struct OmegaArr {
+  double v[GW_MAX_NW];
+};
+
+// ---------------------------------------------------------- workspace -------
+// Bump allocator over the caller's workspace (256-byte aligned slices).
+struct WsCursor {
+  char* base;
+  size_t size;
+  size_t used;
+  __host__ void* take(size_t bytes) {
+    size_t off = (used + 255) & ~size_t(255);
+    if (base == nullptr || off + bytes > size) return nullptr;
+    used = off + bytes;
+    return base + off;
+  }
+};
+inline size_t ws_round(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------- launchers -------
+// a1
+int launch_weights(int64_t K, const double* delta, const double* f, double pref, int nw,
+                   const OmegaArr& om, double* w, cudaStream_t s, const DeviceCtx& ctx);
+
+// a2
+struct PolQ {
+  const void* M;
+  const double* delta;
+  const double* f;
+  double* P;
+  int64_t K;
+  int nb;
+};
+size_t pol_fp64_workspace(int nq, const int64_t* K, const int* nb, int nw);
+int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, void* ws,
+             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
+size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision);
+int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
+           void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
+
+// a3
+size_t dielectric_workspace(int nq, const int* nb, int nw);
+int dielectric_wc(int nq, const int* nb, int nw, const double* const* v, const double* const* P,
+                  double* const* Wc, void* ws, size_t ws_bytes, cudaStream_t s,
+                  const DeviceCtx& ctx);
+
+// a5
+size_t paircoef_workspace(int nq, const int64_t* npair, const int* nb, int nw, int precision);
+int paircoef(int nq, const int64_t* npair, const int* nb, const void* const* Msig, int dtype,
+             int nw, const double* const* Wc, double* const* c, int precision, void* ws,
+             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
+
+// a6
+size_t convolve_workspace(int nq, const int64_t* npair, int nw, int nw_out);
+int convolve(int nq, const double* wq, const int64_t* npair, int nw, const OmegaArr& om,
+             const double* const* c, const int* const* pair_state, const double* const* eps,
+             int nw_out, const OmegaArr& om_out, int nsig, double* sigma, void* ws,
+             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
+
+}  // namespace gw
+
+namespace gw {
+int synth_projections(uint64_t seed, uint32_t tid, uint32_t q, int64_t row0, int64_t rows, int nb,
+                      int dtype, void* out, cudaStream_t s, const DeviceCtx& ctx);
+int launch_lm(int ncurve, int nw, const OmegaArr& om, const double* sigma, const double* sign,
+              int npole, const double* theta_init, double* params, double* cost, int* iters,
+              int* status, int keep_better, cudaStream_t s);
+int mlp_forward(int n, const double* sigma, const float* w, float* out, cudaStream_t s);
+int mlp_train_step(int n, const OmegaArr& om, const double* sigma, float* w, float* grad, float* m,
+                   float* v, float lr, int step, float* loss, cudaStream_t s);
+constexpr int MLP_NIN = 48, MLP_NH = 128, MLP_NOUT = 8;
+constexpr int MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NOUT * MLP_NH + MLP_NOUT;
+}  // namespace gw

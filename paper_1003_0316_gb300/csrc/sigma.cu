@@ -1,0 +1,422 @@
+// a5 pair coefficients and a6 frequency convolution of the correlation self-energy
+// (Eq. SEc_AC and the paragraph after it).
+//
+// a5 (FP64 path): for each (q, frequency) the CTA tile computes
+//   Y[p][I] = sum_J m[p][J] W^c[I][J]      (64 pairs x 64 basis functions)
+// and folds it at once into c_p += Re sum_I conj(m[p][I]) Y[p][I]; partial sums per
+// I-tile are reduced in a fixed order.
+//
+// a6: the node values c_j of each pair are interpolated by a cubic spline in
+// lambda = w/(1+w); with w(lambda) = lambda/(1-lambda) the kernel of the w' integral,
+//   [g(w+w') + g(w-w')] dw'/dlambda,  g(x) = 1/(i x - e),
+// reduces by partial fractions to K(lambda) = -i b+/(A + b+ lambda) + i b-/(A + b- lambda)
+// with A = i w - e and b(+-) = +-i - A (the 1/(1-lambda) parts cancel between the two
+// terms). Each spline piece times K is integrated in closed form (moments of
+// 1/(z0 + b t), by series when the pole is far and by recurrence from the complex
+// logarithm otherwise), and the tail c_N w_N^2 / w'^2 beyond the last node likewise.
+#include <vector>
+#include <algorithm>
+
+#include "gw_internal.cuh"
+
+namespace gw {
+
+// ------------------------------------------------------------------ a5 -------
+constexpr int ST = 64;   // pair / basis tile
+constexpr int SKC = 8;   // J chunk
+constexpr int SMAXQ = 64;
+
+struct PairLaunch {
+  const double2* M[SMAXQ];
+  const double2* W[SMAXQ];
+  int64_t npair[SMAXQ];
+  int nb[SMAXQ];
+  int ptiles[SMAXQ];
+  int itiles[SMAXQ];
+  int64_t blk0[SMAXQ + 1];   // first block of q: blocks ordered (j, ptile, itile)
+  size_t part0[SMAXQ];       // first partial double of q
+  int nq;
+  int nw;
+};
+
+__global__ void __launch_bounds__(256) k_paircoef_fp64(PairLaunch L, double* __restrict__ part) {
+  int64_t blk = blockIdx.x;
+  int q = 0;
+  while (q + 1 < L.nq && blk >= L.blk0[q + 1]) ++q;
+  int64_t loc = blk - L.blk0[q];
+  const int it = int(loc % L.itiles[q]);
+  loc /= L.itiles[q];
+  const int pt = int(loc % L.ptiles[q]);
+  const int j = int(loc / L.ptiles[q]);
+  const int nb = L.nb[q];
+  const int64_t np = L.npair[q];
+  const double2* __restrict__ M = L.M[q];
+  const double2* __restrict__ W = L.W[q] + size_t(j) * nb * nb;
+
+  __shared__ double2 As[SKC][ST + 1];   // As[k][p] = m[p0+p][J0+k]
+  __shared__ double2 Bs[SKC][ST + 1];   // Bs[k][i] = W[I0+i][J0+k]
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t p0 = int64_t(pt) * ST;
+  const int I0 = it * ST;
+  double2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0.0, 0.0);
+
+  for (int J0 = 0; J0 < nb; J0 += SKC) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int e = tid + 256 * r;
+      int row = e >> 3, k = e & 7;
+      int J = J0 + k;
+      double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+      if (J < nb) {
+        if (p0 + row < np) a = M[(p0 + row) * nb + J];
+        if (I0 + row < nb) b = W[size_t(I0 + row) * nb + J];
+      }
+      As[k][row] = a;
+      Bs[k][row] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SKC; ++k) {
+      double2 av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          // Y[p][I] += m[p][J] * W[I][J]
+          acc[a][b].x = fma(av[a].x, bv[b].x, fma(-av[a].y, bv[b].y, acc[a][b].x));
+          acc[a][b].y = fma(av[a].x, bv[b].y, fma(av[a].y, bv[b].x, acc[a][b].y));
+        }
+    }
+    __syncthreads();
+  }
+  // c_p partial = Re sum_I conj(m[p][I]) Y[p][I]
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int64_t p = p0 + ty + 16 * a;
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int I = I0 + tx + 16 * b;
+      if (p < np && I < nb) {
+        double2 m = M[p * nb + I];
+        s = fma(m.x, acc[a][b].x, fma(m.y, acc[a][b].y, s));
+      }
+    }
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (tx == 0 && p < np) part[L.part0[q] + (size_t(j) * L.itiles[q] + it) * np + p] = s;
+  }
+}
+
+__global__ void k_paircoef_reduce(PairLaunch L, const double* __restrict__ part,
+                                  double* const* __restrict__ cout_unused, double* c0, int q,
+                                  int64_t np, int itiles, size_t part0, int nw) {
+  int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (e >= np * nw) return;
+  int j = int(e / np);
+  int64_t p = e % np;
+  double s = 0.0;
+  for (int it = 0; it < itiles; ++it) s += part[part0 + (size_t(j) * itiles + it) * np + p];
+  c0[size_t(j) * np + p] = s;
+}
+
+size_t paircoef_workspace(int nq, const int64_t* npair, const int* nb, int nw, int precision) {
+  size_t b = 0;
+  for (int q = 0; q < nq; ++q) {
+    int it = (nb[q] + ST - 1) / ST;
+    b += size_t(nw) * it * size_t(npair[q]);
+  }
+  return ws_round(b * sizeof(double));
+}
+
+int paircoef(int nq, const int64_t* npair, const int* nb, const void* const* Msig, int dtype,
+             int nw, const double* const* Wc, double* const* c, int precision, void* ws,
+             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
+  if (precision != GW_FP64) return set_error(GW_EUNSUPPORTED, "pair coefficients: precision %d not built", precision);
+  double* part = static_cast<double*>(ws);
+  for (int q0 = 0; q0 < nq; q0 += SMAXQ) {
+    int n = std::min(SMAXQ, nq - q0);
+    PairLaunch L{};
+    L.nq = n;
+    L.nw = nw;
+    int64_t blk = 0;
+    size_t p0 = 0;
+    for (int q = 0; q < n; ++q) {
+      int Q = q0 + q;
+      L.M[q] = static_cast<const double2*>(Msig[Q]);
+      L.W[q] = reinterpret_cast<const double2*>(Wc[Q]);
+      L.npair[q] = npair[Q];
+      L.nb[q] = nb[Q];
+      L.ptiles[q] = int((npair[Q] + ST - 1) / ST);
+      L.itiles[q] = (nb[Q] + ST - 1) / ST;
+      L.blk0[q] = blk;
+      L.part0[q] = p0;
+      blk += int64_t(nw) * L.ptiles[q] * L.itiles[q];
+      p0 += size_t(nw) * L.itiles[q] * size_t(npair[Q]);
+    }
+    L.blk0[n] = blk;
+    if (blk > 0) {
+      k_paircoef_fp64<<<unsigned(blk), 256, 0, s>>>(L, part);
+      GW_LAUNCH_CHECK("k_paircoef_fp64");
+    }
+    for (int q = 0; q < n; ++q) {
+      int64_t np = L.npair[q];
+      if (np == 0) continue;
+      int64_t tot = np * nw;
+      k_paircoef_reduce<<<unsigned((tot + 255) / 256), 256, 0, s>>>(
+          L, part, nullptr, c[q0 + q], q, np, L.itiles[q], L.part0[q], nw);
+      GW_LAUNCH_CHECK("k_paircoef_reduce");
+    }
+  }
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ a6 -------
+struct cplx {
+  double x, y;
+};
+__device__ __forceinline__ cplx mk(double x, double y) { return cplx{x, y}; }
+__device__ __forceinline__ cplx operator+(cplx a, cplx b) { return mk(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cplx operator-(cplx a, cplx b) { return mk(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cplx operator*(cplx a, cplx b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ cplx operator*(double s, cplx a) { return mk(s * a.x, s * a.y); }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  // Smith's algorithm
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    return mk((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    double r = b.x / b.y, d = b.y + b.x * r;
+    return mk((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+__device__ __forceinline__ double cabs_(cplx a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ cplx clog_(cplx a) { return mk(log(hypot(a.x, a.y)), atan2(a.y, a.x)); }
+
+constexpr double SERIES_R = 0.3;
+constexpr int SERIES_N = 36;
+
+// I_k = int_0^H t^k / (z0 + b t) dt, k = 0..3
+__device__ void moments(cplx z0, cplx b, double H, cplx I[4]) {
+  cplx r = cdiv(H * b, z0);
+  if (cabs_(r) < SERIES_R) {
+    cplx term = mk(1.0, 0.0);
+    cplx nr = mk(-r.x, -r.y);
+    cplx s0 = mk(0, 0), s1 = mk(0, 0), s2 = mk(0, 0), s3 = mk(0, 0);
+    for (int m = 0; m < SERIES_N; ++m) {
+      s0 = s0 + (1.0 / (m + 1)) * term;
+      s1 = s1 + (1.0 / (m + 2)) * term;
+      s2 = s2 + (1.0 / (m + 3)) * term;
+      s3 = s3 + (1.0 / (m + 4)) * term;
+      term = term * nr;
+    }
+    cplx iz = cdiv(mk(1.0, 0.0), z0);
+    double h1 = H, h2 = H * H, h3 = h2 * H, h4 = h3 * H;
+    I[0] = h1 * (s0 * iz);
+    I[1] = h2 * (s1 * iz);
+    I[2] = h3 * (s2 * iz);
+    I[3] = h4 * (s3 * iz);
+  } else {
+    cplx ib = cdiv(mk(1.0, 0.0), b);
+    I[0] = clog_(mk(1.0 + r.x, r.y)) * ib;
+    double hk = 1.0;
+    for (int k = 1; k < 4; ++k) {
+      hk *= H;
+      I[k] = (mk(hk / k, 0.0) - z0 * I[k - 1]) * ib;
+    }
+  }
+}
+
+// int_X^inf dx / (x^2 (A + i s x))
+__device__ cplx tail_integral(cplx A, double sgn, double X) {
+  cplx isg = mk(0.0, sgn);
+  cplx rho = cdiv(A, mk(0.0, sgn * X));
+  if (cabs_(rho) < 0.5) {
+    cplx term = mk(1.0, 0.0), nr = mk(-rho.x, -rho.y), s = mk(0, 0);
+    for (int m = 0; m < 56; ++m) {
+      s = s + (1.0 / (m + 2)) * term;
+      term = term * nr;
+    }
+    return cdiv(s, mk(0.0, sgn * X * X));
+  }
+  cplx a2 = A * A;
+  cplx zx = mk(A.x / X, A.y / X + sgn);
+  cplx L = clog_(cdiv(isg, zx));
+  return cdiv(mk(1.0, 0.0), mk(A.x * X, A.y * X)) + cdiv(isg * L, a2);
+}
+
+__device__ cplx pair_integral(const double* __restrict__ c, int64_t stride, int nw,
+                              const double* lam, const double* h, double wN, double w,
+                              double e) {
+  // node values and secant slopes
+  double y[GW_MAX_NW], m[GW_MAX_NW], cp[GW_MAX_NW];
+  for (int j = 0; j < nw; ++j) y[j] = c[j * stride];
+  const int n = nw;
+  // tridiagonal system for the slopes (not-a-knot left, clamped right)
+  {
+    double d0 = (y[1] - y[0]) / h[0], d1 = (y[2] - y[1]) / h[1];
+    double b0 = h[1], c0 = h[0] + h[1];
+    double r0 = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * d0 + h[0] * h[0] * d1) / (h[0] + h[1]);
+    cp[0] = c0 / b0;
+    m[0] = r0 / b0;
+    for (int i = 1; i < n - 1; ++i) {
+      double dl = (y[i] - y[i - 1]) / h[i - 1], dr = (y[i + 1] - y[i]) / h[i];
+      double a = h[i], b = 2.0 * (h[i - 1] + h[i]), cc = h[i - 1];
+      double r = 3.0 * (h[i] * dl + h[i - 1] * dr);
+      double den = b - a * cp[i - 1];
+      cp[i] = cc / den;
+      m[i] = (r - a * m[i - 1]) / den;
+    }
+    double sig = -2.0 * (1.0 + wN) * (1.0 + wN) / wN;
+    m[n - 1] = sig * y[n - 1];
+    for (int i = n - 2; i >= 0; --i) m[i] = m[i] - cp[i] * m[i + 1];
+  }
+  const cplx A = mk(-e, w);
+  const cplx bp = mk(A.x * -1.0, 1.0 - A.y);    // i - A
+  const cplx bm = mk(A.x * -1.0, -1.0 - A.y);   // -i - A
+  cplx total = mk(0, 0);
+  for (int s = 0; s < n; ++s) {
+    // piece s: s = 0 is [0, lam0] with segment 0 extrapolated; s >= 1 is segment s-1
+    int g = s == 0 ? 0 : s - 1;
+    double dlt = (y[g + 1] - y[g]) / h[g];
+    double C[4];
+    C[0] = y[g];
+    C[1] = m[g];
+    C[2] = (3.0 * dlt - 2.0 * m[g] - m[g + 1]) / h[g];
+    C[3] = (m[g] + m[g + 1] - 2.0 * dlt) / (h[g] * h[g]);
+    double la, H;
+    if (s == 0) {
+      // re-centre the cubic at lambda = 0: t = u - lam0
+      double x0 = -lam[0];
+      double D0 = C[0] + x0 * (C[1] + x0 * (C[2] + x0 * C[3]));
+      double D1 = C[1] + x0 * (2.0 * C[2] + 3.0 * x0 * C[3]);
+      double D2 = C[2] + 3.0 * x0 * C[3];
+      C[0] = D0;
+      C[1] = D1;
+      C[2] = D2;
+      la = 0.0;
+      H = lam[0];
+    } else {
+      la = lam[g];
+      H = h[g];
+    }
+    cplx Ip[4], Im[4];
+    moments(A + la * bp, bp, H, Ip);
+    moments(A + la * bm, bm, H, Im);
+    cplx acc_p = mk(0, 0), acc_m = mk(0, 0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc_p = acc_p + C[k] * Ip[k];
+      acc_m = acc_m + C[k] * Im[k];
+    }
+    // -i b+ acc_p + i b- acc_m
+    cplx t1 = mk(0.0, -1.0) * (bp * acc_p);
+    cplx t2 = mk(0.0, 1.0) * (bm * acc_m);
+    total = total + t1 + t2;
+  }
+  cplx tl = tail_integral(A, 1.0, wN) + tail_integral(A, -1.0, wN);
+  total = total + (y[n - 1] * wN * wN) * tl;
+  return total;
+}
+
+constexpr int CTHREADS = 256;
+struct ConvLaunch {
+  const double* c[SMAXQ];
+  const int* state[SMAXQ];
+  const double* eps[SMAXQ];
+  int64_t npair[SMAXQ];
+  double wq[SMAXQ];
+  int nq;
+};
+
+__global__ void __launch_bounds__(CTHREADS) k_convolve(ConvLaunch L, int nw, OmegaArr om,
+                                                       OmegaArr om_out, int nw_out,
+                                                       double* __restrict__ sigma, int accumulate,
+                                                       unsigned* status) {
+  const int sidx = blockIdx.x, i = blockIdx.y;
+  __shared__ double lam[GW_MAX_NW], h[GW_MAX_NW];
+  __shared__ double red_x[CTHREADS], red_y[CTHREADS];
+  if (threadIdx.x < nw) lam[threadIdx.x] = om.v[threadIdx.x] / (1.0 + om.v[threadIdx.x]);
+  __syncthreads();
+  if (threadIdx.x < nw - 1) h[threadIdx.x] = lam[threadIdx.x + 1] - lam[threadIdx.x];
+  __syncthreads();
+  const double w = om_out.v[i];
+  const double wN = om.v[nw - 1];
+  double sx = 0.0, sy = 0.0;
+  for (int q = 0; q < L.nq; ++q) {
+    const int64_t np = L.npair[q];
+    double px = 0.0, py = 0.0;
+    for (int64_t p = threadIdx.x; p < np; p += CTHREADS) {
+      if (L.state[q][p] != sidx) continue;
+      double e = L.eps[q][p];
+      if (!(e != 0.0) || !isfinite(e)) {
+        raise_status(status, ST_EINVAL);
+        continue;
+      }
+      cplx v = pair_integral(L.c[q] + p, np, nw, lam, h, wN, w, e);
+      px += v.x;
+      py += v.y;
+    }
+    sx += L.wq[q] * px;
+    sy += L.wq[q] * py;
+  }
+  red_x[threadIdx.x] = sx;
+  red_y[threadIdx.x] = sy;
+  __syncthreads();
+  for (int off = CTHREADS / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      red_x[threadIdx.x] += red_x[threadIdx.x + off];
+      red_y[threadIdx.x] += red_y[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double f = -1.0 / (2.0 * 3.14159265358979323846);
+    double2* out = reinterpret_cast<double2*>(sigma) + size_t(sidx) * nw_out + i;
+    double2 v = make_double2(f * red_x[0], f * red_y[0]);
+    if (accumulate) {
+      double2 o = *out;
+      v.x += o.x;
+      v.y += o.y;
+    }
+    *out = v;
+  }
+}
+
+size_t convolve_workspace(int, const int64_t*, int, int) { return 0; }
+
+int convolve(int nq, const double* wq, const int64_t* npair, int nw, const OmegaArr& om,
+             const double* const* c, const int* const* pair_state, const double* const* eps,
+             int nw_out, const OmegaArr& om_out, int nsig, double* sigma, void*, size_t,
+             cudaStream_t s, const DeviceCtx& ctx) {
+  for (int q0 = 0; q0 < nq; q0 += SMAXQ) {
+    int n = std::min(SMAXQ, nq - q0);
+    ConvLaunch L{};
+    L.nq = n;
+    for (int q = 0; q < n; ++q) {
+      L.c[q] = c[q0 + q];
+      L.state[q] = pair_state[q0 + q];
+      L.eps[q] = eps[q0 + q];
+      L.npair[q] = npair[q0 + q];
+      L.wq[q] = wq[q0 + q];
+    }
+    dim3 grid(nsig, nw_out);
+    k_convolve<<<grid, CTHREADS, 0, s>>>(L, nw, om, om_out, nw_out, sigma, q0 > 0 ? 1 : 0,
+                                         ctx.status);
+    GW_LAUNCH_CHECK("k_convolve");
+  }
+  return GW_OK;
+}
+
+}  // namespace gw
