@@ -1,13 +1,613 @@
-// a2 tensor-core path (placeholder until the tcgen05 kernel lands).
+// a2 tensor-core path: P_IJ(q, i w_j) = sum_t w_tj M_tI conj(M_tJ) (Eq. polar_MB at
+// w = i omega) on tcgen05 with split-precision operands.
+//
+// The complex rank-K update is one real weighted Gram matrix: with x the FP32
+// interleaved view of M ([K][2 N_b]) and s_tj = |w_tj|,
+//   G_j = x^T diag(s_j) x,   P_IJ = -(G[2I][2J] + G[2I+1][2J+1]) - i (G[2I+1][2J] - G[2I][2J+1]).
+// A CTA tile is 128 rows (A: the s_tj-scaled columns of x) by 128 columns (B: the plain
+// columns of x) of G_j for one frequency. Every operand y is split as y = hi + lo (TF32
+// or BF16 pieces, each rounded to nearest) and each product is formed as
+//   lo_A*hi_B + hi_A*lo_B + hi_A*hi_B
+// by three MMAs into the same TMEM accumulator.
+//
+// Accuracy: the tensor core adds into its FP32 accumulator with truncation, which
+// biases a long chain of additions toward zero (about 2e-8 of the running value per
+// MMA). Every chunk of 64 bytes of K (16 TF32 or 32 BF16 transitions) therefore starts
+// a fresh accumulator; the epilogue adds the chunk results into FP32 registers (round
+// to nearest) and folds each running sum into FP64 every 256 chunks (FP64 reductions
+// performed at L2 into per-CTA sums), so no truncating
+// chain is longer than six MMAs (one chunk); the round-to-nearest FP32 sums add only
+// unbiased errors that average out over the folds.
+//
+// Layout and roles (512 threads, one persistent CTA per SM; 512 TMEM columns):
+//   TMEM  cols [0,128) and [128,256): two accumulators (chunk c uses c mod 2);
+//         cols [256,352): three A slots (16 columns hi + 16 lo each).
+//   warps 0-3    A transform: scale x by s_tj, split, tcgen05.st into the A slot of
+//                their lane quadrant;
+//   warps 4-5    B transform: split x into the K-major 64-byte-swizzled hi/lo tiles
+//                of a three-stage shared-memory ring;
+//   warp 6       one thread issues tcgen05.mma (A from TMEM, B from shared memory);
+//                warp 7 idles
+//                and tcgen05.commit;
+//   warps 8-15   epilogue: tcgen05.ld of the finished accumulator, FP32 running sums
+//                in registers (64 per thread),
+//                FP64 folding, the final complex combination and the Hermitian store.
+// Only tiles that meet the upper triangle (complex I <= J) are computed. Every mbarrier
+// wait is bounded; on expiry the CTA records a timeout in the status word and winds
+// down, waiting for its own MMAs before releasing TMEM.
+#include <vector>
+#include <algorithm>
+#include <cstdlib>
+#include <cuda_bf16.h>
+
 #include "gw_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace gw {
 
-size_t pol_tc_workspace(int, const int64_t*, const int*, int, int) { return 0; }
+namespace {
 
-int pol_tc(int, const PolQ*, double, int, const OmegaArr&, int precision, void*, size_t,
-           cudaStream_t, const DeviceCtx&) {
-  return set_error(GW_EUNSUPPORTED, "tensor-core polarization (precision %d) not built", precision);
+constexpr int TM = 128;          // real Gram rows per tile (A operand, in TMEM)
+constexpr int TN = 128;          // real Gram columns per tile (B operand, in shared memory)
+constexpr int SWB = 64;          // bytes of K per B row per chunk (64-byte swizzle)
+constexpr int NS = 3;            // B stages in shared memory = A slots in TMEM
+constexpr int B_TILE = TN * SWB;                 // 8 KB
+constexpr int STAGE_BYTES = 2 * B_TILE;          // hi + lo
+constexpr uint32_t ACC_COL = 0;                  // two accumulators: cols [0,128), [128,256)
+constexpr uint32_t A_COL = 2 * TN;               // A slots: 32 columns each (16 hi + 16 lo)
+constexpr int NWARPS = 16;
+constexpr int NTHREADS = NWARPS * 32;
+constexpr int PROD_WARP = 4;     // one thread: bulk copies of the pre-split B tiles
+constexpr int MMA_WARP = 5;      // warps 6-7 idle
+constexpr int EPI_WARP0 = 8;     // warps 8-15: drain/epilogue (two per lane quadrant)
+constexpr int EPI_COLS = TN / 2; // 64 columns per epilogue thread
+#ifndef GW_TC_CPD
+#define GW_TC_CPD 1
+#endif
+constexpr int CPD = GW_TC_CPD;                   // chunks accumulated per TMEM drain
+constexpr int FLUSH = 256;                       // chunks per FP64 fold of a running sum
+constexpr int TQ = 64;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+
+struct TcLaunch {
+  const float* xT[TQ];      // [ncolp][kpad] column-major copy of the FP32 view of M (zero padded)
+  const char* bsp[TQ];      // [nbi][nch] pre-split B tiles: 8 KB hi + 8 KB lo, swizzled
+  const float* s[TQ];       // [nw][kpad] |w_tj| in FP32 (zero padded)
+  double2* P[TQ];
+  int64_t K[TQ];
+  int64_t kpad[TQ];
+  int nb[TQ];
+  int nbi[TQ];
+  int ntile[TQ];
+  int64_t item0[TQ + 1];
+  int nq;
+  int nw;
+};
+
+__device__ __forceinline__ void decode_item(const TcLaunch& L, int64_t item, int& q, int& j,
+                                            int& bi, int& bj) {
+  q = 0;
+  while (q + 1 < L.nq && item >= L.item0[q + 1]) ++q;
+  int64_t loc = item - L.item0[q];
+  int u = int(loc % L.ntile[q]);
+  j = int(loc / L.ntile[q]);
+  const int nbi = L.nbi[q];
+  (void)nbi;
+  bj = 0;
+  while (u > bj) {      // upper tiles bi <= bj, column by column
+    u -= bj + 1;
+    ++bj;
+  }
+  bi = u;
+}
+
+// byte offset of (row n, 16-byte chunk kc) in a K-major, 64-byte-swizzled tile
+__device__ __forceinline__ uint32_t sw64_off(int n, int kc) {
+  return uint32_t((n >> 3) * 512 + (n & 7) * 64 + ((kc ^ ((n & 7) >> 1)) << 4));
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float y) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(y));
+  return r;
+}
+
+// y -> (hi, lo) pieces packed as 32-bit TMEM / shared-memory words.
+// TF32: one value per word. BF16: two consecutive K values per word (low half first).
+template <bool BF16>
+__device__ __forceinline__ void split_words(const float* y, uint32_t* hi, uint32_t* lo, int nwords) {
+  if (!BF16) {
+    for (int i = 0; i < nwords; ++i) {
+      uint32_t h = tf32_rna(y[i]);
+      hi[i] = h;
+      lo[i] = tf32_rna(y[i] - __uint_as_float(h));
+    }
+  } else {
+    for (int i = 0; i < nwords; ++i) {
+      __nv_bfloat16 h0 = __float2bfloat16_rn(y[2 * i]), h1 = __float2bfloat16_rn(y[2 * i + 1]);
+      __nv_bfloat16 l0 = __float2bfloat16_rn(y[2 * i] - __bfloat162float(h0));
+      __nv_bfloat16 l1 = __float2bfloat16_rn(y[2 * i + 1] - __bfloat162float(h1));
+      hi[i] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+      lo[i] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+    }
+  }
+}
+
+// One bounded wait by lane 0, broadcast to the warp; raises the abort flag on expiry.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          unsigned* status) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) {
+    ok = (!*abort && tc::mbar_wait(bar, parity, abort, WAIT_LIMIT)) ? 1 : 0;
+    if (!ok && !*abort) {
+      *abort = 1;
+      raise_status(status, ST_ETIMEOUT);
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_herk_tc(const __grid_constant__ TcLaunch L, double* __restrict__ acc64, unsigned* status) {
+  constexpr int CH = BF16 ? 32 : 16;          // transitions per chunk (64 bytes of K)
+  constexpr int EPC = CH / 4;                 // K values per 16-byte chunk of a B row
+  constexpr uint32_t IDESC = tc::instr_desc(BF16 ? 1u : 2u, TM, TN);
+
+  extern __shared__ __align__(1024) char dsmem[];
+  char* ring = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[NS], empty_bar[NS], accf_bar[2], acce_bar[2], done_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NS; ++i) {
+      tc::mbar_init(&full_bar[i], 5);      // 4 A warps + the bulk-copy producer
+      tc::mbar_init(&empty_bar[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&accf_bar[i], 1);
+      tc::mbar_init(&acce_bar[i], 8);      // 8 epilogue warps
+    }
+    tc::mbar_init(&done_bar, 1);
+    s_abort = 0;
+    tc::mbar_fence_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&s_tmem, 512);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int64_t nitems = L.item0[L.nq];
+
+  if (warp < PROD_WARP) {
+    // ------------------------------------------------ A transform -> TMEM
+    // Units of 16 transitions (one TF32 chunk, half a BF16 chunk): each lane reads its
+    // column of the column-major copy and the weights as float4s; two units of loads
+    // are kept in flight ahead of the split.
+    const int qd = warp;                      // TMEM lane quadrant = A rows 32 qd .. 32 qd + 31
+    const int m = qd * 32 + lane;
+    constexpr int UPC = CH / 16;              // units per chunk
+    uint32_t g = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+      int q, j, bi, bj;
+      decode_item(L, item, q, j, bi, bj);
+      const int64_t K = L.K[q];
+      const int64_t kpad = L.kpad[q];
+      const float4* __restrict__ xc = reinterpret_cast<const float4*>(L.xT[q] + size_t(bi * TM + m) * kpad);
+      const float4* __restrict__ sj = reinterpret_cast<const float4*>(L.s[q] + size_t(j) * kpad);
+      const int64_t nch = (K + CH - 1) / CH;
+      const int64_t nunit = nch * UPC;
+      float4 xa[4], sa[4], xb[4], sb[4];
+      if (nunit > 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xa[e] = __ldg(xc + e);
+          sa[e] = __ldg(sj + e);
+        }
+      }
+      if (nunit > 1) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xb[e] = __ldg(xc + 4 + e);
+          sb[e] = __ldg(sj + 4 + e);
+        }
+      }
+      bool stop = false;
+      for (int64_t u = 0; u < nunit; ++u) {
+        const int64_t c = u / UPC;
+        const int uc = int(u % UPC);
+        const uint32_t gg = g + uint32_t(c);
+        const int st = gg % NS;
+        float4 xn[4], sn[4];
+        if (u + 2 < nunit) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            xn[e] = __ldg(xc + (u + 2) * 4 + e);
+            sn[e] = __ldg(sj + (u + 2) * 4 + e);
+          }
+        }
+        if (uc == 0 && !warp_wait(&empty_bar[st], ((gg / NS) & 1) ^ 1, &s_abort, status)) {
+          stop = true;
+          break;
+        }
+        float y[16];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          y[4 * e + 0] = sa[e].x * xa[e].x;
+          y[4 * e + 1] = sa[e].y * xa[e].y;
+          y[4 * e + 2] = sa[e].z * xa[e].z;
+          y[4 * e + 3] = sa[e].w * xa[e].w;
+        }
+        const uint32_t slot = tmem + (uint32_t(qd * 32) << 16) + A_COL + st * 32;
+        if (!BF16) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t hw[8], lw[8];
+            split_words<false>(y + 8 * h, hw, lw, 8);
+            tc::tmem_st8(slot + h * 8, hw);
+            tc::tmem_st8(slot + 16 + h * 8, lw);
+          }
+        } else {
+          uint32_t hw[8], lw[8];
+          split_words<true>(y, hw, lw, 8);
+          tc::tmem_st8(slot + uc * 8, hw);
+          tc::tmem_st8(slot + 16 + uc * 8, lw);
+        }
+        if (uc == UPC - 1) {
+          tc::tmem_wait_st();
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&full_bar[st]);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xa[e] = xb[e];
+          sa[e] = sb[e];
+          xb[e] = xn[e];
+          sb[e] = sn[e];
+        }
+      }
+      g += uint32_t(nch);
+      if (stop) break;
+    }
+  } else if (warp == PROD_WARP) {
+    // ------------------------------------------------ B tiles: bulk copies
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        int q, j, bi, bj;
+        decode_item(L, item, q, j, bi, bj);
+        const int64_t nch = (L.K[q] + CH - 1) / CH;
+        const char* src = L.bsp[q] + size_t(bj) * nch * STAGE_BYTES;
+        for (int64_t c = 0; c < nch; ++c, ++g) {
+          const int st = g % NS;
+          if (!tc::mbar_wait(&empty_bar[st], ((g / NS) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&full_bar[st], STAGE_BYTES);
+          tc::bulk_g2s(ring + st * STAGE_BYTES, src + size_t(c) * STAGE_BYTES, STAGE_BYTES,
+                       &full_bar[st]);
+        }
+      }
+      if (!ok && !s_abort) {
+        s_abort = 1;
+        raise_status(status, ST_ETIMEOUT);
+      }
+    }
+    __syncwarp();
+  } else if (warp == MMA_WARP) {
+    // ------------------------------------------------ MMA issue
+    if (lane == 0) {
+      uint32_t g = 0, gp = 0;
+      const uint32_t ring_addr = tc::smem_u32(ring);
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        int q, j, bi, bj;
+        decode_item(L, item, q, j, bi, bj);
+        const int64_t nch = (L.K[q] + CH - 1) / CH;
+        for (int64_t c = 0; c < nch; ++c, ++g) {
+          const int st = g % NS;
+          const int buf = gp & 1;
+          const bool first = (c % CPD) == 0;
+          if (!tc::mbar_wait(&full_bar[st], (g / NS) & 1, &s_abort, WAIT_LIMIT) ||
+              (first && !tc::mbar_wait(&acce_bar[buf], ((gp >> 1) & 1) ^ 1, &s_abort, WAIT_LIMIT))) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t d = tmem + ACC_COL + buf * TN;
+          const uint32_t a = tmem + A_COL + st * 32;
+          const uint32_t bs = ring_addr + st * STAGE_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t dBh = tc::smem_desc(bs + ks * 32, 512, 4);
+            const uint64_t dBl = tc::smem_desc(bs + B_TILE + ks * 32, 512, 4);
+            const uint32_t ah = a + ks * 8, al = a + 16 + ks * 8;
+            const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
+            if (BF16) {
+              tc::mma_f16_ta(d, al, dBh, IDESC, acc0);
+              tc::mma_f16_ta(d, ah, dBl, IDESC, 1u);
+              tc::mma_f16_ta(d, ah, dBh, IDESC, 1u);
+            } else {
+              tc::mma_tf32_ta(d, al, dBh, IDESC, acc0);
+              tc::mma_tf32_ta(d, ah, dBl, IDESC, 1u);
+              tc::mma_tf32_ta(d, ah, dBh, IDESC, 1u);
+            }
+          }
+          tc::mma_commit(&empty_bar[st]);
+          if ((c % CPD) == CPD - 1 || c == nch - 1) {
+            tc::mma_commit(&accf_bar[buf]);
+            ++gp;
+          }
+        }
+      }
+      if (!ok && !s_abort) {
+        s_abort = 1;
+        raise_status(status, ST_ETIMEOUT);
+      }
+      tc::mma_commit(&done_bar);
+      int never = 0;
+      tc::mbar_wait(&done_bar, 0, reinterpret_cast<volatile int*>(&never), WAIT_LIMIT);
+    }
+    __syncwarp();
+  } else if (warp >= EPI_WARP0) {
+    // ------------------------------------------------ drain / epilogue
+    const int qd = warp & 3;
+    const int hf = (warp - EPI_WARP0) >> 2;
+    const int r = qd * 32 + lane;               // tile row
+    const int c0 = hf * EPI_COLS;               // first tile column of this thread
+    double* acc = acc64 + size_t(blockIdx.x) * TN * TM + size_t(c0) * TM + r;   // [col][row]
+    uint32_t gp = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+      int q, j, bi, bj;
+      decode_item(L, item, q, j, bi, bj);
+      const int64_t nch = (L.K[q] + CH - 1) / CH;
+      const int64_t nper = (nch + CPD - 1) / CPD;
+      const int nb = L.nb[q];
+      float sum[EPI_COLS];
+#pragma unroll
+      for (int i = 0; i < EPI_COLS; ++i) {
+        sum[i] = 0.0f;
+        acc[size_t(i) * TM] = 0.0;
+      }
+      bool stop = false;
+      for (int64_t c = 0; c < nper; ++c, ++gp) {
+        const int buf = gp & 1;
+        if (!warp_wait(&accf_bar[buf], (gp >> 1) & 1, &s_abort, status)) {
+          stop = true;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + ACC_COL + buf * TN + c0;
+#pragma unroll
+        for (int k = 0; k < EPI_COLS / 32; ++k) {
+          float v[32];
+          tc::tmem_ld32(base + k * 32, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) sum[k * 32 + i] += v[i];
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
+        // fold the FP32 running sums into FP64 every FLUSH chunks, staggered over the
+        // epilogue warps so the slow FP64 adds of different warps do not coincide
+        if (int((c + (warp - EPI_WARP0) * (FLUSH / 8)) % FLUSH) == FLUSH - 1) {
+#pragma unroll
+          for (int i = 0; i < EPI_COLS; ++i) {
+            atomicAdd(acc + size_t(i) * TM, double(sum[i]));   // reduction at L2, no load
+            sum[i] = 0.0f;
+          }
+        }
+      }
+      if (stop) break;
+      // final fold, then the complex combination of rows (2I, 2I+1) held by lanes (2l, 2l+1)
+#pragma unroll
+      for (int i = 0; i < EPI_COLS; ++i) atomicAdd(acc + size_t(i) * TM, double(sum[i]));
+      __threadfence();
+      const int R = bi * TM + r;
+      const int I = R >> 1;
+      const bool odd = R & 1;
+      double2* P = L.P[q] + size_t(j) * nb * nb;
+#pragma unroll 4
+      for (int jj = 0; jj < EPI_COLS / 2; ++jj) {
+        double e0 = acc[size_t(2 * jj) * TM];
+        double e1 = acc[size_t(2 * jj + 1) * TM];
+        double o0 = __shfl_xor_sync(0xffffffffu, e0, 1);
+        double o1 = __shfl_xor_sync(0xffffffffu, e1, 1);
+        if (!odd) {
+          const int J = (bj * TN + c0) / 2 + jj;
+          if (I < nb && J < nb && I <= J) {
+            double re = -(e0 + o1);
+            double im = (I == J) ? 0.0 : -(o0 - e1);
+            P[size_t(I) * nb + J] = make_double2(re, im);
+            if (I != J) P[size_t(J) * nb + I] = make_double2(re, -im);
+          }
+        }
+      }
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// Per q, once: the column-major copy xT (A side) and the pre-split, pre-swizzled B tiles
+// (frequency independent). One CTA per (128-column block, chunk); the chunk of x is
+// staged through shared memory with coalesced float4 loads.
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, int64_t K, int ncol,
+                                                 int64_t kpad, int64_t nch, float* __restrict__ xT,
+                                                 char* __restrict__ bsp) {
+  constexpr int CH = BF16 ? 32 : 16;
+  constexpr int EPC = CH / 4;
+  __shared__ __align__(16) float tile[CH][TM + 4];
+  const int cb = blockIdx.x;
+  const int64_t c = blockIdx.y;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < CH * (TM / 4); idx += 128) {
+    const int t = idx / (TM / 4), c4 = idx % (TM / 4);
+    const int64_t row = c * CH + t;
+    const int col = cb * TM + 4 * c4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < K && col < ncol) v = __ldg(reinterpret_cast<const float4*>(x + row * ncol + col));
+    *reinterpret_cast<float4*>(&tile[t][4 * c4]) = v;
+  }
+  __syncthreads();
+  const int n = tid;
+  float v[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t) v[t] = tile[t][n];
+  float4* dst = reinterpret_cast<float4*>(xT + size_t(cb * TM + n) * kpad + c * CH);
+#pragma unroll
+  for (int t = 0; t < CH / 4; ++t) dst[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+  char* hi = bsp + (size_t(cb) * nch + c) * STAGE_BYTES;
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) {
+    uint32_t hw[4], lw[4];
+    split_words<BF16>(v + kc * EPC, hw, lw, 4);
+    const uint32_t off = sw64_off(n, kc);
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(hi + B_TILE + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+// s_tj = |w_tj| = prefactor f_t 2 Delta_t / (Delta_t^2 + omega_j^2), stored in FP32
+__global__ void k_abs_weights_f32(int64_t K, int64_t kpad, const double* __restrict__ delta,
+                                  const double* __restrict__ f, double pref, int nw, OmegaArr om,
+                                  float* __restrict__ s, unsigned* status) {
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (; t < kpad; t += stride) {
+    if (t >= K) {
+      for (int j = 0; j < nw; ++j) s[size_t(j) * kpad + t] = 0.0f;
+      continue;
+    }
+    double d = delta[t];
+    if (!(d > 0.0)) raise_status(status, ST_EINVAL);
+    double a = 2.0 * pref * (f ? f[t] : 1.0) * d;
+    for (int j = 0; j < nw; ++j) s[size_t(j) * kpad + t] = float(a / (d * d + om.v[j] * om.v[j]));
+  }
+}
+
+int tile_count(int nb, int* nbi_out) {
+  int nbi = (2 * nb + TM - 1) / TM;   // TM == TN: square tiles, upper triangle
+  if (nbi_out) *nbi_out = nbi;
+  return nbi * (nbi + 1) / 2;
+}
+
+}  // namespace
+
+static int64_t chunk_rows(int precision) { return precision == GW_BF16X3 ? 32 : 16; }
+
+static void q_sizes(int64_t K, int nb, int precision, int64_t* nch, int64_t* kpad, int* nbi) {
+  const int64_t ch = chunk_rows(precision);
+  *nch = (K + ch - 1) / ch;
+  *kpad = *nch * ch;
+  *nbi = (2 * nb + TM - 1) / TM;
+}
+
+size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision) {
+  int sm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  size_t b = ws_round(size_t(sm) * TN * TM * sizeof(double));
+  for (int q = 0; q < nq; ++q) {
+    int64_t nch, kpad;
+    int nbi;
+    q_sizes(K[q], nb[q], precision, &nch, &kpad, &nbi);
+    b += ws_round(size_t(nw) * size_t(kpad) * sizeof(float));            // weights
+    b += ws_round(size_t(nbi) * TM * size_t(kpad) * sizeof(float));       // column-major copy
+    b += ws_round(size_t(nbi) * size_t(nch) * STAGE_BYTES);              // pre-split B tiles
+  }
+  return b;
+}
+
+template <bool BF16>
+static int prepare_kernel(const DeviceCtx& ctx, size_t smem) {
+  static bool done[64] = {};
+  if (done[ctx.device]) return GW_OK;
+  GW_CUDA_TRY(cudaFuncSetAttribute(k_herk_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  done[ctx.device] = true;
+  return GW_OK;
+}
+
+int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
+           void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
+  for (int q = 0; q < nq; ++q)
+    if (qs[q].nb & 1)
+      return set_error(GW_EINVAL, "tensor-core path needs an even N_b (q=%d has %d)", q, qs[q].nb);
+  const bool bf = precision == GW_BF16X3;
+  WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
+  double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
+  if (!acc64) return set_error(GW_EWORKSPACE, "internal: tensor-core workspace too small");
+  std::vector<float*> sw(nq), xT(nq);
+  std::vector<char*> bsp(nq);
+  std::vector<int64_t> kp(nq);
+  for (int q = 0; q < nq; ++q) {
+    int64_t nch, kpad;
+    int nbi;
+    q_sizes(qs[q].K, qs[q].nb, precision, &nch, &kpad, &nbi);
+    kp[q] = kpad;
+    sw[q] = static_cast<float*>(cur.take(size_t(nw) * size_t(kpad) * sizeof(float)));
+    xT[q] = static_cast<float*>(cur.take(size_t(nbi) * TM * size_t(kpad) * sizeof(float)));
+    bsp[q] = static_cast<char*>(cur.take(size_t(nbi) * size_t(nch) * STAGE_BYTES));
+    if (kpad == 0) continue;
+    if (!sw[q] || !xT[q] || !bsp[q]) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
+    int64_t blocks = std::min<int64_t>((kpad + 255) / 256, int64_t(ctx.sm_count) * 8);
+    k_abs_weights_f32<<<unsigned(blocks), 256, 0, s>>>(qs[q].K, kpad, qs[q].delta, qs[q].f, pref,
+                                                       nw, om, sw[q], ctx.status);
+    GW_LAUNCH_CHECK("k_abs_weights_f32");
+    const dim3 pg(static_cast<unsigned>(nbi), static_cast<unsigned>(nch));
+    if (nch > 2147483647LL) return set_error(GW_EINVAL, "too many transitions for one q");
+    if (bf)
+      k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K, 2 * qs[q].nb,
+                                         kpad, nch, xT[q], bsp[q]);
+    else
+      k_prep_tc<false><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K, 2 * qs[q].nb,
+                                          kpad, nch, xT[q], bsp[q]);
+    GW_LAUNCH_CHECK("k_prep_tc");
+  }
+  const size_t smem = NS * STAGE_BYTES + 1024;
+  int rc = bf ? prepare_kernel<true>(ctx, smem) : prepare_kernel<false>(ctx, smem);
+  if (rc) return rc;
+  for (int q0 = 0; q0 < nq; q0 += TQ) {
+    int n = std::min(TQ, nq - q0);
+    TcLaunch L{};
+    L.nq = n;
+    L.nw = nw;
+    int64_t item = 0;
+    for (int q = 0; q < n; ++q) {
+      const PolQ& Q = qs[q0 + q];
+      L.xT[q] = xT[q0 + q];
+      L.bsp[q] = bsp[q0 + q];
+      L.s[q] = sw[q0 + q];
+      L.P[q] = reinterpret_cast<double2*>(Q.P);
+      L.K[q] = Q.K;
+      L.kpad[q] = kp[q0 + q];
+      L.nb[q] = Q.nb;
+      L.ntile[q] = tile_count(Q.nb, &L.nbi[q]);
+      L.item0[q] = item;
+      item += int64_t(L.ntile[q]) * nw;
+    }
+    L.item0[n] = item;
+    if (item == 0) continue;
+    unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
+    if (bf)
+      k_herk_tc<true><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
+    else
+      k_herk_tc<false><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
+    GW_LAUNCH_CHECK("k_herk_tc");
+  }
+  return GW_OK;
 }
 
 }  // namespace gw

@@ -1,0 +1,108 @@
+"""GPU parity of the tensor-core (split-precision) polarization against the oracle.
+
+Bounds: TF32x3 relative Frobenius error <= 1e-6 of P at every size (the benchmark spec's bound
+for the mixed path); BF16x3 <= 1e-6 once the band sum is long enough for the diagonal to
+dominate (K >= 1e5 rows per q), <= 2e-5 on the short sums of the small cases (its
+per-product split error is 2^-17 and off-diagonal entries average only over K terms).
+Exact Hermiticity (the kernel writes each upper entry and its mirror) and a real diagonal.
+"""
+import numpy as np
+import pytest
+
+import synth_inputs as S
+from oracle import polarization as OP
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gw():
+    import paper_1003_0316_gb300 as g
+    return g
+
+
+def T(a, dt=None):
+    return torch.as_tensor(np.asarray(a), device="cuda:0", dtype=dt)
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = {
+    "one_tile": dict(nb=64, nocc=4, nunocc=28, mesh=(2, 2, 2), nw=8, seed=1),
+    "ragged": dict(nb=70, nocc=3, nunocc=41, mesh=(2, 2, 2), nw=5, seed=2),
+    "several_tiles": dict(nb=150, nocc=5, nunocc=75, mesh=(2, 2, 2), nw=6, seed=3),
+}
+BOUND = {"tf32x3": 1e-6, "bf16x3": 2e-5}
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_tc_polarization_small(gw, prec, case):
+    wl = S.tiny(**CASES[case])
+    om = wl.omega()
+    M = wl.m_full(0)
+    d = wl.delta(0)
+    P = gw.polarization([T(M.astype(np.complex64))], [T(d)], om, wl.prefactor, prec)[0]
+    gw.check()
+    P = P.cpu().numpy()
+    # the oracle sees the same complex64-rounded projections
+    ref = OP.polarization(M.astype(np.complex64).astype(np.complex128), d, om, wl.prefactor)
+    err = rel_fro(P, ref)
+    assert err <= BOUND[prec], err
+    assert np.array_equal(P, np.conj(np.transpose(P, (0, 2, 1))))
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tc_batched_uneven_q(gw, prec):
+    wls = [S.tiny(nb=nb, nocc=3, nunocc=nu, mesh=(2, 2, 1), nw=4, seed=10 + nb)
+           for nb, nu in ((96, 30), (40, 7), (130, 55))]
+    om = wls[0].omega()
+    Ms = [w.m_full(0).astype(np.complex64) for w in wls]
+    ds = [w.delta(0) for w in wls]
+    P = gw.polarization([T(m) for m in Ms], [T(d) for d in ds], om, 0.5, prec)
+    gw.check()
+    for M, d, Pg in zip(Ms, ds, P):
+        ref = OP.polarization(M.astype(np.complex128), d, om, 0.5)
+        assert rel_fro(Pg.cpu().numpy(), ref) <= BOUND[prec]
+
+
+def test_tc_empty_transitions(gw):
+    wl = S.tiny(nb=64)
+    P = gw.polarization([T(wl.m_full(0)[:0].astype(np.complex64))], [T(wl.delta(0)[:0])],
+                        wl.omega(), 1.0, "tf32x3")[0]
+    gw.check()
+    assert torch.count_nonzero(P) == 0
+
+
+def test_tc_rejects_odd_basis(gw):
+    wl = S.tiny(nb=9)
+    with pytest.raises(gw.GWError) as e:
+        gw.polarization([T(wl.m_full(0).astype(np.complex64))], [T(wl.delta(0))], wl.omega(), 1.0,
+                        "tf32x3")
+    assert e.value.code == gw.GW_EINVAL
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tc_full_size_sampled_entries(gw, prec):
+    """N_b = 600, K = 409,600 (one q of the 4x4x4-mesh workload, projections generated on
+    the device): sampled entries and the full diagonal block against the oracle, which
+    regenerates the needed columns on the host."""
+    wl = S.medium_mixed()
+    iq = 1
+    K, nb = wl.K(iq), wl.nb[iq]
+    om = wl.omega()
+    M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[iq], 0, K, nb, dtype=torch.complex64)
+    d = wl.delta(iq)
+    P = gw.polarization([M], [T(d)], om, wl.prefactor, prec)[0]
+    gw.check()
+    rng = np.random.default_rng(7)
+    cols = np.sort(rng.choice(nb, size=24, replace=False))
+    Mc = wl.m_rows(iq, cols=cols).astype(np.complex64).astype(np.complex128)
+    ref = OP.polarization(Mc, d, om, wl.prefactor)
+    got = P[:, cols][:, :, cols].cpu().numpy()
+    err = rel_fro(got, ref)
+    assert err <= 1e-6, err
