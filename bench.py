@@ -1,0 +1,417 @@
+"""Throughput of the GW hot path on one GB300 (or N, one rank per GPU).
+
+One step = one pass of the whole path over the 4x4x4-mesh workload (8 transfer
+momenta q, N_MPB = 600, 16 occupied / 400 unoccupied bands -> K = 409,600
+transitions per q, 16 imaginary frequencies, 16 self-energy states):
+  transition weights + split-precision polarization P (Eq. polar_MB)
+  -> FP64 dielectric solve and W^c (Eqs. dielec_MB, screen_MB)
+  -> pair coefficients and frequency convolution of Sigma^c (Eq. SEc_AC)
+  -> multipole fit of every Sigma^c curve (Eq. modelf).
+The metric is algorithmic GFLOP/s of P + the Sigma^c contraction per step:
+  P: 4 K N_b (N_b + 1) per (q, omega); Sigma: 8 N_b^2 N_pair per (q, omega).
+Inputs are synthetic (seeded Philox draws, see synth_inputs) and generated on the
+device; with N ranks each rank runs its own copy of the workload (weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|bf16x3|fp64]
+    python bench.py --impl reference ...   # the CPU FP64 oracle on a bounded sample
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth_inputs as S  # noqa: E402
+
+METRIC = "P(iω)+Σ^c GFLOP/s and % of roofline, mixed vs FP64 on GB300 at ≤1e-6 rel err"
+
+
+def workload_flops(wl):
+    nw = wl.nw
+    fp = sum(4.0 * wl.K(i) * wl.nb[i] * (wl.nb[i] + 1) * nw for i in range(wl.nq))
+    npair = len(wl.sigma_states()) * (wl.nocc + wl.nunocc_max)
+    fs = sum(8.0 * wl.nb[i] ** 2 * npair * nw for i in range(wl.nq))
+    return fp, fs
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(wl, budget_s=20.0):
+    """Time the CPU oracle on a bounded sample: P for one q over the transitions of
+    the first k-points (all 16 frequencies), plus the Sigma^c pair coefficients of 256
+    pairs at one frequency; returns algorithmic GFLOP/s and the sample description."""
+    from oracle import polarization as OP
+    from oracle import screening as OS
+    from oracle import selfenergy as OE
+    om = wl.omega()
+    nb = wl.nb[0]
+    per_k = wl.nocc * wl.nunocc[0]
+    rows = per_k * 12                                # transitions of 12 of the 64 k-points
+    M = wl.m_rows(0, rows=np.arange(rows))
+    d = wl.delta(0)[:rows]
+    t0 = time.perf_counter()
+    P = OP.polarization(M, d, om, wl.prefactor)
+    t1 = time.perf_counter()
+    fl_p = 4.0 * rows * nb * (nb + 1) * len(om)
+    Wc = OS.screened_wc(P[0], wl.v(0))
+    Ms = wl.msig_rows(0, rows=np.arange(256))
+    t2 = time.perf_counter()
+    OE.pair_coefficients(Ms, Wc[None])
+    t3 = time.perf_counter()
+    fl_s = 8.0 * nb * nb * 256
+    secs = (t1 - t0) + (t3 - t2)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": (fl_p + fl_s) / secs / 1e9, "unit": "GFLOP/s", "cores": cores,
+            "kind": "oracle", "seconds": round(secs, 3),
+            "sample": f"P of q=0 over {rows} of {wl.K(0)} transitions (12 of 64 k-points), "
+                      f"all {len(om)} frequencies, N_b={nb}; Sigma pair coefficients of 256 "
+                      f"pairs at one frequency (numpy FP64, BLAS threads)"}
+
+
+def run_reference(args, rank, world):
+    wl = S.medium_mixed()
+    if rank != 0:
+        return
+    res = []
+    for _ in range(max(1, args.warmup)):
+        cpu_oracle_sample(wl)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        res.append(cpu_oracle_sample(wl))
+    el = time.perf_counter() - t
+    v = statistics.median([r["value"] for r in res])
+    cb = dict(res[0])
+    cb["value"] = v
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "sample": cb["sample"]},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+class Pipeline:
+    """Device-resident workload and one step of the hot path."""
+
+    def __init__(self, wl, precision, device):
+        import torch
+        import paper_1003_0316_gb300 as gw
+        self.gw, self.torch, self.wl, self.prec = gw, torch, wl, precision
+        self.dev = device
+        cdt = torch.complex128 if precision == "fp64" else torch.complex64
+        self.om = wl.omega()
+        self.om_out = wl.omega()
+        self.M = [gw.synth_projections(wl.seed, S.TID_M, wl.qs[i], 0, wl.K(i), wl.nb[i], dtype=cdt)
+                  for i in range(wl.nq)]
+        self.delta = [torch.as_tensor(wl.delta(i), device=device) for i in range(wl.nq)]
+        self.v = [torch.as_tensor(wl.v(i), device=device) for i in range(wl.nq)]
+        ps, eps = zip(*[wl.sigma_pairs(i) for i in range(wl.nq)])
+        self.pair_state = [torch.as_tensor(p, device=device, dtype=torch.int32) for p in ps]
+        self.eps = [torch.as_tensor(e, device=device) for e in eps]
+        npair = [len(p) for p in ps]
+        sig_cdt = torch.complex128 if precision == "fp64" else torch.complex64
+        self.Msig = [gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[i], 0, npair[i], wl.nb[i],
+                                          dtype=sig_cdt) for i in range(wl.nq)]
+        self.nsig = len(wl.sigma_states())
+        self.sign = torch.as_tensor(np.sign(wl.state_energies()), device=device)
+        nw = wl.nw
+        self.P = [torch.empty((nw, nb, nb), dtype=torch.complex128, device=device) for nb in wl.nb]
+        self.sigma = torch.empty((self.nsig, len(self.om_out)), dtype=torch.complex128, device=device)
+        Ks = [wl.K(i) for i in range(wl.nq)]
+        self.ws_p = torch.empty(gw.polarization_workspace(Ks, list(wl.nb), nw, precision),
+                                dtype=torch.uint8, device=device)
+        self.ws_w = torch.empty(gw.screened_w_workspace(list(wl.nb), nw), dtype=torch.uint8,
+                                device=device)
+        sprec = precision if self._sigma_mixed_ok() else "fp64"
+        self.sprec = sprec
+        if sprec == "fp64" and precision != "fp64":
+            self.Msig = [m.to(torch.complex128) for m in self.Msig]
+        self.ws_s = torch.empty(gw.sigma_workspace(npair, list(wl.nb), nw, sprec), dtype=torch.uint8,
+                                device=device)
+        self.ev_p0 = torch.cuda.Event(enable_timing=True)
+        self.ev_p1 = torch.cuda.Event(enable_timing=True)
+        self.p_ms = []
+
+    def _sigma_mixed_ok(self):
+        return getattr(self.gw, "SIGMA_MIXED", False)
+
+    def step(self, time_p=False):
+        gw = self.gw
+        if time_p:
+            self.ev_p0.record()
+        gw.polarization(self.M, self.delta, self.om, self.wl.prefactor, self.prec, out=self.P,
+                        ws=self.ws_p)
+        if time_p:
+            self.ev_p1.record()
+        gw.screened_w(self.P, self.v, out=self.P, ws=self.ws_w)
+        gw.sigma_c(list(self.wl.wq), self.Msig, self.pair_state, self.eps, self.P, self.om,
+                   self.om_out, self.nsig, precision=self.sprec, out=self.sigma, ws=self.ws_s)
+        return gw.continue_fit(self.sigma, self.om_out, npole=2, sign=self.sign)
+
+    def launches_per_step(self):
+        nq = self.wl.nq
+        if self.prec == "fp64":
+            p = 2
+        else:
+            p = 2 * nq + 1          # weights + prep per q, one HERK launch
+        w = (nq * self.wl.nw + 255) // 256
+        s = 1 + nq + 1             # pair coefficients, reductions, convolution
+        return p + w + s + 1       # + LM fit
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = S.medium_mixed()
+    pipe = Pipeline(wl, args.precision, dev)
+    gw = pipe.gw
+    fp, fs = workload_flops(wl)
+    step_flops = fp + fs
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        pipe.step()
+    gw.check()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    p_ms = []
+    e0.record()
+    for _ in range(args.steps):
+        pipe.step(time_p=True)
+        p_ms.append((pipe.ev_p0, pipe.ev_p1))
+        pipe.ev_p0 = torch.cuda.Event(enable_timing=True)
+        pipe.ev_p1 = torch.cuda.Event(enable_timing=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    p_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in p_ms)
+    barrier()
+    ck = clocks.stop()
+    gw.check()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API with host buffers: H2D of the step's inputs,
+    # the step, D2H of the fitted parameters and Sigma^c
+    e2e = e2e_measure(pipe, args, world)
+
+    # FP64 GPU path on a bounded sample (one q, 2 frequencies) for the mixed-vs-FP64 line
+    fp64 = fp64_sample(pipe) if args.precision != "fp64" else None
+    err = sampled_error(pipe)
+
+    if rank != 0:
+        return
+    pk, src = peaks()
+    ratio = 0.5 if args.precision == "tf32x3" else 1.0
+    peak_tf = pk["bf16_tflops"] * ratio if args.precision != "fp64" else 1.25
+    achieved = fp / wl.nq * wl.nq / (p_launch_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": step_flops * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"tf32x3": "tf32x3+f32acc(P,Sigma)/f64(W,fit)",
+                  "bf16x3": "bf16x3+f32acc(P,Sigma)/f64(W,fit)", "fp64": "f64"}[args.precision],
+        "data": "synthetic (seeded Philox draws shaped like the paper's systems)",
+        "config": {"workload": wl.name, "nq": wl.nq, "N_MPB": wl.nb[0], "K_per_q": wl.K(0),
+                   "n_omega": wl.nw, "n_sigma_states": pipe.nsig, "precision": args.precision,
+                   "sigma_precision": pipe.sprec, "l2": "inputs larger than L2 (M = "
+                   f"{sum(m.numel() * m.element_size() for m in pipe.M) / 1e9:.1f} GB)"},
+        "roofline": {"bound": "tensor" if args.precision != "fp64" else "alu",
+                     "kernel": "gw_polarization (split-precision HERK + per-q prep)",
+                     "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tf,
+                     "peak_source": (f"{src} bf16 x 0.5 (nominal tf32/bf16)" if args.precision == "tf32x3"
+                                     else f"{src} bf16" if args.precision == "bf16x3"
+                                     else "nominal FP64 1.25 TFLOP/s"),
+                     "traffic": None, "launch_ms": p_launch_ms},
+        "clocks": ck,
+        "e2e": e2e,
+        "gpu_launches": pipe.launches_per_step() * args.steps,
+        "fp64_gpu_sample": fp64,
+        "sampled_rel_err_P": err,
+    }
+    if world == 1:
+        line["cpu_baseline"] = cpu_oracle_sample(wl)
+    print(json.dumps(line), flush=True)
+
+
+def e2e_measure(pipe, args, world):
+    torch = pipe.torch
+    wl = pipe.wl
+    host_M = [m.cpu().pin_memory() for m in pipe.M]
+    host_Ms = [m.cpu().pin_memory() for m in pipe.Msig]
+    host_d = [d.cpu().pin_memory() for d in pipe.delta]
+    h2d = sum(t.numel() * t.element_size() for t in host_M + host_Ms + host_d)
+    steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    d2h = 0
+    for _ in range(steps):
+        for dst, src in zip(pipe.M, host_M):
+            dst.copy_(src, non_blocking=True)
+        for dst, src in zip(pipe.Msig, host_Ms):
+            dst.copy_(src, non_blocking=True)
+        for dst, src in zip(pipe.delta, host_d):
+            dst.copy_(src, non_blocking=True)
+        params, cost, iters, status = pipe.step()
+        out_p = params.to("cpu", non_blocking=False)
+        out_s = pipe.sigma.to("cpu", non_blocking=False)
+        d2h = out_p.numel() * out_p.element_size() + out_s.numel() * out_s.element_size()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    fp, fs = workload_flops(wl)
+    return {"value": (fp + fs) * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms}
+
+
+def fp64_sample(pipe):
+    torch = pipe.torch
+    gw = pipe.gw
+    wl = pipe.wl
+    K, nb = wl.K(0), wl.nb[0]
+    M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[0], 0, K, nb, dtype=torch.complex128)
+    om = pipe.om[:2]
+    gw.polarization([M], [pipe.delta[0]], om, wl.prefactor, "fp64")
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gw.polarization([M], [pipe.delta[0]], om, wl.prefactor, "fp64")
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fl = 4.0 * K * nb * (nb + 1) * len(om)
+    del M
+    return {"value": fl / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms": ms,
+            "sample": f"FP64 polarization of q=0 (K={K}, N_b={nb}) at 2 frequencies"}
+
+
+def sampled_error(pipe):
+    """Relative Frobenius error of sampled P entries (last step, q=1) against the oracle,
+    which regenerates the needed projection columns on the host."""
+    from oracle import polarization as OP
+    gw = pipe.gw
+    wl = pipe.wl
+    iq = 1
+    cols = np.arange(0, wl.nb[iq], 41)
+    gw.polarization(pipe.M, pipe.delta, pipe.om, wl.prefactor, pipe.prec, out=pipe.P, ws=pipe.ws_p)
+    got = pipe.P[iq][:, cols][:, :, cols].cpu().numpy()
+    Mc = wl.m_rows(iq, cols=cols)
+    if pipe.prec != "fp64":
+        Mc = Mc.astype(np.complex64).astype(np.complex128)
+    ref = OP.polarization(Mc, wl.delta(iq), pipe.om, wl.prefactor)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp64"])
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
