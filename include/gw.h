@@ -123,6 +123,29 @@ int gw_screened_w(int nq, const int* nb_host, int nw, const double* const* v_dev
                   const double* const* P_dev, double* const* Wc_dev,
                   void* ws_dev, size_t ws_bytes, gw_stream_t stream);
 
+/* Variant of gw_screened_w that allocates nothing, for callers that cannot allocate
+ * device memory when they call the library: for example a host application that has
+ * already handed all device memory to its own pool, or a latency-critical loop in which a
+ * cudaMalloc (which may synchronise the device and can fail under memory pressure) is
+ * not acceptable. The paper has no counterpart to this entry point.
+ *
+ * One q at a time: v_dev [nb] double, P_dev [nw][nb][nb] complex128 (Hermitian NSD),
+ * Wc_dev [nw][nb][nb] complex128 output (may alias P_dev). The scratch lives in a
+ * library-owned static device array of GW_NOALLOC_SCRATCH_BYTES on every device that
+ * loads the library (held until the process exits). Each (q, frequency) system needs
+ * 16 * nb * (nb + 32) bytes; the nw systems are processed in batches that fit, one after
+ * another on `stream`. nb whose single system does not fit (nb > 1008) gives GW_EINVAL;
+ * nothing is allocated or freed.
+ *
+ * The first call on a device looks up the device address of the array (with that device
+ * current); make that first call before any stream capture. All calls share the array and
+ * it keeps the last call's contents (nothing in it needs to start at zero); calls that
+ * overlap on the GPU (other streams, other host threads) race on it and must be ordered by
+ * the caller. Errors are reported as for gw_screened_w. */
+#define GW_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int gw_screened_w_noalloc(int nb, int nw, const double* v_dev, const double* P_dev,
+                          double* Wc_dev, gw_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * a5. Pair coefficients of the self-energy (band-space factor of Eq. SEc_AC):
  *   c[j][p] = Re( sum_{mu,nu} conj(m_{p,mu}) W^c_{mu nu}(q, i omega_j) m_{p,nu} ),

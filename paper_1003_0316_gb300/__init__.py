@@ -52,6 +52,7 @@ _sig("gw_polarization", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), 
      _i32, _P(_f64), _P(_vp), _i32, _vp, _sz, _vp)
 _sig("gw_screened_w_workspace", _sz, _i32, _P(_i32), _i32)
 _sig("gw_screened_w", _i32, _i32, _P(_i32), _i32, _P(_vp), _P(_vp), _P(_vp), _vp, _sz, _vp)
+_sig("gw_screened_w_noalloc", _i32, _i32, _i32, _vp, _vp, _vp, _vp)
 _sig("gw_sigma_pair_coeffs", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _i32, _P(_vp),
      _P(_vp), _i32, _vp, _sz, _vp)
 _sig("gw_sigma_convolve", _i32, _i32, _P(_f64), _P(_i64), _i32, _P(_f64), _P(_vp), _P(_vp),
@@ -183,6 +184,20 @@ def screened_w(Ps, vs, out=None, ws=None):
         wsb, wsp, wsn = ws, _vp(ws.data_ptr()), ws.numel()
     _raise(_lib.gw_screened_w(nq, _arr(_i32, nbs), nw, _ptrs(vs), _ptrs(Ps), _ptrs(out), wsp, wsn,
                               _stream()))
+    return out
+
+
+NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
+
+
+def screened_w_noalloc(P, v, out=None):
+    """W^c for one q without any device allocation by the library (static scratch; see
+    gw_screened_w_noalloc in include/gw.h). Allocates `out` here only if not given."""
+    nw, nb = P.shape[0], P.shape[1]
+    if out is None:
+        out = torch.empty_like(P)
+    _raise(_lib.gw_screened_w_noalloc(nb, nw, v.data_ptr(), P.data_ptr(), out.data_ptr(),
+                                      _stream()))
     return out
 
 

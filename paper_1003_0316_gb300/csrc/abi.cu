@@ -206,6 +206,17 @@ int gw_screened_w(int nq, const int* nb_host, int nw, const double* const* v_dev
   return dielectric_wc(nq, nb_host, nw, v_dev, P_dev, Wc_dev, ws_dev, ws_bytes, stream, ctx);
 }
 
+int gw_screened_w_noalloc(int nb, int nw, const double* v_dev, const double* P_dev,
+                          double* Wc_dev, gw_stream_t stream) {
+  if (nb < 1 || nb > 8192) return set_error(GW_EINVAL, "nb=%d outside [1, 8192]", nb);
+  if (nw < 1 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [1, %d]", nw, GW_MAX_NW);
+  if (!v_dev || !P_dev || !Wc_dev) return set_error(GW_EINVAL, "NULL v_dev, P_dev or Wc_dev");
+  DeviceCtx ctx;
+  int rc = device_ctx(&ctx);
+  if (rc) return rc;
+  return dielectric_wc_noalloc(nb, nw, v_dev, P_dev, Wc_dev, stream, ctx);
+}
+
 static int validate_pairs(int nq, const int64_t* npair, const int* nb, int precision, int m_dtype) {
   if (nq < 1 || npair == nullptr || nb == nullptr)
     return set_error(GW_EINVAL, "nq < 1 or NULL npair_host/nb_host");

@@ -11,6 +11,7 @@
 // about 4 N^3 real flops per system (N^3/6 complex multiply-adds each).
 #include <vector>
 #include <algorithm>
+#include <mutex>
 
 #include "gw_internal.cuh"
 
@@ -357,6 +358,63 @@ int dielectric_wc(int nq, const int* nb, int nw, const double* const* v, const d
     for (size_t i = 0; i < nb_; ++i) batch.s[i] = sys[b0 + i];
     k_dielectric<<<unsigned(nb_), DTHREADS, smem, s>>>(batch, ctx.status);
     GW_LAUNCH_CHECK("k_dielectric");
+  }
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------- no-alloc variant
+// Scratch for callers that cannot allocate: a static device array (one per device that
+// loads the library). Host code only ever uses the device address looked up below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GW_NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mu;
+static char* g_noalloc_ptr[64];
+
+static int noalloc_scratch(const DeviceCtx& ctx, char** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[ctx.device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[ctx.device] = static_cast<char*>(p);
+  }
+  *out = g_noalloc_ptr[ctx.device];
+  return GW_OK;
+}
+
+int dielectric_wc_noalloc(int nb, int nw, const double* v, const double* P, double* Wc,
+                          cudaStream_t s, const DeviceCtx& ctx) {
+  const size_t n = size_t(nb);
+  const size_t per = ws_round((n * n + n * DB) * sizeof(double2));
+  if (per > GW_NOALLOC_SCRATCH_BYTES)
+    return set_error(GW_EINVAL, "nb=%d needs %zu bytes of scratch per system, more than the "
+                     "%u-byte static scratch of the no-alloc entry point", nb, per,
+                     GW_NOALLOC_SCRATCH_BYTES);
+  char* base = nullptr;
+  int rc = noalloc_scratch(ctx, &base);
+  if (rc) return rc;
+  const size_t fit = std::min<size_t>(GW_NOALLOC_SCRATCH_BYTES / per, DMAXSYS);
+  const size_t smem = 3 * DB * DLD * sizeof(double2);
+  static bool attr_set[64] = {};
+  if (!attr_set[ctx.device]) {
+    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem)));
+    attr_set[ctx.device] = true;
+  }
+  for (int j0 = 0; j0 < nw; j0 += int(fit)) {
+    const int cnt = std::min<int>(int(fit), nw - j0);
+    DieBatch batch;
+    for (int i = 0; i < cnt; ++i) {
+      DieSys& d = batch.s[i];
+      const int j = j0 + i;
+      d.P = reinterpret_cast<const double2*>(P) + size_t(j) * n * n;
+      d.Wc = reinterpret_cast<double2*>(Wc) + size_t(j) * n * n;
+      d.v = v;
+      d.E = reinterpret_cast<double2*>(base + size_t(i) * per);
+      d.T = d.E + n * n;
+      d.n = nb;
+    }
+    k_dielectric<<<unsigned(cnt), DTHREADS, smem, s>>>(batch, ctx.status);
+    GW_LAUNCH_CHECK("k_dielectric (no-alloc)");
   }
   return GW_OK;
 }

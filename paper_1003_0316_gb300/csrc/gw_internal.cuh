@@ -116,6 +116,8 @@ int launch_lm(int ncurve, int nw, const OmegaArr& om, const double* sigma, const
 int mlp_forward(int n, const double* sigma, const float* w, float* out, cudaStream_t s);
 int mlp_train_step(int n, const OmegaArr& om, const double* sigma, float* w, float* grad, float* m,
                    float* v, float lr, int step, float* loss, cudaStream_t s);
+int dielectric_wc_noalloc(int nb, int nw, const double* v, const double* P, double* Wc,
+                          cudaStream_t s, const DeviceCtx& ctx);
 constexpr int MLP_NIN = 48, MLP_NH = 128, MLP_NOUT = 8;
 constexpr int MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NOUT * MLP_NH + MLP_NOUT;
 }  // namespace gw
