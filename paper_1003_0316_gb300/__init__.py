@@ -24,6 +24,7 @@ GW_FP64, GW_TF32X3, GW_BF16X3 = 0, 1, 2
 GW_FIT_PLAIN, GW_FIT_MLP = 0, 1
 PRECISIONS = {"fp64": GW_FP64, "tf32x3": GW_TF32X3, "bf16x3": GW_BF16X3}
 MAX_NW = 64
+SIGMA_MIXED = True   # the pair coefficients have tensor-core (split precision) paths
 
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int

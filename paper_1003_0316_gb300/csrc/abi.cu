@@ -241,9 +241,12 @@ int gw_sigma_pair_coeffs(int nq, const int64_t* npair_host, const int* nb_host,
   if (rc) return rc;
   if (nw < 1 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [1, %d]", nw, GW_MAX_NW);
   if (!Msig_dev || !Wc_dev || !c_dev) return set_error(GW_EINVAL, "NULL pointer array");
-  for (int q = 0; q < nq; ++q)
+  for (int q = 0; q < nq; ++q) {
     if (npair_host[q] > 0 && (!Msig_dev[q] || !Wc_dev[q] || !c_dev[q]))
       return set_error(GW_EINVAL, "NULL pointer for q=%d", q);
+    if (precision != GW_FP64 && (reinterpret_cast<uintptr_t>(Msig_dev[q]) & 15u))
+      return set_error(GW_EINVAL, "Msig_dev[%d] not 16-byte aligned", q);
+  }
   size_t need = paircoef_workspace(nq, npair_host, nb_host, nw, precision);
   if ((rc = check_ws(ws_dev, ws_bytes, need))) return rc;
   DeviceCtx ctx;

@@ -73,17 +73,22 @@ struct TcLaunch {
   const float* xT[TQ];      // [ncolp][kpad] column-major copy of the FP32 view of M (zero padded)
   const char* bsp[TQ];      // [nbi][nch] pre-split B tiles: 8 KB hi + 8 KB lo, swizzled
   const float* s[TQ];       // [nw][kpad] |w_tj| in FP32 (zero padded)
-  double2* P[TQ];
+  double2* P[TQ];           // polarization output (Hermitian store)
+  double* cq[TQ];           // quadratic-form output c[nw][nrow] (accumulated with atomics)
+  int64_t bsp_jstride[TQ];  // bytes between the B tiles of consecutive frequencies (0: shared)
+  int64_t nrow[TQ];         // valid A rows (quadratic form)
   int64_t K[TQ];
   int64_t kpad[TQ];
   int nb[TQ];
   int nbi[TQ];
+  int nbj[TQ];
   int ntile[TQ];
   int64_t item0[TQ + 1];
   int nq;
   int nw;
 };
 
+template <bool QF>
 __device__ __forceinline__ void decode_item(const TcLaunch& L, int64_t item, int& q, int& j,
                                             int& bi, int& bj) {
   q = 0;
@@ -91,8 +96,11 @@ __device__ __forceinline__ void decode_item(const TcLaunch& L, int64_t item, int
   int64_t loc = item - L.item0[q];
   int u = int(loc % L.ntile[q]);
   j = int(loc / L.ntile[q]);
-  const int nbi = L.nbi[q];
-  (void)nbi;
+  if (QF) {             // full rectangular grid; consecutive items share the B column block
+    bi = u % L.nbi[q];
+    bj = u / L.nbi[q];
+    return;
+  }
   bj = 0;
   while (u > bj) {      // upper tiles bi <= bj, column by column
     u -= bj + 1;
@@ -147,7 +155,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-template <bool BF16>
+template <bool BF16, bool QF>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_herk_tc(const __grid_constant__ TcLaunch L, double* __restrict__ acc64, unsigned* status) {
   constexpr int CH = BF16 ? 32 : 16;          // transitions per chunk (64 bytes of K)
@@ -195,11 +203,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t g = 0;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
       int q, j, bi, bj;
-      decode_item(L, item, q, j, bi, bj);
+      decode_item<QF>(L, item, q, j, bi, bj);
       const int64_t K = L.K[q];
       const int64_t kpad = L.kpad[q];
       const float4* __restrict__ xc = reinterpret_cast<const float4*>(L.xT[q] + size_t(bi * TM + m) * kpad);
-      const float4* __restrict__ sj = reinterpret_cast<const float4*>(L.s[q] + size_t(j) * kpad);
+      // quadratic form: no weights (the A operand is the pair projections themselves)
+      const float4* __restrict__ sj =
+          QF ? nullptr : reinterpret_cast<const float4*>(L.s[q] + size_t(j) * kpad);
       const int64_t nch = (K + CH - 1) / CH;
       const int64_t nunit = nch * UPC;
       float4 xa[4], sa[4], xb[4], sb[4];
@@ -207,14 +217,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           xa[e] = __ldg(xc + e);
-          sa[e] = __ldg(sj + e);
+          sa[e] = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(sj + e);
         }
       }
       if (nunit > 1) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           xb[e] = __ldg(xc + 4 + e);
-          sb[e] = __ldg(sj + 4 + e);
+          sb[e] = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(sj + 4 + e);
         }
       }
       bool stop = false;
@@ -228,7 +238,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             xn[e] = __ldg(xc + (u + 2) * 4 + e);
-            sn[e] = __ldg(sj + (u + 2) * 4 + e);
+            sn[e] = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(sj + (u + 2) * 4 + e);
           }
         }
         if (uc == 0 && !warp_wait(&empty_bar[st], ((gg / NS) & 1) ^ 1, &s_abort, status)) {
@@ -282,9 +292,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         int q, j, bi, bj;
-        decode_item(L, item, q, j, bi, bj);
+        decode_item<QF>(L, item, q, j, bi, bj);
         const int64_t nch = (L.K[q] + CH - 1) / CH;
-        const char* src = L.bsp[q] + size_t(bj) * nch * STAGE_BYTES;
+        const char* src = L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * nch * STAGE_BYTES;
         for (int64_t c = 0; c < nch; ++c, ++g) {
           const int st = g % NS;
           if (!tc::mbar_wait(&empty_bar[st], ((g / NS) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
@@ -310,7 +320,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         int q, j, bi, bj;
-        decode_item(L, item, q, j, bi, bj);
+        decode_item<QF>(L, item, q, j, bi, bj);
         const int64_t nch = (L.K[q] + CH - 1) / CH;
         for (int64_t c = 0; c < nch; ++c, ++g) {
           const int st = g % NS;
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t gp = 0;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
       int q, j, bi, bj;
-      decode_item(L, item, q, j, bi, bj);
+      decode_item<QF>(L, item, q, j, bi, bj);
       const int64_t nch = (L.K[q] + CH - 1) / CH;
       const int64_t nper = (nch + CPD - 1) / CPD;
       const int nb = L.nb[q];
@@ -407,27 +417,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       if (stop) break;
-      // final fold, then the complex combination of rows (2I, 2I+1) held by lanes (2l, 2l+1)
+      // final fold
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) atomicAdd(acc + size_t(i) * TM, double(sum[i]));
       __threadfence();
-      const int R = bi * TM + r;
-      const int I = R >> 1;
-      const bool odd = R & 1;
-      double2* P = L.P[q] + size_t(j) * nb * nb;
+      if (QF) {
+        // c_p += sum_c X[p][c] Y[p][c] over this tile's columns (X = the A rows themselves)
+        const int64_t p = int64_t(bi) * TM + r;
+        const float* xr = L.xT[q] + size_t(p) * L.kpad[q] + size_t(bj) * TN + c0;
+        double part = 0.0;
+#pragma unroll 8
+        for (int i = 0; i < EPI_COLS; ++i) part = fma(double(__ldg(xr + i)), acc[size_t(i) * TM], part);
+        if (p < L.nrow[q]) atomicAdd(L.cq[q] + size_t(j) * L.nrow[q] + p, part);
+      } else {
+        // complex combination of rows (2I, 2I+1) held by lanes (2l, 2l+1)
+        const int R = bi * TM + r;
+        const int I = R >> 1;
+        const bool odd = R & 1;
+        double2* P = L.P[q] + size_t(j) * nb * nb;
 #pragma unroll 4
-      for (int jj = 0; jj < EPI_COLS / 2; ++jj) {
-        double e0 = acc[size_t(2 * jj) * TM];
-        double e1 = acc[size_t(2 * jj + 1) * TM];
-        double o0 = __shfl_xor_sync(0xffffffffu, e0, 1);
-        double o1 = __shfl_xor_sync(0xffffffffu, e1, 1);
-        if (!odd) {
-          const int J = (bj * TN + c0) / 2 + jj;
-          if (I < nb && J < nb && I <= J) {
-            double re = -(e0 + o1);
-            double im = (I == J) ? 0.0 : -(o0 - e1);
-            P[size_t(I) * nb + J] = make_double2(re, im);
-            if (I != J) P[size_t(J) * nb + I] = make_double2(re, -im);
+        for (int jj = 0; jj < EPI_COLS / 2; ++jj) {
+          double e0 = acc[size_t(2 * jj) * TM];
+          double e1 = acc[size_t(2 * jj + 1) * TM];
+          double o0 = __shfl_xor_sync(0xffffffffu, e0, 1);
+          double o1 = __shfl_xor_sync(0xffffffffu, e1, 1);
+          if (!odd) {
+            const int J = (bj * TN + c0) / 2 + jj;
+            if (I < nb && J < nb && I <= J) {
+              double re = -(e0 + o1);
+              double im = (I == J) ? 0.0 : -(o0 - e1);
+              P[size_t(I) * nb + J] = make_double2(re, im);
+              if (I != J) P[size_t(J) * nb + I] = make_double2(re, -im);
+            }
           }
         }
       }
@@ -474,6 +495,57 @@ __global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, in
   for (int kc = 0; kc < 4; ++kc) {
     uint32_t hw[4], lw[4];
     split_words<BF16>(v + kc * EPC, hw, lw, 4);
+    const uint32_t off = sw64_off(n, kc);
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(hi + B_TILE + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+// Quadratic form c_p = x_p^T R x_p (pair coefficients of the self-energy): the A operand is
+// the real view X of the pair projections, row-padded to 128 and column-padded to kpad.
+__global__ void k_prep_xpad(const float* __restrict__ x, int64_t nrow, int ncol, int64_t nrowp,
+                            int64_t kpad, float* __restrict__ xp) {
+  const int64_t n4 = nrowp * (kpad / 4);
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n4;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = e / (kpad / 4);
+    const int64_t c = (e % (kpad / 4)) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < nrow && c < ncol) v = __ldg(reinterpret_cast<const float4*>(x + row * ncol + c));
+    reinterpret_cast<float4*>(xp)[e] = v;
+  }
+}
+
+// B operand of the quadratic form for one frequency: the real symmetric form R of the
+// Hermitian W^c (R[2I+a][2J+b] = Re W_IJ for a = b, -Im W_IJ for (a,b) = (0,1), Im W_IJ for
+// (1,0)), split and swizzled like the polarization's B tiles, [c block][k chunk].
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W, int nb,
+                                                   int64_t nch, char* __restrict__ bsp) {
+  constexpr int CH = BF16 ? 32 : 16;
+  constexpr int EPC = CH / 4;
+  const int cb = blockIdx.x;
+  const int64_t ch = blockIdx.y;
+  const int n = threadIdx.x;
+  const int c = cb * TN + n;
+  const int J = c >> 1, b = c & 1;
+  char* hi = bsp + (size_t(cb) * nch + ch) * STAGE_BYTES;
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) {
+    float v[EPC];
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) {
+      const int64_t k = ch * CH + kc * EPC + e;
+      const int I = int(k >> 1), a = int(k & 1);
+      float r = 0.0f;
+      if (c < 2 * nb && k < 2 * nb) {
+        const double2 w = W[size_t(I) * nb + J];
+        r = float(a == b ? w.x : (a == 0 ? -w.y : w.y));
+      }
+      v[e] = r;
+    }
+    uint32_t hw[4], lw[4];
+    split_words<BF16>(v, hw, lw, 4);
     const uint32_t off = sw64_off(n, kc);
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     *reinterpret_cast<uint4*>(hi + B_TILE + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -531,12 +603,26 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
   return b;
 }
 
-template <bool BF16>
+template <bool BF16, bool QF>
 static int prepare_kernel(const DeviceCtx& ctx, size_t smem) {
   static bool done[64] = {};
   if (done[ctx.device]) return GW_OK;
-  GW_CUDA_TRY(cudaFuncSetAttribute(k_herk_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  GW_CUDA_TRY(cudaFuncSetAttribute(k_herk_tc<BF16, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(smem)));
   done[ctx.device] = true;
+  return GW_OK;
+}
+
+template <bool QF>
+static int launch_tc(const TcLaunch& L, bool bf, unsigned grid, size_t smem, double* acc64,
+                     cudaStream_t s, const DeviceCtx& ctx) {
+  int rc = bf ? prepare_kernel<true, QF>(ctx, smem) : prepare_kernel<false, QF>(ctx, smem);
+  if (rc) return rc;
+  if (bf)
+    k_herk_tc<true, QF><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
+  else
+    k_herk_tc<false, QF><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
+  GW_LAUNCH_CHECK("k_herk_tc");
   return GW_OK;
 }
 
@@ -577,8 +663,6 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     GW_LAUNCH_CHECK("k_prep_tc");
   }
   const size_t smem = NS * STAGE_BYTES + 1024;
-  int rc = bf ? prepare_kernel<true>(ctx, smem) : prepare_kernel<false>(ctx, smem);
-  if (rc) return rc;
   for (int q0 = 0; q0 < nq; q0 += TQ) {
     int n = std::min(TQ, nq - q0);
     TcLaunch L{};
@@ -595,17 +679,116 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
       L.kpad[q] = kp[q0 + q];
       L.nb[q] = Q.nb;
       L.ntile[q] = tile_count(Q.nb, &L.nbi[q]);
+      L.nbj[q] = L.nbi[q];
       L.item0[q] = item;
       item += int64_t(L.ntile[q]) * nw;
     }
     L.item0[n] = item;
     if (item == 0) continue;
     unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
-    if (bf)
-      k_herk_tc<true><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
-    else
-      k_herk_tc<false><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
-    GW_LAUNCH_CHECK("k_herk_tc");
+    int rc = launch_tc<false>(L, bf, grid, smem, acc64, s, ctx);
+    if (rc) return rc;
+  }
+  return GW_OK;
+}
+
+// ------------------------------------------------------------ pair coefficients
+static void quad_sizes(int64_t npair, int nb, int precision, int64_t* nch, int64_t* kpad,
+                       int64_t* nrowp, int* nbi, int* nbj) {
+  const int64_t ch = chunk_rows(precision);
+  *nch = (2 * int64_t(nb) + ch - 1) / ch;
+  *nbj = (2 * nb + TN - 1) / TN;
+  *kpad = int64_t(*nbj) * TN;                 // multiple of 128 (>= every chunk end)
+  *nbi = int((npair + TM - 1) / TM);
+  *nrowp = int64_t(*nbi) * TM;
+}
+
+size_t quad_tc_workspace(int nq, const int64_t* npair, const int* nb, int nw, int precision) {
+  int sm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  size_t b = ws_round(size_t(sm) * TN * TM * sizeof(double));
+  for (int q = 0; q < nq; ++q) {
+    int64_t nch, kpad, nrowp;
+    int nbi, nbj;
+    quad_sizes(npair[q], nb[q], precision, &nch, &kpad, &nrowp, &nbi, &nbj);
+    b += ws_round(size_t(nrowp) * size_t(kpad) * sizeof(float));
+    b += ws_round(size_t(nw) * size_t(nbj) * size_t(nch) * STAGE_BYTES);
+  }
+  return b;
+}
+
+int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig, int nw,
+            const double* const* Wc, double* const* c, int precision, void* ws, size_t ws_bytes,
+            cudaStream_t s, const DeviceCtx& ctx) {
+  for (int q = 0; q < nq; ++q)
+    if (nb[q] & 1)
+      return set_error(GW_EINVAL, "tensor-core path needs an even N_b (q=%d has %d)", q, nb[q]);
+  const bool bf = precision == GW_BF16X3;
+  WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
+  double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
+  if (!acc64) return set_error(GW_EWORKSPACE, "internal: tensor-core workspace too small");
+  std::vector<float*> xp(nq);
+  std::vector<char*> bsp(nq);
+  std::vector<int64_t> kp(nq), nchv(nq);
+  std::vector<int> nbiv(nq), nbjv(nq);
+  for (int q = 0; q < nq; ++q) {
+    int64_t nch, kpad, nrowp;
+    int nbi, nbj;
+    quad_sizes(npair[q], nb[q], precision, &nch, &kpad, &nrowp, &nbi, &nbj);
+    kp[q] = kpad;
+    nchv[q] = nch;
+    nbiv[q] = nbi;
+    nbjv[q] = nbj;
+    xp[q] = static_cast<float*>(cur.take(size_t(nrowp) * size_t(kpad) * sizeof(float)));
+    bsp[q] = static_cast<char*>(cur.take(size_t(nw) * size_t(nbj) * size_t(nch) * STAGE_BYTES));
+    if (npair[q] == 0) continue;
+    if (!xp[q] || !bsp[q]) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
+    GW_CUDA_TRY(cudaMemsetAsync(c[q], 0, sizeof(double) * size_t(nw) * size_t(npair[q]), s));
+    const int64_t n4 = nrowp * (kpad / 4);
+    k_prep_xpad<<<unsigned(std::min<int64_t>((n4 + 255) / 256, int64_t(ctx.sm_count) * 16)), 256, 0,
+                  s>>>(static_cast<const float*>(Msig[q]), npair[q], 2 * nb[q], nrowp, kpad, xp[q]);
+    GW_LAUNCH_CHECK("k_prep_xpad");
+    const dim3 pg(static_cast<unsigned>(nbj), static_cast<unsigned>(nch));
+    for (int j = 0; j < nw; ++j) {
+      const double2* W = reinterpret_cast<const double2*>(Wc[q]) + size_t(j) * nb[q] * nb[q];
+      char* dst = bsp[q] + size_t(j) * nbj * nch * STAGE_BYTES;
+      if (bf)
+        k_prep_quad<true><<<pg, 128, 0, s>>>(W, nb[q], nch, dst);
+      else
+        k_prep_quad<false><<<pg, 128, 0, s>>>(W, nb[q], nch, dst);
+      GW_LAUNCH_CHECK("k_prep_quad");
+    }
+  }
+  const size_t smem = NS * STAGE_BYTES + 1024;
+  for (int q0 = 0; q0 < nq; q0 += TQ) {
+    int n = std::min(TQ, nq - q0);
+    TcLaunch L{};
+    L.nq = n;
+    L.nw = nw;
+    int64_t item = 0;
+    for (int q = 0; q < n; ++q) {
+      const int Q = q0 + q;
+      L.xT[q] = xp[Q];
+      L.bsp[q] = bsp[Q];
+      L.s[q] = nullptr;
+      L.cq[q] = c[Q];
+      L.bsp_jstride[q] = int64_t(nbjv[Q]) * nchv[Q] * STAGE_BYTES;
+      L.nrow[q] = npair[Q];
+      L.K[q] = npair[Q] > 0 ? 2 * int64_t(nb[Q]) : 0;
+      L.kpad[q] = kp[Q];
+      L.nb[q] = nb[Q];
+      L.nbi[q] = nbiv[Q];
+      L.nbj[q] = nbjv[Q];
+      L.ntile[q] = npair[Q] > 0 ? nbiv[Q] * nbjv[Q] : 0;
+      L.item0[q] = item;
+      item += int64_t(L.ntile[q]) * nw;
+    }
+    L.item0[n] = item;
+    if (item == 0) continue;
+    unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
+    int rc = launch_tc<true>(L, bf, grid, smem, acc64, s, ctx);
+    if (rc) return rc;
   }
   return GW_OK;
 }

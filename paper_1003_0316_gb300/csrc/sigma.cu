@@ -130,6 +130,7 @@ __global__ void k_paircoef_reduce(PairLaunch L, const double* __restrict__ part,
 }
 
 size_t paircoef_workspace(int nq, const int64_t* npair, const int* nb, int nw, int precision) {
+  if (precision != GW_FP64) return quad_tc_workspace(nq, npair, nb, nw, precision);
   size_t b = 0;
   for (int q = 0; q < nq; ++q) {
     int it = (nb[q] + ST - 1) / ST;
@@ -141,7 +142,8 @@ size_t paircoef_workspace(int nq, const int64_t* npair, const int* nb, int nw, i
 int paircoef(int nq, const int64_t* npair, const int* nb, const void* const* Msig, int dtype,
              int nw, const double* const* Wc, double* const* c, int precision, void* ws,
              size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
-  if (precision != GW_FP64) return set_error(GW_EUNSUPPORTED, "pair coefficients: precision %d not built", precision);
+  if (precision != GW_FP64)
+    return quad_tc(nq, npair, nb, Msig, nw, Wc, c, precision, ws, ws_bytes, s, ctx);
   double* part = static_cast<double*>(ws);
   for (int q0 = 0; q0 < nq; q0 += SMAXQ) {
     int n = std::min(SMAXQ, nq - q0);

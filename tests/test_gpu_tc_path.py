@@ -106,3 +106,53 @@ def test_tc_full_size_sampled_entries(gw, prec):
     got = P[:, cols][:, :, cols].cpu().numpy()
     err = rel_fro(got, ref)
     assert err <= 1e-6, err
+
+
+# ---------------------------------------------------- Sigma pair coefficients ---
+from oracle import screening as OS  # noqa: E402
+from oracle import selfenergy as OE  # noqa: E402
+
+PAIR_BOUND = {"tf32x3": 2e-6, "bf16x3": 2e-5}
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("nb", [70, 150])
+def test_tc_pair_coefficients(gw, prec, nb):
+    """c[j, p] = Re m_p^H W^c_j m_p on tensor cores against the oracle (same complex64
+    projections); ragged pair and basis tiles; max error relative to max |c|."""
+    wl = S.tiny(nb=nb, nocc=3, nunocc=20, mesh=(2, 1, 2), nw=5, seed=nb + 1)
+    om = wl.omega()
+    Wo = OS.screened_wc_all(OP.polarization(wl.m_full(0), wl.delta(0), om, wl.prefactor), wl.v(0))
+    Ms = wl.msig_rows(0).astype(np.complex64)
+    c = gw.sigma_pair_coeffs([T(Ms)], [T(Wo)], precision=prec)[0]
+    gw.check()
+    c = c.cpu().numpy()
+    ref = OE.pair_coefficients(Ms.astype(np.complex128), Wo)
+    err = float(np.abs(c - ref).max() / np.abs(ref).max())
+    assert err <= PAIR_BOUND[prec], err
+
+
+@pytest.mark.parametrize("prec", ["tf32x3"])
+def test_tc_sigma_end_to_end_small(gw, prec):
+    """Sigma^c through the split-precision P and pair coefficients against the all-FP64
+    oracle chain: max |dSigma| <= 1e-5 * max(1 Ha, max |Sigma|). The mixed-path bound of
+    1e-5 Ha is meant for self-energies of physical size (~1 Ha); the synthetic projections
+    are not normalised like real ones and give |Sigma| ~ 10^3 Ha, so it is applied relative
+    to the largest entry there."""
+    wl = S.tiny(nb=64, nocc=4, nunocc=28, mesh=(2, 2, 2), nw=8, seed=9)
+    om = wl.omega()
+    M = wl.m_full(0).astype(np.complex64)
+    ps, eps = wl.sigma_pairs(0)
+    Ms = wl.msig_rows(0).astype(np.complex64)
+    nsig = len(wl.sigma_states())
+    P = gw.polarization([T(M)], [T(wl.delta(0))], om, wl.prefactor, prec)
+    W = gw.screened_w(P, [T(wl.v(0))])
+    sig = gw.sigma_c(list(wl.wq), [T(Ms)], [T(ps, torch.int32)], [T(eps)], W, om, om, nsig,
+                     precision=prec)
+    gw.check()
+    Po = OP.polarization(M.astype(np.complex128), wl.delta(0), om, wl.prefactor)
+    Wo = OS.screened_wc_all(Po, wl.v(0))
+    co = OE.pair_coefficients(Ms.astype(np.complex128), Wo)
+    so = OE.sigma_c(om, om, list(wl.wq), [co], [ps], [eps], nsig)
+    bound = 1e-5 * max(1.0, float(np.abs(so).max()))
+    assert float(np.abs(sig.cpu().numpy() - so).max()) <= bound
