@@ -50,22 +50,22 @@ namespace {
 constexpr int TM = 128;          // real Gram rows per tile (A operand, in TMEM)
 constexpr int TN = 128;          // real Gram columns per tile (B operand, in shared memory)
 constexpr int SWB = 64;          // bytes of K per B row per chunk (64-byte swizzle)
-constexpr int NS = 3;            // B stages in shared memory = A slots in TMEM
+constexpr int NSB = 8;           // B stages in shared memory
+constexpr int NSA = 4;           // A slots in TMEM
 constexpr int B_TILE = TN * SWB;                 // 8 KB
 constexpr int STAGE_BYTES = 2 * B_TILE;          // hi + lo
+constexpr int STAGE_STRIDE = STAGE_BYTES + 1024; // + the stage's weights slice, 1024-aligned
 constexpr uint32_t ACC_COL = 0;                  // two accumulators: cols [0,128), [128,256)
-constexpr uint32_t A_COL = 2 * TN;               // A slots: 32 columns each (16 hi + 16 lo)
-constexpr int NWARPS = 16;
+constexpr uint32_t SUM_COL = 2 * TN;             // FP32 running sums: cols [256,384)
+constexpr uint32_t A_COL = 3 * TN;               // A slots: [384,512), 32 columns each
+constexpr int NWARPS = 15;
 constexpr int NTHREADS = NWARPS * 32;
-constexpr int PROD_WARP = 4;     // one thread: bulk copies of the pre-split B tiles
-constexpr int MMA_WARP = 5;      // warps 6-7 idle
-constexpr int EPI_WARP0 = 8;     // warps 8-15: drain/epilogue (two per lane quadrant)
-constexpr int EPI_COLS = TN / 2; // 64 columns per epilogue thread
-#ifndef GW_TC_CPD
-#define GW_TC_CPD 1
-#endif
-constexpr int CPD = GW_TC_CPD;                   // chunks accumulated per TMEM drain
-constexpr int FLUSH = 256;                       // chunks per FP64 fold of a running sum
+constexpr int A_WARPS = 8;       // warps 0-7: A transform, two per TMEM lane quadrant
+constexpr int PROD_WARP = 8;     // one thread: bulk copies of B tiles and weights
+constexpr int MMA_WARP = 9;      // warps 9 and 10 issue MMAs for even and odd chunks
+constexpr int EPI_WARP0 = 11;    // warps 11-14: drain/epilogue, one per lane quadrant
+constexpr int CPD = 2;                           // own chunks accumulated per TMEM drain
+constexpr int FLUSH = 256;                       // periods per FP64 fold of the running sums
 constexpr int TQ = 64;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
@@ -132,11 +132,10 @@ __device__ __forceinline__ void split_words(const float* y, uint32_t* hi, uint32
     }
   } else {
     for (int i = 0; i < nwords; ++i) {
-      __nv_bfloat16 h0 = __float2bfloat16_rn(y[2 * i]), h1 = __float2bfloat16_rn(y[2 * i + 1]);
-      __nv_bfloat16 l0 = __float2bfloat16_rn(y[2 * i] - __bfloat162float(h0));
-      __nv_bfloat16 l1 = __float2bfloat16_rn(y[2 * i + 1] - __bfloat162float(h1));
-      hi[i] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
-      lo[i] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+      const uint32_t h = tc::cvt_bf16x2(y[2 * i], y[2 * i + 1]);     // both hi pieces, RN
+      const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xFFFF0000u);
+      hi[i] = h;
+      lo[i] = tc::cvt_bf16x2(y[2 * i] - h0, y[2 * i + 1] - h1);
     }
   }
 }
@@ -159,26 +158,32 @@ template <bool BF16, bool QF>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_herk_tc(const __grid_constant__ TcLaunch L, double* __restrict__ acc64, unsigned* status) {
   constexpr int CH = BF16 ? 32 : 16;          // transitions per chunk (64 bytes of K)
-  constexpr int EPC = CH / 4;                 // K values per 16-byte chunk of a B row
+  constexpr int CH4 = CH / 4;                 // float4 per chunk column
   constexpr uint32_t IDESC = tc::instr_desc(BF16 ? 1u : 2u, TM, TN);
 
   extern __shared__ __align__(1024) char dsmem[];
   char* ring = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_bar[NS], empty_bar[NS], accf_bar[2], acce_bar[2], done_bar;
+  __shared__ __align__(8) uint64_t fullB[NSB], emptyB[NSB], fullA[NSA], emptyA[NSA], accf_bar[2],
+      acce_bar[2], done_bar[2];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NS; ++i) {
-      tc::mbar_init(&full_bar[i], 5);      // 4 A warps + the bulk-copy producer
-      tc::mbar_init(&empty_bar[i], 1);
+    for (int i = 0; i < NSB; ++i) {
+      tc::mbar_init(&fullB[i], 1);
+      tc::mbar_init(&emptyB[i], 1);
+    }
+    for (int i = 0; i < NSA; ++i) {
+      tc::mbar_init(&fullA[i], 4);         // the 4 lane-quadrant warps handling the chunk
+      tc::mbar_init(&emptyA[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&accf_bar[i], 1);
-      tc::mbar_init(&acce_bar[i], 8);      // 8 epilogue warps
+      tc::mbar_init(&acce_bar[i], 4);      // 4 epilogue warps
     }
-    tc::mbar_init(&done_bar, 1);
+    tc::mbar_init(&done_bar[0], 1);
+    tc::mbar_init(&done_bar[1], 1);
     s_abort = 0;
     tc::mbar_fence_init();
   }
@@ -192,101 +197,69 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = s_tmem;
   const int64_t nitems = L.item0[L.nq];
 
-  if (warp < PROD_WARP) {
+  if (warp < A_WARPS) {
     // ------------------------------------------------ A transform -> TMEM
-    // Units of 16 transitions (one TF32 chunk, half a BF16 chunk): each lane reads its
-    // column of the column-major copy and the weights as float4s; two units of loads
-    // are kept in flight ahead of the split.
-    const int qd = warp;                      // TMEM lane quadrant = A rows 32 qd .. 32 qd + 31
+    // The two warps of a lane quadrant take alternate chunks. Each lane reads its column of
+    // the column-major copy (float4s, the next chunk's loads in flight while the current one
+    // is split) and the chunk's weights from the shared-memory stage.
+    const int qd = warp & 3, par = warp >> 2;
     const int m = qd * 32 + lane;
-    constexpr int UPC = CH / 16;              // units per chunk
-    uint32_t g = 0;
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    uint32_t g0 = 0;
+    bool stop = false;
+    for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       int q, j, bi, bj;
       decode_item<QF>(L, item, q, j, bi, bj);
-      const int64_t K = L.K[q];
-      const int64_t kpad = L.kpad[q];
-      const float4* __restrict__ xc = reinterpret_cast<const float4*>(L.xT[q] + size_t(bi * TM + m) * kpad);
-      // quadratic form: no weights (the A operand is the pair projections themselves)
-      const float4* __restrict__ sj =
-          QF ? nullptr : reinterpret_cast<const float4*>(L.s[q] + size_t(j) * kpad);
-      const int64_t nch = (K + CH - 1) / CH;
-      const int64_t nunit = nch * UPC;
-      float4 xa[4], sa[4], xb[4], sb[4];
-      if (nunit > 0) {
+      const int64_t nch = (L.K[q] + CH - 1) / CH;
+      const float4* __restrict__ xc =
+          reinterpret_cast<const float4*>(L.xT[q] + size_t(bi * TM + m) * L.kpad[q]);
+      const int64_t c_first = int64_t((par - int(g0 & 1)) & 1);
+      float4 cur[CH4], nxt[CH4];
+      if (c_first < nch) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          xa[e] = __ldg(xc + e);
-          sa[e] = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(sj + e);
-        }
+        for (int e = 0; e < CH4; ++e) cur[e] = __ldg(xc + c_first * CH4 + e);
       }
-      if (nunit > 1) {
+      for (int64_t c = c_first; c < nch; c += 2) {
+        const uint32_t gg = g0 + uint32_t(c);
+        const int slot = gg % NSA, st = gg % NSB;
+        if (c + 2 < nch) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          xb[e] = __ldg(xc + 4 + e);
-          sb[e] = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(sj + 4 + e);
+          for (int e = 0; e < CH4; ++e) nxt[e] = __ldg(xc + (c + 2) * CH4 + e);
         }
-      }
-      bool stop = false;
-      for (int64_t u = 0; u < nunit; ++u) {
-        const int64_t c = u / UPC;
-        const int uc = int(u % UPC);
-        const uint32_t gg = g + uint32_t(c);
-        const int st = gg % NS;
-        float4 xn[4], sn[4];
-        if (u + 2 < nunit) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            xn[e] = __ldg(xc + (u + 2) * 4 + e);
-            sn[e] = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : __ldg(sj + (u + 2) * 4 + e);
-          }
-        }
-        if (uc == 0 && !warp_wait(&empty_bar[st], ((gg / NS) & 1) ^ 1, &s_abort, status)) {
+        if (!warp_wait(&fullB[st], (gg / NSB) & 1, &s_abort, status) ||
+            !warp_wait(&emptyA[slot], ((gg / NSA) & 1) ^ 1, &s_abort, status)) {
           stop = true;
           break;
         }
-        float y[16];
+        const float4* sw = reinterpret_cast<const float4*>(ring + st * STAGE_STRIDE + STAGE_BYTES);
+        const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * 32;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          y[4 * e + 0] = sa[e].x * xa[e].x;
-          y[4 * e + 1] = sa[e].y * xa[e].y;
-          y[4 * e + 2] = sa[e].z * xa[e].z;
-          y[4 * e + 3] = sa[e].w * xa[e].w;
-        }
-        const uint32_t slot = tmem + (uint32_t(qd * 32) << 16) + A_COL + st * 32;
-        if (!BF16) {
+        for (int h = 0; h < 2; ++h) {               // halves of the chunk: 8 TMEM words each
+          float y[CH / 2];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t hw[8], lw[8];
-            split_words<false>(y + 8 * h, hw, lw, 8);
-            tc::tmem_st8(slot + h * 8, hw);
-            tc::tmem_st8(slot + 16 + h * 8, lw);
+          for (int e = 0; e < CH4 / 2; ++e) {
+            const float4 xv = cur[h * (CH4 / 2) + e];
+            const float4 wv = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : sw[h * (CH4 / 2) + e];
+            y[4 * e + 0] = wv.x * xv.x;
+            y[4 * e + 1] = wv.y * xv.y;
+            y[4 * e + 2] = wv.z * xv.z;
+            y[4 * e + 3] = wv.w * xv.w;
           }
-        } else {
           uint32_t hw[8], lw[8];
-          split_words<true>(y, hw, lw, 8);
-          tc::tmem_st8(slot + uc * 8, hw);
-          tc::tmem_st8(slot + 16 + uc * 8, lw);
+          split_words<BF16>(y, hw, lw, 8);
+          tc::tmem_st8(base + h * 8, hw);
+          tc::tmem_st8(base + 16 + h * 8, lw);
         }
-        if (uc == UPC - 1) {
-          tc::tmem_wait_st();
-          tc::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&full_bar[st]);
-        }
+        tc::tmem_wait_st();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&fullA[slot]);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          xa[e] = xb[e];
-          sa[e] = sb[e];
-          xb[e] = xn[e];
-          sb[e] = sn[e];
-        }
+        for (int e = 0; e < CH4; ++e) cur[e] = nxt[e];
       }
-      g += uint32_t(nch);
-      if (stop) break;
+      g0 += uint32_t(nch);
     }
   } else if (warp == PROD_WARP) {
-    // ------------------------------------------------ B tiles: bulk copies
+    // ------------------------------------------------ B tiles and weights: bulk copies
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
@@ -295,15 +268,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         decode_item<QF>(L, item, q, j, bi, bj);
         const int64_t nch = (L.K[q] + CH - 1) / CH;
         const char* src = L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * nch * STAGE_BYTES;
+        const float* ws = QF ? nullptr : L.s[q] + size_t(j) * L.kpad[q];
         for (int64_t c = 0; c < nch; ++c, ++g) {
-          const int st = g % NS;
-          if (!tc::mbar_wait(&empty_bar[st], ((g / NS) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
+          const int st = g % NSB;
+          if (!tc::mbar_wait(&emptyB[st], ((g / NSB) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
             ok = false;
             break;
           }
-          tc::mbar_arrive_expect_tx(&full_bar[st], STAGE_BYTES);
-          tc::bulk_g2s(ring + st * STAGE_BYTES, src + size_t(c) * STAGE_BYTES, STAGE_BYTES,
-                       &full_bar[st]);
+          char* dst = ring + st * STAGE_STRIDE;
+          tc::mbar_arrive_expect_tx(&fullB[st], STAGE_BYTES + (QF ? 0 : CH * 4));
+          tc::bulk_g2s(dst, src + size_t(c) * STAGE_BYTES, STAGE_BYTES, &fullB[st]);
+          if (!QF) tc::bulk_g2s(dst + STAGE_BYTES, ws + c * CH, CH * 4, &fullB[st]);
         }
       }
       if (!ok && !s_abort) {
@@ -312,29 +287,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     __syncwarp();
-  } else if (warp == MMA_WARP) {
-    // ------------------------------------------------ MMA issue
+  } else if (warp == MMA_WARP || warp == MMA_WARP + 1) {
+    // ------------------------------------------------ MMA issue (two threads, alternate chunks)
+    // Chunk g goes to accumulator g mod 2 and is issued by MMA warp g mod 2, so the barrier
+    // waits of one issuing thread overlap the tensor-core work of the other.
+    const uint32_t mpar = uint32_t(warp - MMA_WARP);
     if (lane == 0) {
-      uint32_t g = 0, gp = 0;
+      uint32_t g = 0, kb = 0;       // kb: periods issued on this warp's accumulator
       const uint32_t ring_addr = tc::smem_u32(ring);
+      const uint32_t d = tmem + ACC_COL + mpar * TN;
       bool ok = true;
       for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         int q, j, bi, bj;
         decode_item<QF>(L, item, q, j, bi, bj);
         const int64_t nch = (L.K[q] + CH - 1) / CH;
-        for (int64_t c = 0; c < nch; ++c, ++g) {
-          const int st = g % NS;
-          const int buf = gp & 1;
-          const bool first = (c % CPD) == 0;
-          if (!tc::mbar_wait(&full_bar[st], (g / NS) & 1, &s_abort, WAIT_LIMIT) ||
-              (first && !tc::mbar_wait(&acce_bar[buf], ((gp >> 1) & 1) ^ 1, &s_abort, WAIT_LIMIT))) {
+        // own chunks of this item: local c = mpar, mpar + 2, ...; CPD of them per period
+        int64_t own = 0;
+        for (int64_t c = mpar; c < nch; c += 2, ++own) {
+          const uint32_t gg = g + uint32_t(c);
+          const int st = gg % NSB, slot = gg % NSA;
+          const bool first = (own % CPD) == 0;
+          const bool last = (own % CPD) == CPD - 1 || c + 2 >= nch;
+          if (!tc::mbar_wait(&fullB[st], (gg / NSB) & 1, &s_abort, WAIT_LIMIT) ||
+              !tc::mbar_wait(&fullA[slot], (gg / NSA) & 1, &s_abort, WAIT_LIMIT) ||
+              (first && !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT))) {
             ok = false;
             break;
           }
           tc::tc_fence_after();
-          const uint32_t d = tmem + ACC_COL + buf * TN;
-          const uint32_t a = tmem + A_COL + st * 32;
-          const uint32_t bs = ring_addr + st * STAGE_BYTES;
+          const uint32_t a = tmem + A_COL + slot * 32;
+          const uint32_t bs = ring_addr + st * STAGE_STRIDE;
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
             const uint64_t dBh = tc::smem_desc(bs + ks * 32, 512, 4);
@@ -351,83 +333,102 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               tc::mma_tf32_ta(d, ah, dBh, IDESC, 1u);
             }
           }
-          tc::mma_commit(&empty_bar[st]);
-          if ((c % CPD) == CPD - 1 || c == nch - 1) {
-            tc::mma_commit(&accf_bar[buf]);
-            ++gp;
+          tc::mma_commit(&emptyB[st]);
+          tc::mma_commit(&emptyA[slot]);
+          if (last) {
+            tc::mma_commit(&accf_bar[mpar]);
+            ++kb;
           }
         }
+        g += uint32_t(nch);
       }
       if (!ok && !s_abort) {
         s_abort = 1;
         raise_status(status, ST_ETIMEOUT);
       }
-      tc::mma_commit(&done_bar);
+      tc::mma_commit(&done_bar[mpar]);
       int never = 0;
-      tc::mbar_wait(&done_bar, 0, reinterpret_cast<volatile int*>(&never), WAIT_LIMIT);
+      tc::mbar_wait(&done_bar[mpar], 0, reinterpret_cast<volatile int*>(&never), WAIT_LIMIT);
     }
     __syncwarp();
   } else if (warp >= EPI_WARP0) {
     // ------------------------------------------------ drain / epilogue
+    // Each chunk's accumulator is added into FP32 running sums kept in TMEM (round to
+    // nearest); every FLUSH chunks (staggered over the warps) the sums are folded into FP64
+    // with L2 reductions.
     const int qd = warp & 3;
-    const int hf = (warp - EPI_WARP0) >> 2;
     const int r = qd * 32 + lane;               // tile row
-    const int c0 = hf * EPI_COLS;               // first tile column of this thread
-    double* acc = acc64 + size_t(blockIdx.x) * TN * TM + size_t(c0) * TM + r;   // [col][row]
-    uint32_t gp = 0;
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const uint32_t lane_base = tmem + (uint32_t(qd * 32) << 16);
+    double* acc = acc64 + size_t(blockIdx.x) * TN * TM + r;   // [col][row]
+    uint32_t kb[2] = {0, 0};        // periods drained per accumulator
+    uint32_t gp = 0;                // periods drained in total (flush schedule)
+    bool stop = false;
+    for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       int q, j, bi, bj;
       decode_item<QF>(L, item, q, j, bi, bj);
       const int64_t nch = (L.K[q] + CH - 1) / CH;
-      const int64_t nper = (nch + CPD - 1) / CPD;
+      const int64_t own0 = (nch + 1) / 2, own1 = nch / 2;
+      const int64_t np0 = (own0 + CPD - 1) / CPD, np1 = (own1 + CPD - 1) / CPD;
       const int nb = L.nb[q];
-      float sum[EPI_COLS];
-#pragma unroll
-      for (int i = 0; i < EPI_COLS; ++i) {
-        sum[i] = 0.0f;
-        acc[size_t(i) * TM] = 0.0;
-      }
-      bool stop = false;
-      for (int64_t c = 0; c < nper; ++c, ++gp) {
-        const int buf = gp & 1;
-        if (!warp_wait(&accf_bar[buf], (gp >> 1) & 1, &s_abort, status)) {
+#pragma unroll 8
+      for (int i = 0; i < TN; ++i) acc[size_t(i) * TM] = 0.0;
+      bool sum_empty = true;
+      for (int64_t k = 0; k < np0 + np1; ++k, ++gp) {
+        // alternate the two accumulators while both have periods left
+        const int64_t m = np0 < np1 ? np0 : np1;
+        const int buf = k < 2 * m ? int(k & 1) : (np0 > np1 ? 0 : 1);
+        if (!warp_wait(&accf_bar[buf], kb[buf] & 1, &s_abort, status)) {
           stop = true;
           break;
         }
+        ++kb[buf];
         tc::tc_fence_after();
-        const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + ACC_COL + buf * TN + c0;
-#pragma unroll
-        for (int k = 0; k < EPI_COLS / 32; ++k) {
+#pragma unroll 1
+        for (int cb = 0; cb < TN / 32; ++cb) {
+          uint32_t va[32], vs[32];
+          tc::tmem_ld32_nowait(lane_base + ACC_COL + buf * TN + cb * 32, va);
+          if (!sum_empty) tc::tmem_ld32_nowait(lane_base + SUM_COL + cb * 32, vs);
+          tc::tmem_wait_ld();
           float v[32];
-          tc::tmem_ld32(base + k * 32, v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) sum[k * 32 + i] += v[i];
+          for (int i = 0; i < 32; ++i)
+            v[i] = sum_empty ? __uint_as_float(va[i]) : __uint_as_float(va[i]) + __uint_as_float(vs[i]);
+          tc::tmem_st32(lane_base + SUM_COL + cb * 32, v);
         }
+        tc::tmem_wait_st();
+        sum_empty = false;
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
-        // fold the FP32 running sums into FP64 every FLUSH chunks, staggered over the
-        // epilogue warps so the slow FP64 adds of different warps do not coincide
-        if (int((c + (warp - EPI_WARP0) * (FLUSH / 8)) % FLUSH) == FLUSH - 1) {
+        if (int((gp + qd * (FLUSH / 4)) % FLUSH) == FLUSH - 1) {
+#pragma unroll 1
+          for (int cb = 0; cb < TN / 32; ++cb) {
+            float sv[32];
+            tc::tmem_ld32(lane_base + SUM_COL + cb * 32, sv);
 #pragma unroll
-          for (int i = 0; i < EPI_COLS; ++i) {
-            atomicAdd(acc + size_t(i) * TM, double(sum[i]));   // reduction at L2, no load
-            sum[i] = 0.0f;
+            for (int i = 0; i < 32; ++i) atomicAdd(acc + size_t(cb * 32 + i) * TM, double(sv[i]));
           }
+          sum_empty = true;
         }
       }
       if (stop) break;
-      // final fold
+      if (!sum_empty) {
+#pragma unroll 1
+        for (int cb = 0; cb < TN / 32; ++cb) {
+          float sv[32];
+          tc::tmem_ld32(lane_base + SUM_COL + cb * 32, sv);
 #pragma unroll
-      for (int i = 0; i < EPI_COLS; ++i) atomicAdd(acc + size_t(i) * TM, double(sum[i]));
+          for (int i = 0; i < 32; ++i) atomicAdd(acc + size_t(cb * 32 + i) * TM, double(sv[i]));
+        }
+      }
       __threadfence();
       if (QF) {
         // c_p += sum_c X[p][c] Y[p][c] over this tile's columns (X = the A rows themselves)
         const int64_t p = int64_t(bi) * TM + r;
-        const float* xr = L.xT[q] + size_t(p) * L.kpad[q] + size_t(bj) * TN + c0;
+        const float* xr = L.xT[q] + size_t(p) * L.kpad[q] + size_t(bj) * TN;
         double part = 0.0;
 #pragma unroll 8
-        for (int i = 0; i < EPI_COLS; ++i) part = fma(double(__ldg(xr + i)), acc[size_t(i) * TM], part);
+        for (int i = 0; i < TN; ++i) part = fma(double(__ldg(xr + i)), acc[size_t(i) * TM], part);
         if (p < L.nrow[q]) atomicAdd(L.cq[q] + size_t(j) * L.nrow[q] + p, part);
       } else {
         // complex combination of rows (2I, 2I+1) held by lanes (2l, 2l+1)
@@ -436,13 +437,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const bool odd = R & 1;
         double2* P = L.P[q] + size_t(j) * nb * nb;
 #pragma unroll 4
-        for (int jj = 0; jj < EPI_COLS / 2; ++jj) {
+        for (int jj = 0; jj < TN / 2; ++jj) {
           double e0 = acc[size_t(2 * jj) * TM];
           double e1 = acc[size_t(2 * jj + 1) * TM];
           double o0 = __shfl_xor_sync(0xffffffffu, e0, 1);
           double o1 = __shfl_xor_sync(0xffffffffu, e1, 1);
           if (!odd) {
-            const int J = (bj * TN + c0) / 2 + jj;
+            const int J = (bj * TN) / 2 + jj;
             if (I < nb && J < nb && I <= J) {
               double re = -(e0 + o1);
               double im = (I == J) ? 0.0 : -(o0 - e1);
@@ -662,7 +663,7 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
                                           kpad, nch, xT[q], bsp[q]);
     GW_LAUNCH_CHECK("k_prep_tc");
   }
-  const size_t smem = NS * STAGE_BYTES + 1024;
+  const size_t smem = NSB * STAGE_STRIDE + 1024;
   for (int q0 = 0; q0 < nq; q0 += TQ) {
     int n = std::min(TQ, nq - q0);
     TcLaunch L{};
@@ -760,7 +761,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
       GW_LAUNCH_CHECK("k_prep_quad");
     }
   }
-  const size_t smem = NS * STAGE_BYTES + 1024;
+  const size_t smem = NSB * STAGE_STRIDE + 1024;
   for (int q0 = 0; q0 < nq; q0 += TQ) {
     int n = std::min(TQ, nq - q0);
     TcLaunch L{};
