@@ -213,23 +213,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const float4* __restrict__ xc =
           reinterpret_cast<const float4*>(L.xT[q] + size_t(bi * TM + m) * L.kpad[q]);
       const int64_t c_first = int64_t((par - int(g0 & 1)) & 1);
-      float4 cur[CH4], nxt[CH4];
-      if (c_first < nch) {
+      const int64_t nown = nch > c_first ? (nch - c_first + 1) / 2 : 0;
+      // own chunk o is local chunk c_first + 2 o; two register buffers, no copies: the loads
+      // of own chunk o + 1 are in flight while own chunk o is split
+      auto load = [&](int64_t o, float4 (&r)[CH4]) {
+        const int64_t c = c_first + 2 * o;
 #pragma unroll
-        for (int e = 0; e < CH4; ++e) cur[e] = __ldg(xc + c_first * CH4 + e);
-      }
-      for (int64_t c = c_first; c < nch; c += 2) {
+        for (int e = 0; e < CH4; ++e) r[e] = __ldg(xc + c * CH4 + e);
+      };
+      auto process = [&](int64_t o, const float4 (&xr)[CH4]) -> bool {
+        const int64_t c = c_first + 2 * o;
         const uint32_t gg = g0 + uint32_t(c);
         const int slot = gg % NSA, st = gg % NSB;
-        if (c + 2 < nch) {
-#pragma unroll
-          for (int e = 0; e < CH4; ++e) nxt[e] = __ldg(xc + (c + 2) * CH4 + e);
-        }
         if (!warp_wait(&fullB[st], (gg / NSB) & 1, &s_abort, status) ||
-            !warp_wait(&emptyA[slot], ((gg / NSA) & 1) ^ 1, &s_abort, status)) {
-          stop = true;
-          break;
-        }
+            !warp_wait(&emptyA[slot], ((gg / NSA) & 1) ^ 1, &s_abort, status))
+          return false;
         const float4* sw = reinterpret_cast<const float4*>(ring + st * STAGE_STRIDE + STAGE_BYTES);
         const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * 32;
 #pragma unroll
@@ -237,7 +235,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           float y[CH / 2];
 #pragma unroll
           for (int e = 0; e < CH4 / 2; ++e) {
-            const float4 xv = cur[h * (CH4 / 2) + e];
+            const float4 xv = xr[h * (CH4 / 2) + e];
             const float4 wv = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : sw[h * (CH4 / 2) + e];
             y[4 * e + 0] = wv.x * xv.x;
             y[4 * e + 1] = wv.y * xv.y;
@@ -253,8 +251,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&fullA[slot]);
-#pragma unroll
-        for (int e = 0; e < CH4; ++e) cur[e] = nxt[e];
+        return true;
+      };
+      float4 X0[CH4], X1[CH4];
+      if (nown > 0) load(0, X0);
+      for (int64_t o = 0; o < nown; o += 2) {
+        if (o + 1 < nown) load(o + 1, X1);
+        if (!process(o, X0)) {
+          stop = true;
+          break;
+        }
+        if (o + 1 >= nown) break;
+        if (o + 2 < nown) load(o + 2, X0);
+        if (!process(o + 1, X1)) {
+          stop = true;
+          break;
+        }
       }
       g0 += uint32_t(nch);
     }
@@ -294,7 +306,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t mpar = uint32_t(warp - MMA_WARP);
     if (lane == 0) {
       uint32_t g = 0, kb = 0;       // kb: periods issued on this warp's accumulator
-      const uint32_t ring_addr = tc::smem_u32(ring);
+      const uint64_t desc0 = tc::smem_desc(tc::smem_u32(ring), 512, 4);
       const uint32_t d = tmem + ACC_COL + mpar * TN;
       bool ok = true;
       for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -316,11 +328,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc::tc_fence_after();
           const uint32_t a = tmem + A_COL + slot * 32;
-          const uint32_t bs = ring_addr + st * STAGE_STRIDE;
+          // descriptor address field is (addr >> 4): advancing the address adds to the low bits
+          const uint64_t dst = desc0 + uint64_t((st * STAGE_STRIDE) >> 4);
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t dBh = tc::smem_desc(bs + ks * 32, 512, 4);
-            const uint64_t dBl = tc::smem_desc(bs + B_TILE + ks * 32, 512, 4);
+            const uint64_t dBh = dst + uint64_t((ks * 32) >> 4);
+            const uint64_t dBl = dst + uint64_t((B_TILE + ks * 32) >> 4);
             const uint32_t ah = a + ks * 8, al = a + 16 + ks * 8;
             const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
             if (BF16) {
