@@ -389,6 +389,40 @@ def sampled_error(pipe):
     return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
 
+def run_case_herk(args):
+    """Profiling case: the polarization alone on one q of the 4x4x4-mesh workload, cut to
+    K = 102,400 transitions (N_b = 600, 16 frequencies; M = 0.49 GB in complex64, so every
+    input is larger than L2 while the device holds about 3 GB). Prints one line of timings,
+    not a bench line."""
+    import torch
+    import paper_1003_0316_gb300 as gw
+    wl = S.medium_mixed()
+    iq, K, nb = 1, 102400, wl.nb[1]
+    cdt = torch.complex128 if args.precision == "fp64" else torch.complex64
+    M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[iq], 0, K, nb, dtype=cdt)
+    d = torch.as_tensor(wl.delta(iq)[:K], device="cuda")
+    om = wl.omega()
+    P = [torch.empty((wl.nw, nb, nb), dtype=torch.complex128, device="cuda")]
+    ws = torch.empty(gw.polarization_workspace([K], [nb], wl.nw, args.precision),
+                     dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        gw.polarization([M], [d], om, wl.prefactor, args.precision, out=P, ws=ws)
+    gw.check()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        gw.polarization([M], [d], om, wl.prefactor, args.precision, out=P, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    gw.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    fl = 4.0 * K * nb * (nb + 1) * wl.nw
+    print(json.dumps({"case": "herk", "K": K, "N_b": nb, "n_omega": wl.nw,
+                      "precision": args.precision, "ms": ms,
+                      "tflops": fl / (ms * 1e-3) / 1e12}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,7 +430,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp64"])
+    ap.add_argument("--case", default=None, choices=["herk"],
+                    help="run one profiling case instead of the bench step")
     args = ap.parse_args()
+    if args.case == "herk":
+        run_case_herk(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
