@@ -67,10 +67,10 @@ constexpr int EPI_WARP0 = 11;    // warps 11-14: drain/epilogue, one per lane qu
 constexpr int CPD = 2;                           // own chunks accumulated per TMEM drain
 constexpr int FLUSH = 256;                       // periods per FP64 fold of the running sums
 constexpr int TQ = 64;
-constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr uint64_t WAIT_LIMIT = 2000000000ull;   // ns: 2 s per bounded wait
 
 struct TcLaunch {
-  const float* xT[TQ];      // [ncolp][kpad] column-major copy of the FP32 view of M (zero padded)
+  const float* xT[TQ];      // A side, chunk-major: float4 [row block][kpad / CH][CH / 4][128 rows]
   const char* bsp[TQ];      // [nbi][nch] pre-split B tiles: 8 KB hi + 8 KB lo, swizzled
   const float* s[TQ];       // [nw][kpad] |w_tj| in FP32 (zero padded)
   double2* P[TQ];           // polarization output (Hermitian store)
@@ -199,9 +199,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp < A_WARPS) {
     // ------------------------------------------------ A transform -> TMEM
-    // The two warps of a lane quadrant take alternate chunks. Each lane reads its column of
-    // the column-major copy (float4s, the next chunk's loads in flight while the current one
-    // is split) and the chunk's weights from the shared-memory stage.
+    // The two warps of a lane quadrant take alternate chunks. Each lane reads its column's
+    // values from the chunk-major copy (each float4 read of a warp is 512 contiguous bytes;
+    // the next chunk's loads in flight while the current one is split) and the chunk's
+    // weights from the shared-memory stage.
     const int qd = warp & 3, par = warp >> 2;
     const int m = qd * 32 + lane;
     uint32_t g0 = 0;
@@ -210,8 +211,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int q, j, bi, bj;
       decode_item<QF>(L, item, q, j, bi, bj);
       const int64_t nch = (L.K[q] + CH - 1) / CH;
-      const float4* __restrict__ xc =
-          reinterpret_cast<const float4*>(L.xT[q] + size_t(bi * TM + m) * L.kpad[q]);
+      const float4* __restrict__ xc = reinterpret_cast<const float4*>(L.xT[q]) +
+                                      size_t(bi) * size_t(L.kpad[q] / CH) * CH4 * TM + m;
       const int64_t c_first = int64_t((par - int(g0 & 1)) & 1);
       const int64_t nown = nch > c_first ? (nch - c_first + 1) / 2 : 0;
       // own chunk o is local chunk c_first + 2 o; two register buffers, no copies: the loads
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       auto load = [&](int64_t o, float4 (&r)[CH4]) {
         const int64_t c = c_first + 2 * o;
 #pragma unroll
-        for (int e = 0; e < CH4; ++e) r[e] = __ldg(xc + c * CH4 + e);
+        for (int e = 0; e < CH4; ++e) r[e] = __ldg(xc + size_t(c * CH4 + e) * TM);
       };
       auto process = [&](int64_t o, const float4 (&xr)[CH4]) -> bool {
         const int64_t c = c_first + 2 * o;
@@ -438,10 +439,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (QF) {
         // c_p += sum_c X[p][c] Y[p][c] over this tile's columns (X = the A rows themselves)
         const int64_t p = int64_t(bi) * TM + r;
-        const float* xr = L.xT[q] + size_t(p) * L.kpad[q] + size_t(bj) * TN;
+        // X[p][k] for k = bj * TN + i, read from the chunk-major copy
+        const float* xb = L.xT[q] + size_t(bi) * size_t(L.kpad[q] / CH) * CH * TM + size_t(r) * 4;
         double part = 0.0;
 #pragma unroll 8
-        for (int i = 0; i < TN; ++i) part = fma(double(__ldg(xr + i)), acc[size_t(i) * TM], part);
+        for (int i = 0; i < TN; ++i) {
+          const int64_t k = int64_t(bj) * TN + i;
+          const float xv = __ldg(xb + size_t((k / CH) * (CH / 4) + (k % CH) / 4) * TM * 4 + (k & 3));
+          part = fma(double(xv), acc[size_t(i) * TM], part);
+        }
         if (p < L.nrow[q]) atomicAdd(L.cq[q] + size_t(j) * L.nrow[q] + p, part);
       } else {
         // complex combination of rows (2I, 2I+1) held by lanes (2l, 2l+1)
@@ -475,9 +481,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// Per q, once: the column-major copy xT (A side) and the pre-split, pre-swizzled B tiles
-// (frequency independent). One CTA per (128-column block, chunk); the chunk of x is
-// staged through shared memory with coalesced float4 loads.
+// Per q, once: the chunk-major copy xT (A side: for each 128-column block and chunk, CH/4
+// float4 groups of 128 consecutive columns, so a warp's reads of one group are contiguous)
+// and the pre-split, pre-swizzled B tiles (frequency independent). One CTA per (128-column
+// block, chunk); the chunk of x is staged through shared memory with coalesced float4 loads.
 template <bool BF16>
 __global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, int64_t K, int ncol,
                                                  int64_t kpad, int64_t nch, float* __restrict__ xT,
@@ -501,9 +508,10 @@ __global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, in
   float v[CH];
 #pragma unroll
   for (int t = 0; t < CH; ++t) v[t] = tile[t][n];
-  float4* dst = reinterpret_cast<float4*>(xT + size_t(cb * TM + n) * kpad + c * CH);
+  float4* dst = reinterpret_cast<float4*>(xT) + (size_t(cb) * (kpad / CH) + c) * (CH / 4) * TM + n;
 #pragma unroll
-  for (int t = 0; t < CH / 4; ++t) dst[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+  for (int t = 0; t < CH / 4; ++t)
+    dst[size_t(t) * TM] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
   char* hi = bsp + (size_t(cb) * nch + c) * STAGE_BYTES;
 #pragma unroll
   for (int kc = 0; kc < 4; ++kc) {
@@ -516,14 +524,22 @@ __global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, in
 }
 
 // Quadratic form c_p = x_p^T R x_p (pair coefficients of the self-energy): the A operand is
-// the real view X of the pair projections, row-padded to 128 and column-padded to kpad.
+// the real view X of the pair projections, row-padded to 128 and column-padded to kpad, in
+// the chunk-major layout of the polarization's A side (rows = pairs, K = basis columns).
+template <int CH>
 __global__ void k_prep_xpad(const float* __restrict__ x, int64_t nrow, int ncol, int64_t nrowp,
                             int64_t kpad, float* __restrict__ xp) {
   const int64_t n4 = nrowp * (kpad / 4);
+  const int64_t nchp = kpad / CH;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n4;
        e += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t row = e / (kpad / 4);
-    const int64_t c = (e % (kpad / 4)) * 4;
+    // destination order: [row block][chunk][group of 4 columns][row in block]
+    const int64_t r = e % TM;
+    const int64_t g = (e / TM) % (CH / 4);
+    const int64_t ch = (e / (TM * (CH / 4))) % nchp;
+    const int64_t blk = e / (TM * (CH / 4) * nchp);
+    const int64_t row = blk * TM + r;
+    const int64_t c = ch * CH + g * 4;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (row < nrow && c < ncol) v = __ldg(reinterpret_cast<const float4*>(x + row * ncol + c));
     reinterpret_cast<float4*>(xp)[e] = v;
@@ -611,7 +627,7 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
     int nbi;
     q_sizes(K[q], nb[q], precision, &nch, &kpad, &nbi);
     b += ws_round(size_t(nw) * size_t(kpad) * sizeof(float));            // weights
-    b += ws_round(size_t(nbi) * TM * size_t(kpad) * sizeof(float));       // column-major copy
+    b += ws_round(size_t(nbi) * TM * size_t(kpad) * sizeof(float));       // chunk-major copy
     b += ws_round(size_t(nbi) * size_t(nch) * STAGE_BYTES);              // pre-split B tiles
   }
   return b;
@@ -760,8 +776,13 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
     if (!xp[q] || !bsp[q]) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
     GW_CUDA_TRY(cudaMemsetAsync(c[q], 0, sizeof(double) * size_t(nw) * size_t(npair[q]), s));
     const int64_t n4 = nrowp * (kpad / 4);
-    k_prep_xpad<<<unsigned(std::min<int64_t>((n4 + 255) / 256, int64_t(ctx.sm_count) * 16)), 256, 0,
-                  s>>>(static_cast<const float*>(Msig[q]), npair[q], 2 * nb[q], nrowp, kpad, xp[q]);
+    const unsigned xg = unsigned(std::min<int64_t>((n4 + 255) / 256, int64_t(ctx.sm_count) * 16));
+    if (bf)
+      k_prep_xpad<32><<<xg, 256, 0, s>>>(static_cast<const float*>(Msig[q]), npair[q], 2 * nb[q],
+                                         nrowp, kpad, xp[q]);
+    else
+      k_prep_xpad<16><<<xg, 256, 0, s>>>(static_cast<const float*>(Msig[q]), npair[q], 2 * nb[q],
+                                         nrowp, kpad, xp[q]);
     GW_LAUNCH_CHECK("k_prep_xpad");
     const dim3 pg(static_cast<unsigned>(nbj), static_cast<unsigned>(nch));
     for (int j = 0; j < nw; ++j) {

@@ -41,24 +41,35 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: returns false if the limit expired or *abort became non-zero.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes or about
+// hint_ns pass, instead of re-polling the barrier (which would load the shared-memory pipe
+// that the other roles' barrier traffic and the tensor-core operand reads also use).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: returns false once limit_ns of wall time (globaltimer) have passed or
+// *abort became non-zero.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
-                                          uint32_t limit) {
-#ifdef GW_SPIN_TEST_WAIT
-  for (uint32_t i = 0; i < limit; ++i) {
-    for (int k = 0; k < 64; ++k)
-      if (mbar_test_wait(bar, parity)) return true;
-    if (*abort) return false;
-  }
-  return false;
-#else
+                                          uint64_t limit_ns) {
   if (mbar_test_wait(bar, parity)) return true;     // fast path: phase already complete
-  for (uint32_t i = 0; i < limit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait_hint(bar, parity, 20000u)) return true;
     if (*abort) return false;
+    if ((i & 7u) == 7u && globaltimer_ns() - t0 > limit_ns) return false;
   }
-  return false;
-#endif
 }
 
 // ------------------------------------------------------------------ proxies
