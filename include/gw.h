@@ -59,7 +59,7 @@ enum gw_dtype { GW_C128 = 0, GW_C64 = 1 };
  * same with a two-term BF16 split. */
 enum gw_precision { GW_FP64 = 0, GW_TF32X3 = 1, GW_BF16X3 = 2 };
 
-enum gw_fit_method { GW_FIT_PLAIN = 0, GW_FIT_MLP = 1 };
+enum gw_fit_method { GW_FIT_PLAIN = 0, GW_FIT_MLP = 1, GW_FIT_MLP_ONLY = 2 };
 
 /* Library version: major * 10000 + minor * 100 + patch. */
 int gw_version(void);
@@ -198,7 +198,10 @@ int gw_sigma_c(int nq, const double* wq_host, const int64_t* npair_host,
  *   method GW_FIT_PLAIN: default start, residues by linear least squares.
  *   method GW_FIT_MLP: start proposed by the network (npole = 2, nw = 24,
  *     mlp_dev = packed FP32 weights, see gw_mlp_param_count); the fit from the
- *     default start is also run and the lower-cost result is kept.
+ *     default start is also run and the lower-cost result is kept (iters and status
+ *     are those of the kept fit).
+ *   method GW_FIT_MLP_ONLY: the fit from the network's start alone (for measuring
+ *     what the learned start gains over the default one).
  *   params_dev [ncurve][npole][4] double output (Re a, Im a, Re w, Im w);
  *   cost_dev [ncurve], iters_dev [ncurve], status_dev [ncurve] outputs
  *   (status 0 converged, 1 iteration limit, 2 damping overflow). */
@@ -212,7 +215,9 @@ int gw_continue(int ncurve, int nw, const double* omega_host, const double* sigm
  * Packed FP32 parameter layout: W1[128][48], b1[128], W2[128][128], b2[128],
  * W3[8][128], b3[8]. */
 int gw_mlp_param_count(void);
-/* Forward pass in BF16 tensor-free arithmetic for inference: out_dev [n][8] float. */
+/* Inference forward pass: input, weights, biases and hidden activations rounded to BF16
+ * (round to nearest even), FP32 accumulation and SiLU; sigma_dev [n][24] complex128,
+ * out_dev [n][8] float. */
 int gw_mlp_forward(int n, const double* sigma_dev, const float* mlp_dev, float* out_dev,
                    gw_stream_t stream);
 /* One FP32 training step on a batch: loss = mean_b (1/24) sum_j |f(i w_j) - y_j|^2/s^2.

@@ -8,7 +8,15 @@ w_p = o_{4p+2} + i o_{4p+3}. Training loss per curve: the imaginary-axis fit res
 of the proposed parameters, L = (1/n_w) sum_j |f(i w_j) - y_j|^2 / s^2, averaged over
 the batch; Adam (Kingma & Ba 2015) updates.
 
-Weights are stored row-major: W1 [128][48], W2 [128][128], W3 [8][128].
+Weights are stored row-major: W1 [128][48], W2 [128][128], W3 [8][128]; the packed
+vector is W1, b1, W2, b2, W3, b3 in that order.
+
+Inference in BF16 storage arithmetic (forward_bf16): the input, weights, biases and
+both hidden activations are rounded to BF16 (round to nearest, ties to even), sums are
+exact (FP64) and SiLU is FP64; a reference for a BF16 inference kernel, not a claim
+about rounding inside its sums.
+
+This module is test infrastructure: only the tests and the benchmark's CPU baseline use it.
 """
 import numpy as np
 
@@ -22,6 +30,41 @@ def silu(z):
 def dsilu(z):
     s = 1.0 / (1.0 + np.exp(-z))
     return s * (1.0 + z * (1.0 - s))
+
+
+ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def pack(p):
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).ravel() for k in ORDER])
+
+
+def unpack(v):
+    v = np.asarray(v, dtype=np.float64)
+    shapes = {"W1": (128, 48), "b1": (128,), "W2": (128, 128), "b2": (128,), "W3": (8, 128),
+              "b3": (8,)}
+    p, o = {}, 0
+    for k in ORDER:
+        n = int(np.prod(shapes[k]))
+        p[k] = v[o:o + n].reshape(shapes[k])
+        o += n
+    assert o == len(v)
+    return p
+
+
+def bf16_round(a):
+    """Round to the nearest BF16 value (ties to even), via the FP32 bit pattern."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(p, x):
+    q = {k: bf16_round(v) for k, v in p.items()}
+    h1 = bf16_round(silu(bf16_round(x) @ q["W1"].T + q["b1"]))
+    h2 = bf16_round(silu(h1 @ q["W2"].T + q["b2"]))
+    return h2 @ q["W3"].T + q["b3"]
 
 
 def init_params(seed):

@@ -21,7 +21,8 @@ GW_OK, GW_EINVAL, GW_EWORKSPACE, GW_ECUDA, GW_ENONFINITE, GW_ENOTHPD, GW_ETIMEOU
     GW_ENOCONV, GW_EUNSUPPORTED = range(9)
 GW_C128, GW_C64 = 0, 1
 GW_FP64, GW_TF32X3, GW_BF16X3 = 0, 1, 2
-GW_FIT_PLAIN, GW_FIT_MLP = 0, 1
+GW_FIT_PLAIN, GW_FIT_MLP, GW_FIT_MLP_ONLY = 0, 1, 2
+FIT_METHODS = {"plain": GW_FIT_PLAIN, "mlp": GW_FIT_MLP, "mlp_only": GW_FIT_MLP_ONLY}
 PRECISIONS = {"fp64": GW_FP64, "tf32x3": GW_TF32X3, "bf16x3": GW_BF16X3}
 MAX_NW = 64
 SIGMA_MIXED = True   # the pair coefficients have tensor-core (split precision) paths
@@ -263,7 +264,10 @@ def sigma_c(wq, Msigs, pair_states, epss, Wcs, omega, omega_out, nsig, precision
 
 # ---------------------------------------------------------------- a7 --------
 def continue_fit(sigma, omega, npole=2, sign=None, method="plain", mlp=None):
-    """Multipole fit per curve; returns (params [n][npole][4], cost, iters, status)."""
+    """Multipole fit per curve; returns (params [n][npole][4], cost, iters, status).
+    method: "plain" (default start), "mlp" (learned start, default start as fallback, the
+    lower cost kept) or "mlp_only" (learned start alone); the learned start needs mlp
+    (packed FP32 weights), npole = 2 and 24 frequencies."""
     om, nw = _om(omega)
     n = sigma.shape[0]
     dev = sigma.device
@@ -271,7 +275,7 @@ def continue_fit(sigma, omega, npole=2, sign=None, method="plain", mlp=None):
     cost = torch.empty(n, dtype=torch.float64, device=dev)
     iters = torch.empty(n, dtype=torch.int32, device=dev)
     status = torch.empty(n, dtype=torch.int32, device=dev)
-    m = GW_FIT_PLAIN if method == "plain" else GW_FIT_MLP
+    m = FIT_METHODS[method]
     _raise(_lib.gw_continue(n, nw, om, sigma.data_ptr(), sign.data_ptr() if sign is not None else None,
                             npole, m, mlp.data_ptr() if mlp is not None else None,
                             params.data_ptr(), cost.data_ptr(), iters.data_ptr(), status.data_ptr(),
@@ -289,6 +293,44 @@ def mlp_forward(sigma, mlp, out=None):
         out = torch.empty((n, 8), dtype=torch.float32, device=sigma.device)
     _raise(_lib.gw_mlp_forward(n, sigma.data_ptr(), mlp.data_ptr(), out.data_ptr(), _stream()))
     return out
+
+
+def mlp_init(seed, device="cuda"):
+    """Packed FP32 parameters: Glorot-uniform weights, zero biases (host draw, seeded)."""
+    g = torch.Generator().manual_seed(int(seed))
+    parts = []
+    for n_in, n_out in ((48, 128), (128, 128), (128, 8)):
+        lim = (6.0 / (n_in + n_out)) ** 0.5
+        parts.append((torch.rand((n_out, n_in), generator=g, dtype=torch.float64) * 2 - 1) * lim)
+        parts.append(torch.zeros(n_out, dtype=torch.float64))
+    w = torch.cat([t.reshape(-1) for t in parts]).to(torch.float32)
+    assert w.numel() == mlp_param_count()
+    return w.to(device)
+
+
+def train_mlp(curves, omega, mlp, steps, batch=512, lr=1e-3, seed=0, log_every=0):
+    """Adam training of the learned start on curves [n][24] (complex128, on the device):
+    each step draws a batch (seeded permutation per epoch) and calls mlp_train_step, which
+    runs forward, loss, back-propagation and the Adam update on the device. Returns the
+    per-step batch losses (read back at the end)."""
+    n = curves.shape[0]
+    dev = curves.device
+    npar = mlp_param_count()
+    grad = torch.empty(npar, dtype=torch.float32, device=dev)
+    m = torch.zeros(npar, dtype=torch.float32, device=dev)
+    v = torch.zeros(npar, dtype=torch.float32, device=dev)
+    losses = torch.empty(steps, dtype=torch.float32, device=dev)
+    g = torch.Generator().manual_seed(int(seed))
+    perm = torch.randperm(n, generator=g).to(dev)
+    pos = 0
+    for t in range(1, steps + 1):
+        if pos + batch > n:
+            perm = torch.randperm(n, generator=g).to(dev)
+            pos = 0
+        xb = curves.index_select(0, perm[pos:pos + batch]).contiguous()
+        pos += batch
+        mlp_train_step(xb, omega, mlp, grad, m, v, lr, t, losses[t - 1:t])
+    return losses.cpu()
 
 
 def mlp_train_step(sigma, omega, mlp, grad, m, v, lr, step, loss):

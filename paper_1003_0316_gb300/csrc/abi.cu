@@ -341,8 +341,18 @@ int gw_continue(int ncurve, int nw, const double* omega_host, const double* sigm
   if (method == GW_FIT_PLAIN)
     return launch_lm(ncurve, nw, om, sigma_dev, sign_dev, npole, nullptr, params_dev, cost_dev,
                      iters_dev, status_dev, 0, stream);
-  if (method != GW_FIT_MLP) return set_error(GW_EINVAL, "unknown fit method %d", method);
-  return set_error(GW_EUNSUPPORTED, "learned start not built");
+  if (method != GW_FIT_MLP && method != GW_FIT_MLP_ONLY)
+    return set_error(GW_EINVAL, "unknown fit method %d", method);
+  if (npole != 2 || nw != 24 || !mlp_dev)
+    return set_error(GW_EINVAL, "the learned start needs npole = 2, nw = 24 and weights");
+  // the network's proposal is written into params_dev and read back as the start
+  rc = mlp_start(ncurve, sigma_dev, mlp_dev, params_dev, stream);
+  if (rc) return rc;
+  rc = launch_lm(ncurve, nw, om, sigma_dev, sign_dev, npole, params_dev, params_dev, cost_dev,
+                 iters_dev, status_dev, 0, stream);
+  if (rc || method == GW_FIT_MLP_ONLY) return rc;
+  return launch_lm(ncurve, nw, om, sigma_dev, sign_dev, npole, nullptr, params_dev, cost_dev,
+                   iters_dev, status_dev, 1, stream);
 }
 
 int gw_mlp_param_count(void) { return MLP_NPARAM; }

@@ -114,6 +114,7 @@ int launch_lm(int ncurve, int nw, const OmegaArr& om, const double* sigma, const
               int npole, const double* theta_init, double* params, double* cost, int* iters,
               int* status, int keep_better, cudaStream_t s);
 int mlp_forward(int n, const double* sigma, const float* w, float* out, cudaStream_t s);
+int mlp_start(int n, const double* sigma, const float* w, double* theta, cudaStream_t s);
 int mlp_train_step(int n, const OmegaArr& om, const double* sigma, float* w, float* grad, float* m,
                    float* v, float lr, int step, float* loss, cudaStream_t s);
 int dielectric_wc_noalloc(int nb, int nw, const double* v, const double* P, double* Wc,

@@ -11,7 +11,10 @@ generator and stands in for them:
   shape: decaying weight for higher Coulomb eigenfunctions);
 * Coulomb eigenvalues v_I = 4 pi / (0.1 + I^(2/3)) (Eq. dielec_MB input);
 * imaginary-frequency mesh omega_j = tan(theta_j), theta_j the Gauss-Legendre nodes on
-  [0, arctan 50] (dense near 0, Sec. III.C).
+  [0, arctan 50] (dense near 0, Sec. III.C);
+* model self-energy curves for the analytic continuation (Sec. III.C): sums of simple
+  poles shaped like the single-transition closed form of Sigma^c (positive residue, pole
+  at eps' + sgn(eps') Omega just off the real axis), many poles per curve.
 
 This module performs none of the method's arithmetic (no weights, no products, no
 solves); it only lays out indices and draws numbers. Both the CPU oracle and the
@@ -32,6 +35,7 @@ TID_MSIG = 4
 TID_SIZES = 5
 TID_KP = 6
 TID_MISC = 7
+TID_CURVES = 8
 
 SEED_BASE = 0x10030316
 
@@ -273,3 +277,37 @@ def tiny(nb=8, nocc=2, nunocc=3, mesh=(1, 1, 2), nw=6, seed=12345, qs=(0,), nw_o
 def sigma_curves_mesh():
     """24-node output mesh used for the analytic-continuation curves."""
     return omega_mesh(24)
+
+
+CURVE_MAXPOLE = 24
+
+
+def model_sigma_curves(seed, n, omega, first=0):
+    """n model curves y_c(i omega_j) = sum_k r_k / (i omega_j - e_k) and state signs.
+
+    Per curve c (counter index first + c): 4 to 24 poles; each pole k draws a band energy
+    eps_k (occupied U[-0.5, 0] or unoccupied U[0.05, 2] Ha, even odds), a plasmon-like
+    energy Omega_k ~ U[0.3, 1.5] Ha and a residue r_k ~ U[0.005, 0.1] Ha; the pole sits at
+    e_k = eps_k + sgn(eps_k) Omega_k - 0.01 i sgn(eps_k) (the side of the real axis that a
+    time-ordered self-energy has). The state sign is +1 or -1 with even odds.
+    Returns (curves [n][len(omega)] complex128, sign [n])."""
+    omega = np.asarray(omega, dtype=np.float64)
+    c = np.arange(first, first + n, dtype=np.int64)
+    per = 2 + 5 * CURVE_MAXPOLE
+    base = c * per
+    u = lambda k: uniforms(seed, TID_CURVES, base + k)
+    npole = 4 + np.minimum((u(0) * 21).astype(np.int64), 20)
+    sign = np.where(u(1) < 0.5, -1.0, 1.0)
+    z = 1j * omega[None, :]
+    y = np.zeros((n, len(omega)), dtype=np.complex128)
+    for k in range(CURVE_MAXPOLE):
+        o = 2 + 5 * k
+        occ = u(o) < 0.5
+        eps = np.where(occ, -0.5 * u(o + 1), 0.05 + 1.95 * u(o + 1))
+        Om = 0.3 + 1.2 * u(o + 2)
+        r = 0.005 + 0.095 * u(o + 3)
+        sg = np.where(occ, -1.0, 1.0)
+        e = eps + sg * Om - 0.01j * sg
+        active = (k < npole).astype(np.float64)
+        y += (active * r)[:, None] / (z - e[:, None])
+    return y, sign

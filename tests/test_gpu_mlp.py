@@ -1,0 +1,130 @@
+"""Learned start of the multipole fit: BF16 inference, FP32 training kernels (loss,
+back-propagation, Adam) against the FP64 oracle, and the gain of the trained network
+over the plain fit's default start on held-out model curves."""
+import numpy as np
+import pytest
+
+import synth_inputs as S
+from oracle import mlp as OM
+from oracle import continuation as OC
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gw():
+    import paper_1003_0316_gb300 as g
+    return g
+
+
+OM24 = S.omega_mesh(24)
+
+
+def curves(n, first=0, seed=S.SEED_BASE + 100):
+    return S.model_sigma_curves(seed, n, OM24, first=first)
+
+
+def dev(a, dt=None):
+    return torch.as_tensor(np.asarray(a), device="cuda:0", dtype=dt)
+
+
+def test_forward_bf16_against_oracle(gw):
+    y, _ = curves(45)                     # ragged: 2 full CTAs of 16 curves + 13
+    w = gw.mlp_init(3)
+    out = gw.mlp_forward(dev(y), w)
+    gw.check()
+    p = OM.unpack(w.cpu().numpy().astype(np.float64))
+    x, s = OM.features(y)
+    ref16 = OM.forward_bf16(p, x)
+    ref64, _ = OM.forward(p, x)
+    got = out.cpu().numpy().astype(np.float64)
+    scale = np.abs(ref64).max()
+    # same BF16 roundings; an activation near a BF16 rounding boundary may round the other
+    # way after FP32 instead of exact sums (2^-8 relative on that activation)
+    assert np.abs(got - ref16).max() <= 5e-3 * scale
+    # against exact FP64 inference: BF16 storage of inputs, weights and activations
+    assert np.abs(got - ref64).max() <= 5e-2 * scale
+
+
+def test_train_step_gradient_against_oracle(gw):
+    y, _ = curves(70, first=1000)
+    w = gw.mlp_init(5)
+    npar = gw.mlp_param_count()
+    grad = torch.empty(npar, dtype=torch.float32, device="cuda:0")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda:0")
+    gw.mlp_train_step(dev(y), OM24, w, grad, None, None, 0.0, 1, loss)
+    gw.check()
+    p = OM.unpack(w.cpu().numpy().astype(np.float64))
+    L, gref = OM.loss_and_grads(p, OM24, y)
+    gref = OM.pack(gref)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - L) <= 1e-5 * abs(L)
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+    # every block of the packed gradient is nonzero and matches on its own
+    off = 0
+    for k in OM.ORDER:
+        n = p[k].size
+        gk, rk = g[off:off + n], gref[off:off + n]
+        assert np.linalg.norm(gk - rk) <= 1e-3 * np.linalg.norm(rk) + 1e-12, k
+        off += n
+
+
+def test_adam_step_against_oracle(gw):
+    y, _ = curves(32, first=2000)
+    w = gw.mlp_init(7)
+    w0 = w.clone()
+    npar = gw.mlp_param_count()
+    grad = torch.empty(npar, dtype=torch.float32, device="cuda:0")
+    m = torch.zeros(npar, dtype=torch.float32, device="cuda:0")
+    v = torch.zeros(npar, dtype=torch.float32, device="cuda:0")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda:0")
+    lr = 1e-3
+    for t in (1, 2):
+        gw.mlp_train_step(dev(y), OM24, w, grad, m, v, lr, t, loss)
+    gw.check()
+    p = OM.unpack(w0.cpu().numpy().astype(np.float64))
+    st = {}
+    for t in (1, 2):
+        _, gr = OM.loss_and_grads(p, OM24, y)
+        p = OM.adam_step(p, gr, st, lr, t)
+    got = w.cpu().numpy().astype(np.float64)
+    ref = OM.pack(p)
+    # a step moves each weight by at most ~lr; components whose gradient is near zero
+    # relative to eps may differ in step size, never by more than 2 lr
+    assert np.abs(got - ref).max() <= 2.0 * lr
+    assert np.median(np.abs(got - ref)) <= 1e-3 * lr
+
+
+def test_trained_start_gain_over_plain_fit(gw):
+    """Train on 20,000 model curves, evaluate on 512 held-out ones: the fit from the
+    learned start alone, the plain fit, and the combined method (learned start with
+    the default start as fallback, lower cost kept)."""
+    ytr, _ = curves(20000, first=0, seed=S.SEED_BASE + 101)
+    yte, sg = curves(512, first=0, seed=S.SEED_BASE + 102)
+    w = gw.mlp_init(11)
+    losses = gw.train_mlp(dev(ytr), OM24, w, steps=3000, batch=512, lr=2e-3, seed=1)
+    gw.check()
+    assert float(losses[-200:].mean()) < 0.5 * float(losses[:50].mean())
+    Y = dev(yte)
+    sign = dev(sg)
+    res = {}
+    for meth in ("plain", "mlp_only", "mlp"):
+        prm, cost, it, st = gw.continue_fit(Y, OM24, npole=2, sign=sign, method=meth, mlp=w)
+        gw.check()
+        res[meth] = (cost.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy())
+    c_plain, it_plain, _ = res["plain"]
+    c_mlp, it_mlp, _ = res["mlp_only"]
+    c_comb, _, _ = res["mlp"]
+    # the combined method never ends above the plain fit
+    assert np.all(c_comb <= c_plain * (1 + 1e-12))
+    # the learned start alone: fewer LM iterations on average, and a failure rate
+    # (final cost above 10x the plain fit's) of at most 10 %
+    fail = np.mean(c_mlp > 10.0 * c_plain)
+    print(f"\nlearned-start gain on {len(c_plain)} held-out curves: mean LM iterations "
+          f"plain {it_plain.mean():.1f}, learned start {it_mlp.mean():.1f}; median final cost "
+          f"plain {np.median(c_plain):.3e}, learned {np.median(c_mlp):.3e}, combined "
+          f"{np.median(c_comb):.3e}; failure rate (cost > 10x plain) {fail:.3f}; "
+          f"training loss {float(losses[:50].mean()):.3e} -> {float(losses[-200:].mean()):.3e}")
+    assert fail <= 0.10, fail
+    assert it_mlp.mean() < it_plain.mean(), (it_mlp.mean(), it_plain.mean())

@@ -273,3 +273,21 @@ def test_mlp_gradients_against_finite_differences():
             fd = (Lp - Lm) / (2 * h)
             an = g[name].reshape(-1)[idx]
             assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-3 * abs(L)) + 1e-11, (name, idx, fd, an)
+
+
+def test_bf16_rounding_matches_torch_and_packing_round_trips():
+    """The BF16 emulation of the inference reference agrees with torch's own BF16
+    conversion (round to nearest, ties to even), including exact ties; the packed layout
+    round-trips."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    a = (rng.normal(size=4000) * 10.0 ** rng.uniform(-3, 3, size=4000)).astype(np.float32)
+    ties = (np.arange(1, 200, dtype=np.uint32) << 16 | 0x8000).view(np.float32)   # exact ties
+    a = np.concatenate([a, ties, -ties])
+    got = OM.bf16_round(a)
+    ref = torch.tensor(a).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(got, ref)
+    p = OM.init_params(3)
+    q = OM.unpack(OM.pack(p))
+    assert all(np.array_equal(p[k], q[k]) for k in OM.ORDER)
+    assert OM.pack(p).size == 128 * 48 + 128 + 128 * 128 + 128 + 8 * 128 + 8
