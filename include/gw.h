@@ -189,6 +189,43 @@ int gw_sigma_c(int nq, const double* wq_host, const int64_t* npair_host,
                int precision, void* ws_dev, size_t ws_bytes, gw_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * a4. q = Gamma head and wings (Sec. III.D, Eqs. polar_Gamma and screen_Gamma and the
+ * expressions after them; Eq. correlation_div). FP64.
+ *   Paug_dev [nw][nb+3][nb+3] complex128: the polarization (gw_polarization, FP64 or
+ *     split precision) of the augmented projections [p | M], where the first three columns
+ *     p_t hold the linear-in-k coefficients of the projection onto the divergent Coulomb
+ *     eigenfunction (k.p input), so that H = Paug[:3,:3], s_nu = Paug[:3, 3+nu],
+ *     P~ = Paug[3:,3:];
+ *   v_dev [nb] the Coulomb eigenvalues of the body.
+ * Writes, per frequency: Wc_dev [nw][nb][nb] the body W~^c plus the l = 0 average of the
+ * rank-one term of Eq. screen_Gamma; head_dev [nw] K^c_00 = sqrt(4 pi) <4 pi / e^T L e> -
+ * (4 pi)^(3/2) (sphere average); L_dev [nw][3][3] complex128 and u_dev [nw][nb][3]
+ * complex128 (u_nu = sum_mu s_mu W~_mu,nu), both optional (NULL).
+ * The head and wings follow the exact block inverse of the full problem:
+ *   W_11 = 4 pi / (k^2 e^T L e), W_1nu = 4 pi e^T u_nu / (k e^T L e),
+ *   L = 1 - 4 pi H - 4 pi sum_nu u_nu s_nu^H.
+ * A direction with e^T L e <= 0 is reported by gw_check as GW_EINVAL. */
+size_t gw_gamma_workspace(int nb, int nw);
+int gw_gamma_screened_w(int nb, int nw, const double* v_dev, const double* Paug_dev,
+                        double* Wc_dev, double* head_dev, double* L_dev, double* u_dev,
+                        void* ws_dev, size_t ws_bytes, gw_stream_t stream);
+/* BZ constant (V / 8 pi^3) int_BZ d^3k / k^2 - sum_{k != 0} 1/k^2 of a simple-cubic lattice
+ * (lattice constant a, n x n x n k mesh, V = (n a)^3) in the erf form of Sec. III.D with
+ * exp(-beta q0^2) = beta. The lattice sum runs on the device; the result is returned to
+ * out_host, so this call synchronizes the stream. */
+size_t gw_bz_constant_workspace(void);
+int gw_bz_constant_sc(double a, int n, double beta, double* out_host, void* ws_dev,
+                      size_t ws_bytes, gw_stream_t stream);
+/* Eq. correlation_div: adds -C / (4 pi^(3/2) V) int dw' K^c_00(w') / (i w + i w' - e_s) to
+ * sigma_dev [nsig][nw_out] (complex128) for each state s (energy eps_state_dev[s] != 0),
+ * the frequency integral by the a6 spline-in-lambda and tail rule on the nodes omega_host. */
+size_t gw_sigma_div_workspace(int nw, int nsig);
+int gw_sigma_div(int nw, const double* omega_host, const double* head_dev, double cbz,
+                 double volume, int nsig, const double* eps_state_dev, int nw_out,
+                 const double* omega_out_host, double* sigma_dev, void* ws_dev, size_t ws_bytes,
+                 gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * a7. Analytic continuation (Eq. modelf): fit f(z) = sum_p a_p / (z - w_p) to each
  * curve Sigma(i omega_j) by FP64 Levenberg-Marquardt (Marquardt's diagonal
  * scaling; cost 1/2 sum_j |f(i omega_j) - Sigma_j|^2).

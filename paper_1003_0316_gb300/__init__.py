@@ -67,6 +67,13 @@ _sig("gw_continue", _i32, _i32, _i32, _P(_f64), _vp, _vp, _i32, _i32, _vp, _vp, 
 _sig("gw_mlp_param_count", _i32)
 _sig("gw_mlp_forward", _i32, _i32, _vp, _vp, _vp, _vp)
 _sig("gw_mlp_train_step", _i32, _i32, _P(_f64), _vp, _vp, _vp, _vp, _vp, _f32, _i32, _vp, _vp)
+_sig("gw_gamma_workspace", _sz, _i32, _i32)
+_sig("gw_gamma_screened_w", _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp)
+_sig("gw_bz_constant_workspace", _sz)
+_sig("gw_bz_constant_sc", _i32, _f64, _i32, _f64, _P(_f64), _vp, _sz, _vp)
+_sig("gw_sigma_div_workspace", _sz, _i32, _i32)
+_sig("gw_sigma_div", _i32, _i32, _P(_f64), _vp, _f64, _f64, _i32, _vp, _i32, _P(_f64), _vp, _vp,
+     _sz, _vp)
 _sig("gw_synth_projections", _i32, _u64, _u32, _u32, _i64, _i64, _i32, _i32, _vp, _vp)
 
 
@@ -260,6 +267,49 @@ def sigma_c(wq, Msigs, pair_states, epss, Wcs, omega, omega_out, nsig, precision
                            _dtype_code(Msigs[0]), _ptrs(pair_states), _ptrs(epss), nw, om,
                            _ptrs(Wcs), nwo, omo, nsig, out.data_ptr(), prec, wsp, wsn, _stream()))
     return out
+
+
+# ---------------------------------------------------------------- a4 --------
+def gamma_screened_w(Paug, v, out=None, want_L=True, want_u=True):
+    """q = Gamma: from the polarization of the augmented projections [p | M] (three k.p
+    columns first), the body W~^c with the l = 0 average of the rank-one term, the head
+    coefficient K^c_00 per frequency, and (optionally) L [nw][3][3] and u [nw][nb][3].
+    Returns (Wc, head, L, u)."""
+    nw, na, _ = Paug.shape
+    nb = na - 3
+    dev = Paug.device
+    if out is None:
+        out = torch.empty((nw, nb, nb), dtype=torch.complex128, device=dev)
+    head = torch.empty(nw, dtype=torch.float64, device=dev)
+    L = torch.empty((nw, 3, 3), dtype=torch.complex128, device=dev) if want_L else None
+    u = torch.empty((nw, nb, 3), dtype=torch.complex128, device=dev) if want_u else None
+    _buf, wsp, wsn = _ws(_lib.gw_gamma_workspace(nb, nw), dev)
+    _raise(_lib.gw_gamma_screened_w(nb, nw, v.data_ptr(), Paug.data_ptr(), out.data_ptr(),
+                                    head.data_ptr(), L.data_ptr() if L is not None else None,
+                                    u.data_ptr() if u is not None else None, wsp, wsn,
+                                    _stream()))
+    return out, head, L, u
+
+
+def bz_constant_sc(a, n, beta=0.005, device="cuda"):
+    """BZ constant of a simple-cubic lattice in the erf form (synchronizes the stream)."""
+    out = ctypes.c_double(0.0)
+    _buf, wsp, wsn = _ws(_lib.gw_bz_constant_workspace(), torch.device(device))
+    _raise(_lib.gw_bz_constant_sc(float(a), int(n), float(beta), ctypes.byref(out), wsp, wsn,
+                                  _stream()))
+    return out.value
+
+
+def sigma_div(omega, head, cbz, volume, eps_state, omega_out, sigma):
+    """Adds the divergent head term of Sigma^c (Eq. correlation_div) to sigma [nsig][nw_out]."""
+    om, nw = _om(omega)
+    omo, nwo = _om(omega_out)
+    nsig = eps_state.shape[0]
+    _buf, wsp, wsn = _ws(_lib.gw_sigma_div_workspace(nw, nsig), sigma.device)
+    _raise(_lib.gw_sigma_div(nw, om, head.data_ptr(), float(cbz), float(volume), nsig,
+                             eps_state.data_ptr(), nwo, omo, sigma.data_ptr(), wsp, wsn,
+                             _stream()))
+    return sigma
 
 
 # ---------------------------------------------------------------- a7 --------

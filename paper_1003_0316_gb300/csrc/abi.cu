@@ -390,3 +390,73 @@ int gw_synth_projections(uint64_t seed, uint32_t tid, uint32_t q, int64_t row0, 
 }
 
 }  // extern "C"
+
+extern "C" {
+
+size_t gw_gamma_workspace(int nb, int nw) {
+  if (nb < 1 || nw < 1) return 0;
+  return gamma_workspace(nb, nw);
+}
+
+int gw_gamma_screened_w(int nb, int nw, const double* v_dev, const double* Paug_dev,
+                        double* Wc_dev, double* head_dev, double* L_dev, double* u_dev,
+                        void* ws_dev, size_t ws_bytes, gw_stream_t stream) {
+  if (nb < 1 || nb > 8192) return set_error(GW_EINVAL, "nb=%d outside [1, 8192]", nb);
+  if (nw < 1 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [1, %d]", nw, GW_MAX_NW);
+  if (!v_dev || !Paug_dev || !Wc_dev || !head_dev)
+    return set_error(GW_EINVAL, "NULL v_dev, Paug_dev, Wc_dev or head_dev");
+  int rc = check_ws(ws_dev, ws_bytes, gamma_workspace(nb, nw));
+  if (rc) return rc;
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return gamma_screened_w(nb, nw, v_dev, Paug_dev, Wc_dev, head_dev, L_dev, u_dev, ws_dev,
+                          ws_bytes, stream, ctx);
+}
+
+size_t gw_bz_constant_workspace(void) {
+  DeviceCtx ctx;
+  if (device_ctx(&ctx)) return 0;
+  return bz_constant_workspace(ctx);
+}
+
+int gw_bz_constant_sc(double a, int n, double beta, double* out_host, void* ws_dev,
+                      size_t ws_bytes, gw_stream_t stream) {
+  if (!(a > 0.0) || n < 1 || !(beta > 0.0 && beta < 1.0) || !out_host)
+    return set_error(GW_EINVAL, "need a > 0, n >= 1, 0 < beta < 1 and an output");
+  DeviceCtx ctx;
+  int rc = device_ctx(&ctx);
+  if (rc) return rc;
+  return bz_constant_sc(a, n, beta, out_host, ws_dev, ws_bytes, stream, ctx);
+}
+
+size_t gw_sigma_div_workspace(int nw, int nsig) {
+  if (nw < 1 || nsig < 1) return 0;
+  return sigma_div_workspace(nw, nsig);
+}
+
+int gw_sigma_div(int nw, const double* omega_host, const double* head_dev, double cbz,
+                 double volume, int nsig, const double* eps_state_dev, int nw_out,
+                 const double* omega_out_host, double* sigma_dev, void* ws_dev, size_t ws_bytes,
+                 gw_stream_t stream) {
+  if (nw < 4) return set_error(GW_EINVAL, "the convolution needs nw >= 4 nodes (nw=%d)", nw);
+  OmegaArr om, om_out;
+  int rc = fill_omega(nw, omega_host, &om, true, true);
+  if (rc) return rc;
+  if (nw_out < 1 || nw_out > GW_MAX_NW || !omega_out_host)
+    return set_error(GW_EINVAL, "nw_out=%d outside [1, %d] or NULL omega_out", nw_out, GW_MAX_NW);
+  memset(&om_out, 0, sizeof(om_out));
+  for (int i = 0; i < nw_out; ++i) {
+    if (!std::isfinite(omega_out_host[i])) return set_error(GW_EINVAL, "omega_out[%d] not finite", i);
+    om_out.v[i] = omega_out_host[i];
+  }
+  if (nsig < 1 || !sigma_dev || !head_dev || !eps_state_dev)
+    return set_error(GW_EINVAL, "nsig < 1 or NULL sigma_dev, head_dev or eps_state_dev");
+  if (!std::isfinite(cbz) || !(volume > 0.0)) return set_error(GW_EINVAL, "bad BZ constant or volume");
+  if ((rc = check_ws(ws_dev, ws_bytes, sigma_div_workspace(nw, nsig)))) return rc;
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return sigma_div(nw, om, head_dev, cbz, volume, nsig, eps_state_dev, nw_out, om_out, sigma_dev,
+                   ws_dev, ws_bytes, stream, ctx);
+}
+
+}  // extern "C"

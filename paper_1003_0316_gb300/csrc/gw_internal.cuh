@@ -104,6 +104,24 @@ int convolve(int nq, const double* wq, const int64_t* npair, int nw, const Omega
              const double* const* c, const int* const* pair_state, const double* const* eps,
              int nw_out, const OmegaArr& om_out, int nsig, double* sigma, void* ws,
              size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
+// the same, adding into sigma when accumulate is set
+int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const OmegaArr& om,
+                 const double* const* c, const int* const* pair_state, const double* const* eps,
+                 int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
+                 cudaStream_t s, const DeviceCtx& ctx);
+
+// a4 (q = Gamma)
+size_t gamma_workspace(int nb, int nw);
+int gamma_screened_w(int nb, int nw, const double* v, const double* Paug, double* Wc,
+                     double* head, double* L, double* u_out, void* ws, size_t ws_bytes,
+                     cudaStream_t s, const DeviceCtx& ctx);
+size_t bz_constant_workspace(const DeviceCtx& ctx);
+int bz_constant_sc(double a, int n, double beta, double* out, void* ws, size_t ws_bytes,
+                   cudaStream_t s, const DeviceCtx& ctx);
+size_t sigma_div_workspace(int nw, int nsig);
+int sigma_div(int nw, const OmegaArr& om, const double* head, double cbz, double volume, int nsig,
+              const double* eps_state, int nw_out, const OmegaArr& om_out, double* sigma,
+              void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
 
 }  // namespace gw
 

@@ -402,6 +402,14 @@ int convolve(int nq, const double* wq, const int64_t* npair, int nw, const Omega
              const double* const* c, const int* const* pair_state, const double* const* eps,
              int nw_out, const OmegaArr& om_out, int nsig, double* sigma, void*, size_t,
              cudaStream_t s, const DeviceCtx& ctx) {
+  return convolve_acc(nq, wq, npair, nw, om, c, pair_state, eps, nw_out, om_out, nsig, sigma,
+                      false, s, ctx);
+}
+
+int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const OmegaArr& om,
+                 const double* const* c, const int* const* pair_state, const double* const* eps,
+                 int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
+                 cudaStream_t s, const DeviceCtx& ctx) {
   for (int q0 = 0; q0 < nq; q0 += SMAXQ) {
     int n = std::min(SMAXQ, nq - q0);
     ConvLaunch L{};
@@ -414,8 +422,8 @@ int convolve(int nq, const double* wq, const int64_t* npair, int nw, const Omega
       L.wq[q] = wq[q0 + q];
     }
     dim3 grid(nsig, nw_out);
-    k_convolve<<<grid, CTHREADS, 0, s>>>(L, nw, om, om_out, nw_out, sigma, q0 > 0 ? 1 : 0,
-                                         ctx.status);
+    k_convolve<<<grid, CTHREADS, 0, s>>>(L, nw, om, om_out, nw_out, sigma,
+                                         (accumulate || q0 > 0) ? 1 : 0, ctx.status);
     GW_LAUNCH_CHECK("k_convolve");
   }
   return GW_OK;
