@@ -492,16 +492,18 @@ __global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, in
   constexpr int CH = BF16 ? 32 : 16;
   constexpr int EPC = CH / 4;
   __shared__ __align__(16) float tile[CH][TM + 4];
-  const int cb = blockIdx.x;
-  const int64_t c = blockIdx.y;
+  const int cb = blockIdx.y;               // column block (grid.y <= 65535)
+  const int64_t c = blockIdx.x;             // chunk (grid.x: up to 2^31 - 1)
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < CH * (TM / 4); idx += 128) {
-    const int t = idx / (TM / 4), c4 = idx % (TM / 4);
+  // float2 loads: a row of the FP32 view has 2 N_b floats, so 8-byte alignment always holds
+  // (16-byte alignment only for even N_b)
+  for (int idx = tid; idx < CH * (TM / 2); idx += 128) {
+    const int t = idx / (TM / 2), c2 = idx % (TM / 2);
     const int64_t row = c * CH + t;
-    const int col = cb * TM + 4 * c4;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (row < K && col < ncol) v = __ldg(reinterpret_cast<const float4*>(x + row * ncol + col));
-    *reinterpret_cast<float4*>(&tile[t][4 * c4]) = v;
+    const int col = cb * TM + 2 * c2;
+    float2 v = make_float2(0.f, 0.f);
+    if (row < K && col < ncol) v = __ldg(reinterpret_cast<const float2*>(x + row * ncol + col));
+    *reinterpret_cast<float2*>(&tile[t][2 * c2]) = v;
   }
   __syncthreads();
   const int n = tid;
@@ -540,8 +542,18 @@ __global__ void k_prep_xpad(const float* __restrict__ x, int64_t nrow, int ncol,
     const int64_t blk = e / (TM * (CH / 4) * nchp);
     const int64_t row = blk * TM + r;
     const int64_t c = ch * CH + g * 4;
+    // two float2 loads (8-byte aligned for any N_b; ncol = 2 N_b is even)
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (row < nrow && c < ncol) v = __ldg(reinterpret_cast<const float4*>(x + row * ncol + c));
+    if (row < nrow && c < ncol) {
+      const float2 a = __ldg(reinterpret_cast<const float2*>(x + row * ncol + c));
+      v.x = a.x;
+      v.y = a.y;
+      if (c + 2 < ncol) {
+        const float2 b = __ldg(reinterpret_cast<const float2*>(x + row * ncol + c + 2));
+        v.z = b.x;
+        v.w = b.y;
+      }
+    }
     reinterpret_cast<float4*>(xp)[e] = v;
   }
 }
@@ -554,8 +566,8 @@ __global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W
                                                    int64_t nch, char* __restrict__ bsp) {
   constexpr int CH = BF16 ? 32 : 16;
   constexpr int EPC = CH / 4;
-  const int cb = blockIdx.x;
-  const int64_t ch = blockIdx.y;
+  const int cb = blockIdx.y;
+  const int64_t ch = blockIdx.x;
   const int n = threadIdx.x;
   const int c = cb * TN + n;
   const int J = c >> 1, b = c & 1;
@@ -658,9 +670,6 @@ static int launch_tc(const TcLaunch& L, bool bf, unsigned grid, size_t smem, dou
 
 int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
            void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
-  for (int q = 0; q < nq; ++q)
-    if (qs[q].nb & 1)
-      return set_error(GW_EINVAL, "tensor-core path needs an even N_b (q=%d has %d)", q, qs[q].nb);
   const bool bf = precision == GW_BF16X3;
   WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
   double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
@@ -682,7 +691,7 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     k_abs_weights_f32<<<unsigned(blocks), 256, 0, s>>>(qs[q].K, kpad, qs[q].delta, qs[q].f, pref,
                                                        nw, om, sw[q], ctx.status);
     GW_LAUNCH_CHECK("k_abs_weights_f32");
-    const dim3 pg(static_cast<unsigned>(nbi), static_cast<unsigned>(nch));
+    const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbi));
     if (nch > 2147483647LL) return set_error(GW_EINVAL, "too many transitions for one q");
     if (bf)
       k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K, 2 * qs[q].nb,
@@ -751,9 +760,6 @@ size_t quad_tc_workspace(int nq, const int64_t* npair, const int* nb, int nw, in
 int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig, int nw,
             const double* const* Wc, double* const* c, int precision, void* ws, size_t ws_bytes,
             cudaStream_t s, const DeviceCtx& ctx) {
-  for (int q = 0; q < nq; ++q)
-    if (nb[q] & 1)
-      return set_error(GW_EINVAL, "tensor-core path needs an even N_b (q=%d has %d)", q, nb[q]);
   const bool bf = precision == GW_BF16X3;
   WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
   double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
@@ -784,7 +790,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
       k_prep_xpad<16><<<xg, 256, 0, s>>>(static_cast<const float*>(Msig[q]), npair[q], 2 * nb[q],
                                          nrowp, kpad, xp[q]);
     GW_LAUNCH_CHECK("k_prep_xpad");
-    const dim3 pg(static_cast<unsigned>(nbj), static_cast<unsigned>(nch));
+    const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbj));
     for (int j = 0; j < nw; ++j) {
       const double2* W = reinterpret_cast<const double2*>(Wc[q]) + size_t(j) * nb[q] * nb[q];
       char* dst = bsp[q] + size_t(j) * nbj * nch * STAGE_BYTES;

@@ -77,12 +77,50 @@ def test_tc_empty_transitions(gw):
     assert torch.count_nonzero(P) == 0
 
 
-def test_tc_rejects_odd_basis(gw):
-    wl = S.tiny(nb=9)
-    with pytest.raises(gw.GWError) as e:
-        gw.polarization([T(wl.m_full(0).astype(np.complex64))], [T(wl.delta(0))], wl.omega(), 1.0,
-                        "tf32x3")
-    assert e.value.code == gw.GW_EINVAL
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("nb", [9, 37, 129])
+def test_tc_odd_basis(gw, prec, nb):
+    """Odd N_b: the FP32 view has 2 N_b (not a multiple of 4) floats per row."""
+    wl = S.tiny(nb=nb, nocc=3, nunocc=17, mesh=(2, 1, 2), nw=4, seed=nb)
+    om = wl.omega()
+    M = wl.m_full(0).astype(np.complex64)
+    P = gw.polarization([T(M)], [T(wl.delta(0))], om, wl.prefactor, prec)[0]
+    gw.check()
+    ref = OP.polarization(M.astype(np.complex128), wl.delta(0), om, wl.prefactor)
+    assert rel_fro(P.cpu().numpy(), ref) <= BOUND[prec]
+
+
+def test_tc_polarization_cuda_graph_replay(gw):
+    """The split-precision polarization captured in a CUDA graph and replayed on new
+    inputs gives the direct call's result bit for bit (every launch only enqueues)."""
+    wls = [S.tiny(nb=nb, nocc=3, nunocc=nu, mesh=(2, 2, 1), nw=5, seed=30 + nb)
+           for nb, nu in ((64, 20), (50, 11))]
+    om = wls[0].omega()
+    Ms = [T(w.m_full(0).astype(np.complex64)) for w in wls]
+    ds = [T(w.delta(0)) for w in wls]
+    Ks = [m.shape[0] for m in Ms]
+    nbs = [m.shape[1] for m in Ms]
+    ws = torch.empty(gw.polarization_workspace(Ks, nbs, len(om), "tf32x3"), dtype=torch.uint8,
+                     device="cuda:0")
+    out = [torch.empty((len(om), nb, nb), dtype=torch.complex128, device="cuda:0") for nb in nbs]
+    gw.polarization(Ms, ds, om, 0.5, "tf32x3", out=out, ws=ws)      # warm-up outside capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            gw.polarization(Ms, ds, om, 0.5, "tf32x3", out=out, ws=ws)
+    for trial in range(2):
+        scale = 1.0 + trial
+        for m, w in zip(Ms, wls):
+            m.copy_(T(w.m_full(0).astype(np.complex64)) * scale)
+        g.replay()
+        torch.cuda.synchronize()
+        got = [o.clone() for o in out]
+        direct = gw.polarization(Ms, ds, om, 0.5, "tf32x3")
+        gw.check()
+        for a, b in zip(got, direct):
+            assert torch.equal(a, b)
 
 
 @pytest.mark.slow
@@ -156,3 +194,29 @@ def test_tc_sigma_end_to_end_small(gw, prec):
     so = OE.sigma_c(om, om, list(wl.wq), [co], [ps], [eps], nsig)
     bound = 1e-5 * max(1.0, float(np.abs(so).max()))
     assert float(np.abs(sig.cpu().numpy() - so).max()) <= bound
+
+
+@pytest.mark.slow
+def test_tc_batched_uneven_full_size_sampled(gw):
+    """The 64-q mesh workload with N_b ~ U[300, 1500] (odd and even N_b): the smallest and
+    largest q and two seeded ones at full size (K up to 1.6e6 transitions, projections
+    generated on the device), 16 sampled columns per q against the oracle."""
+    wl = S.batched_uneven()
+    om = wl.omega()
+    nbs = np.array(wl.nb)
+    rng = np.random.default_rng(64)
+    picks = [int(np.argmin(nbs)), int(np.argmax(nbs))] + [int(x) for x in rng.choice(64, 2, replace=False)]
+    for iq in picks:
+        K, nb = wl.K(iq), wl.nb[iq]
+        M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[iq], 0, K, nb, dtype=torch.complex64)
+        P = gw.polarization([M], [T(wl.delta(iq))], om, wl.prefactor, "tf32x3")[0]
+        gw.check()
+        del M
+        cols = np.sort(rng.choice(nb, size=16, replace=False))
+        got = P[:, cols][:, :, cols].cpu().numpy()
+        del P
+        torch.cuda.empty_cache()
+        Mc = wl.m_rows(iq, cols=cols).astype(np.complex64).astype(np.complex128)
+        ref = OP.polarization(Mc, wl.delta(iq), om, wl.prefactor)
+        err = rel_fro(got, ref)
+        assert err <= 1e-6, (iq, nb, K, err)
