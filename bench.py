@@ -137,7 +137,7 @@ def cpu_oracle_sample(wl, budget_s=20.0):
 
 
 def run_reference(args, rank, world):
-    wl = S.medium_mixed()
+    wl = S.medium_mixed_sharded(world)
     if rank != 0:
         return
     res = []
@@ -167,7 +167,9 @@ class Pipeline:
     def __init__(self, wl, precision, device):
         import torch
         import paper_1003_0316_gb300 as gw
+        from paper_1003_0316_gb300 import distributed
         self.gw, self.torch, self.wl, self.prec = gw, torch, wl, precision
+        self.dist = distributed
         self.dev = device
         cdt = torch.complex128 if precision == "fp64" else torch.complex64
         self.om = wl.omega()
@@ -217,6 +219,8 @@ class Pipeline:
         gw.screened_w(self.P, self.v, out=self.P, ws=self.ws_w)
         gw.sigma_c(list(self.wl.wq), self.Msig, self.pair_state, self.eps, self.P, self.om,
                    self.om_out, self.nsig, precision=self.sprec, out=self.sigma, ws=self.ws_s)
+        # ranks hold partial sums over their q points: the one exchange of the path
+        self.dist.allreduce_sum_(self.sigma)
         return gw.continue_fit(self.sigma, self.om_out, npole=2, sign=self.sign)
 
     def launches_per_step(self):
@@ -236,7 +240,11 @@ def run_gpu(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = S.medium_mixed()
+    # weak scaling: 8 q points per rank of the 4x4x4-mesh workload, Sigma summed over ranks
+    from paper_1003_0316_gb300 import distributed
+    wl_all = S.medium_mixed_sharded(world)
+    lo, hi = distributed.shard(wl_all.nq, rank, world)
+    wl = wl_all.subset(range(lo, hi)) if world > 1 else wl_all
     pipe = Pipeline(wl, args.precision, dev)
     gw = pipe.gw
     fp, fs = workload_flops(wl)
@@ -295,7 +303,8 @@ def run_gpu(args, rank, world):
         "dtype": {"tf32x3": "tf32x3+f32acc(P,Sigma)/f64(W,fit)",
                   "bf16x3": "bf16x3+f32acc(P,Sigma)/f64(W,fit)", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded Philox draws shaped like the paper's systems)",
-        "config": {"workload": wl.name, "nq": wl.nq, "N_MPB": wl.nb[0], "K_per_q": wl.K(0),
+        "config": {"workload": wl_all.name, "nq": wl_all.nq, "nq_per_rank": wl.nq,
+                   "N_MPB": wl.nb[0], "K_per_q": wl.K(0),
                    "n_omega": wl.nw, "n_sigma_states": pipe.nsig, "precision": args.precision,
                    "sigma_precision": pipe.sprec, "l2": "inputs larger than L2 (M = "
                    f"{sum(m.numel() * m.element_size() for m in pipe.M) / 1e9:.1f} GB)"},

@@ -94,6 +94,16 @@ class Workload:
     def nk(self):
         return int(np.prod(self.mesh))
 
+    def subset(self, idx):
+        """The same problem restricted to the q points idx (BZ weights kept: a shard of a
+        sum over q)."""
+        idx = list(idx)
+        from dataclasses import replace
+        return replace(self, name=f"{self.name}_q{idx[0]}-{idx[-1]}" if idx else self.name + "_empty",
+                       qs=tuple(self.qs[i] for i in idx), wq=tuple(self.wq[i] for i in idx),
+                       nb=tuple(self.nb[i] for i in idx), nunocc=tuple(self.nunocc[i] for i in idx),
+                       extra=dict(self.extra))
+
     @property
     def nq(self):
         return len(self.qs)
@@ -238,6 +248,26 @@ def medium_mixed():
                   mesh=mesh, qs=qs, wq=tuple([8.0 / 64.0] * 8), nb=tuple([600] * 8),
                   nocc=16, nunocc=tuple([400] * 8), nw=16)
     wl.states = _top_states(wl, 8, 8)
+    return wl
+
+
+def medium_mixed_sharded(world):
+    """The 4x4x4-mesh workload of medium_mixed with 8 q per rank for world ranks (weak
+    scaling): the 8 points with n_i in {0,1} first, then further mesh points in index
+    order; every q has weight 1 / (8 world)."""
+    base = medium_mixed()
+    if world == 1:
+        return base
+    mesh = base.mesh
+    nq = 8 * int(world)
+    if nq > int(np.prod(mesh)):
+        raise ValueError("at most 8 ranks: the 4x4x4 mesh has 64 q points")
+    rest = [q for q in range(int(np.prod(mesh))) if q not in base.qs]
+    qs = tuple(base.qs) + tuple(rest[:nq - 8])
+    wl = Workload(name=f"nk64_{nq}q_nb600_nocc16_nunocc400_nw16", seed=base.seed, mesh=mesh,
+                  qs=qs, wq=tuple([1.0 / nq] * nq), nb=tuple([600] * nq), nocc=16,
+                  nunocc=tuple([400] * nq), nw=16)
+    wl.states = base.states
     return wl
 
 
