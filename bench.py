@@ -10,9 +10,13 @@ transitions per q, 16 imaginary frequencies, 16 self-energy states):
 The metric is algorithmic GFLOP/s of P + the Sigma^c contraction per step:
   P: 4 K N_b (N_b + 1) per (q, omega); Sigma: 8 N_b^2 N_pair per (q, omega).
 Inputs are synthetic (seeded Philox draws, see synth_inputs) and generated on the
-device; with N ranks each rank runs its own copy of the workload (weak scaling).
+device; with N ranks each rank takes 8 further q points of the mesh (weak scaling) and the
+partial Sigma^c curves are summed over ranks before the fit.
+The default split precision is BF16x3; the sampled error of P against the oracle is
+measured in every run and reported beside the number, and the TF32x3 polarization is timed
+too (field "tf32x3_polarization").
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|bf16x3|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|tf32x3|fp64]
     python bench.py --impl reference ...   # the CPU FP64 oracle on a bounded sample
 """
 import argparse
@@ -32,6 +36,11 @@ sys.path.insert(0, ROOT)
 import synth_inputs as S  # noqa: E402
 
 METRIC = "P(iω)+Σ^c GFLOP/s and % of roofline, mixed vs FP64 on GB300 at ≤1e-6 rel err"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one bench launch of the
+# split-precision HERK, from the ncu capture summarised in profiles/ (one q cut to
+# K = 102,400, scaled by K x q to the 8 q of K = 409,600). Valid for the kernel as profiled.
+HERK_TRAFFIC_BYTES = {"tf32x3": 14.74e9 * 32, "bf16x3": 9.87e9 * 32}
 
 
 def workload_flops(wl):
@@ -288,6 +297,7 @@ def run_gpu(args, rank, world):
 
     # FP64 GPU path on a bounded sample (one q, 2 frequencies) for the mixed-vs-FP64 line
     fp64 = fp64_sample(pipe) if args.precision != "fp64" else None
+    tf32 = tf32_polarization(pipe) if args.precision == "bf16x3" else None
     err = sampled_error(pipe)
 
     if rank != 0:
@@ -315,11 +325,14 @@ def run_gpu(args, rank, world):
                      "peak_source": (f"{src} bf16 x 0.5 (nominal tf32/bf16)" if args.precision == "tf32x3"
                                      else f"{src} bf16" if args.precision == "bf16x3"
                                      else "nominal FP64 1.25 TFLOP/s"),
-                     "traffic": None, "launch_ms": p_launch_ms},
+                     "traffic": HERK_TRAFFIC_BYTES.get(args.precision),
+                     "traffic_source": "ncu capture of one q at K = 102,400 scaled by K x q",
+                     "launch_ms": p_launch_ms},
         "clocks": ck,
         "e2e": e2e,
         "gpu_launches": pipe.launches_per_step() * args.steps,
         "fp64_gpu_sample": fp64,
+        "tf32x3_polarization": tf32,
         "sampled_rel_err_P": err,
     }
     if world == 1:
@@ -381,7 +394,35 @@ def fp64_sample(pipe):
             "sample": f"FP64 polarization of q=0 (K={K}, N_b={nb}) at 2 frequencies"}
 
 
-def sampled_error(pipe):
+def tf32x3_polarization_note():
+    return "TF32x3 gw_polarization on the same 8 q (events around the call), sampled error"
+
+
+def tf32_polarization(pipe):
+    """The same polarization call in TF32x3 (two timed calls after one warm-up) and its
+    sampled error, for the TF32x3-vs-BF16x3 comparison."""
+    torch = pipe.torch
+    gw = pipe.gw
+    wl = pipe.wl
+    ws = torch.empty(gw.polarization_workspace([wl.K(i) for i in range(wl.nq)], list(wl.nb), wl.nw,
+                                               "tf32x3"), dtype=torch.uint8, device=pipe.dev)
+    gw.polarization(pipe.M, pipe.delta, pipe.om, wl.prefactor, "tf32x3", out=pipe.P, ws=ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(2):
+        gw.polarization(pipe.M, pipe.delta, pipe.om, wl.prefactor, "tf32x3", out=pipe.P, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 2
+    fp, _ = workload_flops(wl)
+    err = sampled_error(pipe, precision="tf32x3", rerun=False)
+    return {"ms": ms, "tflops": fp / (ms * 1e-3) / 1e12, "sampled_rel_err_P": err,
+            "note": tf32x3_polarization_note()}
+
+
+def sampled_error(pipe, precision=None, rerun=True):
     """Relative Frobenius error of sampled P entries (last step, q=1) against the oracle,
     which regenerates the needed projection columns on the host."""
     from oracle import polarization as OP
@@ -389,10 +430,12 @@ def sampled_error(pipe):
     wl = pipe.wl
     iq = 1
     cols = np.arange(0, wl.nb[iq], 41)
-    gw.polarization(pipe.M, pipe.delta, pipe.om, wl.prefactor, pipe.prec, out=pipe.P, ws=pipe.ws_p)
+    if rerun:
+        gw.polarization(pipe.M, pipe.delta, pipe.om, wl.prefactor, pipe.prec, out=pipe.P,
+                        ws=pipe.ws_p)
     got = pipe.P[iq][:, cols][:, :, cols].cpu().numpy()
     Mc = wl.m_rows(iq, cols=cols)
-    if pipe.prec != "fp64":
+    if (precision or pipe.prec) != "fp64":
         Mc = Mc.astype(np.complex64).astype(np.complex128)
     ref = OP.polarization(Mc, wl.delta(iq), pipe.om, wl.prefactor)
     return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
@@ -438,7 +481,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp64"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
     ap.add_argument("--case", default=None, choices=["herk"],
                     help="run one profiling case instead of the bench step")
     args = ap.parse_args()
