@@ -12,26 +12,30 @@
 //
 // Accuracy: the tensor core adds into its FP32 accumulator with truncation, which
 // biases a long chain of additions toward zero (about 2e-8 of the running value per
-// MMA). Every chunk of 64 bytes of K (16 TF32 or 32 BF16 transitions) therefore starts
-// a fresh accumulator; the epilogue adds the chunk results into FP32 registers (round
-// to nearest) and folds each running sum into FP64 every 256 chunks (FP64 reductions
-// performed at L2 into per-CTA sums), so no truncating
-// chain is longer than six MMAs (one chunk); the round-to-nearest FP32 sums add only
-// unbiased errors that average out over the folds.
+// MMA). Every round of two 64-byte K chunks (2 x 16 TF32 or 2 x 32 BF16 transitions, 12
+// MMAs) therefore starts a fresh accumulator; the epilogue adds each round's result into
+// FP32 running sums kept in TMEM (round to nearest) and folds them into FP64 every 256
+// rounds (FP64 reductions performed at L2 into per-CTA sums), so no truncating chain is
+// longer than 12 MMAs; the round-to-nearest FP32 sums add only unbiased errors that
+// average out over the folds.
 //
-// Layout and roles (512 threads, one persistent CTA per SM; 512 TMEM columns):
-//   TMEM  cols [0,128) and [128,256): two accumulators (chunk c uses c mod 2);
-//         cols [256,352): three A slots (16 columns hi + 16 lo each).
-//   warps 0-3    A transform: scale x by s_tj, split, tcgen05.st into the A slot of
-//                their lane quadrant;
-//   warps 4-5    B transform: split x into the K-major 64-byte-swizzled hi/lo tiles
-//                of a three-stage shared-memory ring;
-//   warp 6       one thread issues tcgen05.mma (A from TMEM, B from shared memory);
-//                warp 7 idles
-//                and tcgen05.commit;
-//   warps 8-15   epilogue: tcgen05.ld of the finished accumulator, FP32 running sums
-//                in registers (64 per thread),
-//                FP64 folding, the final complex combination and the Hermitian store.
+// Layout and roles (480 threads, one persistent CTA per SM; 512 TMEM columns):
+//   TMEM  cols [0,256): two accumulators (round g uses g mod 2);
+//         cols [256,384): FP32 running sums;
+//         cols [384,512): two A slots of one round each (per chunk 16 columns hi + 16 lo).
+//   warps 0-7    A transform: scale x by s_tj, split, tcgen05.st into the A slot of their
+//                lane quadrant; set g mod 2 (warps 4 (g mod 2) .. + 3) takes round g and
+//                owns slot g mod 2;
+//   warp 8       one thread issues the bulk copies of a round's pre-split B tiles and
+//                weights into a 6-stage shared-memory ring;
+//   warps 9-10   one thread each issues the MMAs (A from TMEM, B from shared memory) of the
+//                rounds of one accumulator, and tcgen05.commit;
+//   warps 11-14  epilogue, one per lane quadrant: tcgen05.ld of the finished accumulator
+//                and of the running sums, their sum back into TMEM, FP64 folding, the final
+//                complex combination and the Hermitian store.
+// Every barrier is waited on only by threads that see each of its phases in order (a
+// parity wait cannot tell phase p from phase p + 2): stage and slot counts are even, so the
+// A set and the MMA issuer of round g also handled rounds g - NSB and g - NSA.
 // Only tiles that meet the upper triangle (complex I <= J) are computed. Every mbarrier
 // wait is bounded; on expiry the CTA records a timeout in the status word and winds
 // down, waiting for its own MMAs before releasing TMEM.
@@ -50,21 +54,23 @@ namespace {
 constexpr int TM = 128;          // real Gram rows per tile (A operand, in TMEM)
 constexpr int TN = 128;          // real Gram columns per tile (B operand, in shared memory)
 constexpr int SWB = 64;          // bytes of K per B row per chunk (64-byte swizzle)
-constexpr int NSB = 8;           // B stages in shared memory
-constexpr int NSA = 4;           // A slots in TMEM
-constexpr int B_TILE = TN * SWB;                 // 8 KB
-constexpr int STAGE_BYTES = 2 * B_TILE;          // hi + lo
-constexpr int STAGE_STRIDE = STAGE_BYTES + 1024; // + the stage's weights slice, 1024-aligned
+constexpr int SUB = 2;           // 64-byte K chunks per barrier round
+constexpr int NSB = 6;           // B stages (rounds) in shared memory
+constexpr int NSA = 2;           // A slots (rounds) in TMEM: one per A set
+constexpr int B_TILE = TN * SWB;                 // 8 KB: one chunk's hi (or lo) tile
+constexpr int CHUNK_BYTES = 2 * B_TILE;          // hi + lo of one chunk (pre-split layout)
+constexpr int STAGE_BYTES = SUB * CHUNK_BYTES;   // one round
+constexpr int STAGE_STRIDE = STAGE_BYTES + 1024; // + the round's weights slice, 1024-aligned
 constexpr uint32_t ACC_COL = 0;                  // two accumulators: cols [0,128), [128,256)
 constexpr uint32_t SUM_COL = 2 * TN;             // FP32 running sums: cols [256,384)
-constexpr uint32_t A_COL = 3 * TN;               // A slots: [384,512), 32 columns each
-constexpr int NWARPS = 15;
-constexpr int NTHREADS = NWARPS * 32;
-constexpr int A_WARPS = 8;       // warps 0-7: A transform, two per TMEM lane quadrant
+constexpr uint32_t A_COL = 3 * TN;               // A slots: [384,512), 64 columns each
+constexpr int A_WARPS = 8;       // warps 0-7: A transform, two sets of one warp per quadrant
 constexpr int PROD_WARP = 8;     // one thread: bulk copies of B tiles and weights
-constexpr int MMA_WARP = 9;      // warps 9 and 10 issue MMAs for even and odd chunks
-constexpr int EPI_WARP0 = 11;    // warps 11-14: drain/epilogue, one per lane quadrant
-constexpr int CPD = 2;                           // own chunks accumulated per TMEM drain
+constexpr int MMA_WARP = 9;      // warps 9 and 10 issue the MMAs of even and odd rounds
+constexpr int EPI_WARP0 = 11;    // warps 11-14: epilogue, one per lane quadrant
+constexpr int NEPI = 4;
+constexpr int NWARPS = EPI_WARP0 + NEPI;
+constexpr int NTHREADS = NWARPS * 32;
 constexpr int FLUSH = 256;                       // periods per FP64 fold of the running sums
 constexpr int TQ = 64;
 constexpr uint64_t WAIT_LIMIT = 2000000000ull;   // ns: 2 s per bounded wait
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&accf_bar[i], 1);
-      tc::mbar_init(&acce_bar[i], 4);      // 4 epilogue warps
+      tc::mbar_init(&acce_bar[i], NEPI);   // every epilogue warp drains every period
     }
     tc::mbar_init(&done_bar[0], 1);
     tc::mbar_init(&done_bar[1], 1);
@@ -199,38 +205,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp < A_WARPS) {
     // ------------------------------------------------ A transform -> TMEM
-    // The two warps of a lane quadrant take alternate chunks. Each lane reads its column's
-    // values from the chunk-major copy (each float4 read of a warp is 512 contiguous bytes;
-    // the next chunk's loads in flight while the current one is split) and the chunk's
-    // weights from the shared-memory stage.
+    // A set par (warps 4 par .. 4 par + 3, one per lane quadrant) takes the rounds g with
+    // g mod 2 == par (g counted over all items of this CTA) and owns A slot par. Each lane
+    // reads its column's values from the chunk-major copy (each float4 read of a warp is 512
+    // contiguous bytes; a ring of register buffers keeps the reads of the next chunks in
+    // flight while the current one is split) and the round's weights from the stage.
+    constexpr int RA = BF16 ? 2 : 4;            // chunks of column reads in flight
     const int qd = warp & 3, par = warp >> 2;
     const int m = qd * 32 + lane;
-    uint32_t g0 = 0;
+    uint64_t g0 = 0;                  // rounds of the previous items
     bool stop = false;
     for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       int q, j, bi, bj;
       decode_item<QF>(L, item, q, j, bi, bj);
-      const int64_t nch = (L.K[q] + CH - 1) / CH;
+      const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
       const float4* __restrict__ xc = reinterpret_cast<const float4*>(L.xT[q]) +
                                       size_t(bi) * size_t(L.kpad[q] / CH) * CH4 * TM + m;
-      const int64_t c_first = int64_t((par - int(g0 & 1)) & 1);
-      const int64_t nown = nch > c_first ? (nch - c_first + 1) / 2 : 0;
-      // own chunk o is local chunk c_first + 2 o; two register buffers, no copies: the loads
-      // of own chunk o + 1 are in flight while own chunk o is split
-      auto load = [&](int64_t o, float4 (&r)[CH4]) {
-        const int64_t c = c_first + 2 * o;
+      const int64_t r_first = int64_t((par + 2 - int(g0 & 1)) & 1);
+      const int64_t nown = nr > r_first ? (nr - r_first + 1) / 2 : 0;
+      // own chunk k (k = 0 .. SUB nown - 1) is chunk SUB (r_first + 2 (k / SUB)) + k % SUB
+      auto load = [&](int64_t k, float4 (&rg)[CH4]) {
+        const int64_t c = SUB * (r_first + 2 * (k / SUB)) + k % SUB;
 #pragma unroll
-        for (int e = 0; e < CH4; ++e) r[e] = __ldg(xc + size_t(c * CH4 + e) * TM);
+        for (int e = 0; e < CH4; ++e) rg[e] = __ldg(xc + size_t(c * CH4 + e) * TM);
       };
-      auto process = [&](int64_t o, const float4 (&xr)[CH4]) -> bool {
-        const int64_t c = c_first + 2 * o;
-        const uint32_t gg = g0 + uint32_t(c);
-        const int slot = gg % NSA, st = gg % NSB;
-        if (!warp_wait(&fullB[st], (gg / NSB) & 1, &s_abort, status) ||
-            !warp_wait(&emptyA[slot], ((gg / NSA) & 1) ^ 1, &s_abort, status))
+      // chunk k of the own rounds: the first one of a round waits for the stage and the slot,
+      // the last one signals the slot full
+      auto process = [&](int64_t k, const float4 (&xr)[CH4]) -> bool {
+        const int u = int(k % SUB);
+        const uint64_t gg = g0 + uint64_t(r_first + 2 * (k / SUB));
+        const int slot = int(gg % NSA), st = int(gg % NSB);
+        if (u == 0 && (!warp_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, status) ||
+                       !warp_wait(&emptyA[slot], (uint32_t(gg / NSA) & 1) ^ 1, &s_abort, status)))
           return false;
-        const float4* sw = reinterpret_cast<const float4*>(ring + st * STAGE_STRIDE + STAGE_BYTES);
-        const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * 32;
+        const float4* sw =
+            reinterpret_cast<const float4*>(ring + st * STAGE_STRIDE + STAGE_BYTES) + u * CH4;
+        const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * (SUB * 32) + u * 32;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {               // halves of the chunk: 8 TMEM words each
           float y[CH / 2];
@@ -248,50 +258,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tc::tmem_st8(base + h * 8, hw);
           tc::tmem_st8(base + 16 + h * 8, lw);
         }
-        tc::tmem_wait_st();
-        tc::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&fullA[slot]);
+        if (u == SUB - 1) {
+          tc::tmem_wait_st();
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&fullA[slot]);
+        }
         return true;
       };
-      float4 X0[CH4], X1[CH4];
-      if (nown > 0) load(0, X0);
-      for (int64_t o = 0; o < nown; o += 2) {
-        if (o + 1 < nown) load(o + 1, X1);
-        if (!process(o, X0)) {
-          stop = true;
-          break;
-        }
-        if (o + 1 >= nown) break;
-        if (o + 2 < nown) load(o + 2, X0);
-        if (!process(o + 1, X1)) {
-          stop = true;
-          break;
+      const int64_t nk = SUB * nown;
+      // ring of RA register buffers: the reads of the next RA - 1 own chunks are in flight
+      float4 X[RA][CH4];
+#pragma unroll
+      for (int v = 0; v < RA - 1; ++v)
+        if (v < nk) load(v, X[v]);
+      for (int64_t kb = 0; kb < nk && !stop; kb += RA) {
+#pragma unroll
+        for (int v = 0; v < RA; ++v) {
+          const int64_t k = kb + v;
+          if (k >= nk) break;
+          if (k + RA - 1 < nk) load(k + RA - 1, X[(v + RA - 1) % RA]);
+          if (!process(k, X[v])) {
+            stop = true;
+            break;
+          }
         }
       }
-      g0 += uint32_t(nch);
+      g0 += uint64_t(nr);
     }
   } else if (warp == PROD_WARP) {
     // ------------------------------------------------ B tiles and weights: bulk copies
+    // One round per stage: the SUB consecutive pre-split chunk tiles (contiguous) and the
+    // round's SUB CH weights.
     if (lane == 0) {
-      uint32_t g = 0;
+      uint64_t g = 0;
       bool ok = true;
       for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         int q, j, bi, bj;
         decode_item<QF>(L, item, q, j, bi, bj);
-        const int64_t nch = (L.K[q] + CH - 1) / CH;
-        const char* src = L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * nch * STAGE_BYTES;
+        const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+        const char* src =
+            L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * size_t(nr * SUB) * CHUNK_BYTES;
         const float* ws = QF ? nullptr : L.s[q] + size_t(j) * L.kpad[q];
-        for (int64_t c = 0; c < nch; ++c, ++g) {
-          const int st = g % NSB;
-          if (!tc::mbar_wait(&emptyB[st], ((g / NSB) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
+        for (int64_t r = 0; r < nr; ++r, ++g) {
+          const int st = int(g % NSB);
+          if (!tc::mbar_wait(&emptyB[st], (uint32_t(g / NSB) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
             ok = false;
             break;
           }
           char* dst = ring + st * STAGE_STRIDE;
-          tc::mbar_arrive_expect_tx(&fullB[st], STAGE_BYTES + (QF ? 0 : CH * 4));
-          tc::bulk_g2s(dst, src + size_t(c) * STAGE_BYTES, STAGE_BYTES, &fullB[st]);
-          if (!QF) tc::bulk_g2s(dst + STAGE_BYTES, ws + c * CH, CH * 4, &fullB[st]);
+          tc::mbar_arrive_expect_tx(&fullB[st], STAGE_BYTES + (QF ? 0 : SUB * CH * 4));
+          tc::bulk_g2s(dst, src + size_t(r) * STAGE_BYTES, STAGE_BYTES, &fullB[st]);
+          if (!QF) tc::bulk_g2s(dst + STAGE_BYTES, ws + r * SUB * CH, SUB * CH * 4, &fullB[st]);
         }
       }
       if (!ok && !s_abort) {
@@ -301,60 +319,60 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
   } else if (warp == MMA_WARP || warp == MMA_WARP + 1) {
-    // ------------------------------------------------ MMA issue (two threads, alternate chunks)
-    // Chunk g goes to accumulator g mod 2 and is issued by MMA warp g mod 2, so the barrier
-    // waits of one issuing thread overlap the tensor-core work of the other.
+    // ------------------------------------------------ MMA issue (two threads, alternate rounds)
+    // Round g goes to accumulator g mod 2 and is issued by MMA warp g mod 2 (g counted over
+    // all items), so the barrier waits of one issuing thread overlap the tensor-core work of
+    // the other. Each round is one drain period: SUB chunks x 2 K steps x 3 MMAs into a fresh
+    // accumulator.
     const uint32_t mpar = uint32_t(warp - MMA_WARP);
     if (lane == 0) {
-      uint32_t g = 0, kb = 0;       // kb: periods issued on this warp's accumulator
+      uint64_t g = 0;
+      uint32_t kb = 0;              // periods issued on this warp's accumulator
       const uint64_t desc0 = tc::smem_desc(tc::smem_u32(ring), 512, 4);
       const uint32_t d = tmem + ACC_COL + mpar * TN;
       bool ok = true;
       for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         int q, j, bi, bj;
         decode_item<QF>(L, item, q, j, bi, bj);
-        const int64_t nch = (L.K[q] + CH - 1) / CH;
-        // own chunks of this item: local c = mpar, mpar + 2, ...; CPD of them per period
-        int64_t own = 0;
-        for (int64_t c = mpar; c < nch; c += 2, ++own) {
-          const uint32_t gg = g + uint32_t(c);
-          const int st = gg % NSB, slot = gg % NSA;
-          const bool first = (own % CPD) == 0;
-          const bool last = (own % CPD) == CPD - 1 || c + 2 >= nch;
-          if (!tc::mbar_wait(&fullB[st], (gg / NSB) & 1, &s_abort, WAIT_LIMIT) ||
-              !tc::mbar_wait(&fullA[slot], (gg / NSA) & 1, &s_abort, WAIT_LIMIT) ||
-              (first && !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT))) {
+        const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+        for (int64_t r = int64_t((mpar + 2 - uint32_t(g & 1)) & 1); r < nr; r += 2) {
+          const uint64_t gg = g + uint64_t(r);
+          const int st = int(gg % NSB), slot = int(gg % NSA);
+          if (!tc::mbar_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, WAIT_LIMIT) ||
+              !tc::mbar_wait(&fullA[slot], uint32_t(gg / NSA) & 1, &s_abort, WAIT_LIMIT) ||
+              !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
             ok = false;
             break;
           }
           tc::tc_fence_after();
-          const uint32_t a = tmem + A_COL + slot * 32;
+          const uint32_t a0 = tmem + A_COL + slot * (SUB * 32);
           // descriptor address field is (addr >> 4): advancing the address adds to the low bits
           const uint64_t dst = desc0 + uint64_t((st * STAGE_STRIDE) >> 4);
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t dBh = dst + uint64_t((ks * 32) >> 4);
-            const uint64_t dBl = dst + uint64_t((B_TILE + ks * 32) >> 4);
-            const uint32_t ah = a + ks * 8, al = a + 16 + ks * 8;
-            const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
-            if (BF16) {
-              tc::mma_f16_ta(d, al, dBh, IDESC, acc0);
-              tc::mma_f16_ta(d, ah, dBl, IDESC, 1u);
-              tc::mma_f16_ta(d, ah, dBh, IDESC, 1u);
-            } else {
-              tc::mma_tf32_ta(d, al, dBh, IDESC, acc0);
-              tc::mma_tf32_ta(d, ah, dBl, IDESC, 1u);
-              tc::mma_tf32_ta(d, ah, dBh, IDESC, 1u);
+          for (int u = 0; u < SUB; ++u) {
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint64_t dBh = dst + uint64_t((u * CHUNK_BYTES + ks * 32) >> 4);
+              const uint64_t dBl = dst + uint64_t((u * CHUNK_BYTES + B_TILE + ks * 32) >> 4);
+              const uint32_t ah = a0 + u * 32 + ks * 8, al = a0 + u * 32 + 16 + ks * 8;
+              const uint32_t acc0 = (u == 0 && ks == 0) ? 0u : 1u;
+              if (BF16) {
+                tc::mma_f16_ta(d, al, dBh, IDESC, acc0);
+                tc::mma_f16_ta(d, ah, dBl, IDESC, 1u);
+                tc::mma_f16_ta(d, ah, dBh, IDESC, 1u);
+              } else {
+                tc::mma_tf32_ta(d, al, dBh, IDESC, acc0);
+                tc::mma_tf32_ta(d, ah, dBl, IDESC, 1u);
+                tc::mma_tf32_ta(d, ah, dBh, IDESC, 1u);
+              }
             }
           }
           tc::mma_commit(&emptyB[st]);
           tc::mma_commit(&emptyA[slot]);
-          if (last) {
-            tc::mma_commit(&accf_bar[mpar]);
-            ++kb;
-          }
+          tc::mma_commit(&accf_bar[mpar]);
+          ++kb;
         }
-        g += uint32_t(nch);
+        g += uint64_t(nr);
       }
       if (!ok && !s_abort) {
         s_abort = 1;
@@ -367,8 +385,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   } else if (warp >= EPI_WARP0) {
     // ------------------------------------------------ drain / epilogue
-    // Each chunk's accumulator is added into FP32 running sums kept in TMEM (round to
-    // nearest); every FLUSH chunks (staggered over the warps) the sums are folded into FP64
+    // Each round's accumulator is added into FP32 running sums kept in TMEM (round to
+    // nearest); every FLUSH rounds (staggered over the warps) the sums are folded into FP64
     // with L2 reductions.
     const int qd = warp & 3;
     const int r = qd * 32 + lane;               // tile row
@@ -376,21 +394,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     double* acc = acc64 + size_t(blockIdx.x) * TN * TM + r;   // [col][row]
     uint32_t kb[2] = {0, 0};        // periods drained per accumulator
     uint32_t gp = 0;                // periods drained in total (flush schedule)
+    uint64_t g0 = 0;                // rounds of the previous items
     bool stop = false;
     for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       int q, j, bi, bj;
       decode_item<QF>(L, item, q, j, bi, bj);
-      const int64_t nch = (L.K[q] + CH - 1) / CH;
-      const int64_t own0 = (nch + 1) / 2, own1 = nch / 2;
-      const int64_t np0 = (own0 + CPD - 1) / CPD, np1 = (own1 + CPD - 1) / CPD;
+      const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
       const int nb = L.nb[q];
 #pragma unroll 8
       for (int i = 0; i < TN; ++i) acc[size_t(i) * TM] = 0.0;
       bool sum_empty = true;
-      for (int64_t k = 0; k < np0 + np1; ++k, ++gp) {
-        // alternate the two accumulators while both have periods left
-        const int64_t m = np0 < np1 ? np0 : np1;
-        const int buf = k < 2 * m ? int(k & 1) : (np0 > np1 ? 0 : 1);
+      for (int64_t k = 0; k < nr; ++k, ++gp) {
+        const int buf = int((g0 + uint64_t(k)) & 1);
         if (!warp_wait(&accf_bar[buf], kb[buf] & 1, &s_abort, status)) {
           stop = true;
           break;
@@ -426,6 +441,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       if (stop) break;
+      g0 += uint64_t(nr);
       if (!sum_empty) {
 #pragma unroll 1
         for (int cb = 0; cb < TN / 32; ++cb) {
@@ -514,7 +530,7 @@ __global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, in
 #pragma unroll
   for (int t = 0; t < CH / 4; ++t)
     dst[size_t(t) * TM] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
-  char* hi = bsp + (size_t(cb) * nch + c) * STAGE_BYTES;
+  char* hi = bsp + (size_t(cb) * nch + c) * CHUNK_BYTES;
 #pragma unroll
   for (int kc = 0; kc < 4; ++kc) {
     uint32_t hw[4], lw[4];
@@ -571,7 +587,7 @@ __global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W
   const int n = threadIdx.x;
   const int c = cb * TN + n;
   const int J = c >> 1, b = c & 1;
-  char* hi = bsp + (size_t(cb) * nch + ch) * STAGE_BYTES;
+  char* hi = bsp + (size_t(cb) * nch + ch) * CHUNK_BYTES;
 #pragma unroll
   for (int kc = 0; kc < 4; ++kc) {
     float v[EPC];
@@ -624,7 +640,7 @@ static int64_t chunk_rows(int precision) { return precision == GW_BF16X3 ? 32 : 
 
 static void q_sizes(int64_t K, int nb, int precision, int64_t* nch, int64_t* kpad, int* nbi) {
   const int64_t ch = chunk_rows(precision);
-  *nch = (K + ch - 1) / ch;
+  *nch = ((K + ch - 1) / ch + SUB - 1) / SUB * SUB;   // whole rounds (padding chunks are zero)
   *kpad = *nch * ch;
   *nbi = (2 * nb + TM - 1) / TM;
 }
@@ -640,7 +656,7 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
     q_sizes(K[q], nb[q], precision, &nch, &kpad, &nbi);
     b += ws_round(size_t(nw) * size_t(kpad) * sizeof(float));            // weights
     b += ws_round(size_t(nbi) * TM * size_t(kpad) * sizeof(float));       // chunk-major copy
-    b += ws_round(size_t(nbi) * size_t(nch) * STAGE_BYTES);              // pre-split B tiles
+    b += ws_round(size_t(nbi) * size_t(nch) * CHUNK_BYTES);              // pre-split B tiles
   }
   return b;
 }
@@ -684,7 +700,7 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     kp[q] = kpad;
     sw[q] = static_cast<float*>(cur.take(size_t(nw) * size_t(kpad) * sizeof(float)));
     xT[q] = static_cast<float*>(cur.take(size_t(nbi) * TM * size_t(kpad) * sizeof(float)));
-    bsp[q] = static_cast<char*>(cur.take(size_t(nbi) * size_t(nch) * STAGE_BYTES));
+    bsp[q] = static_cast<char*>(cur.take(size_t(nbi) * size_t(nch) * CHUNK_BYTES));
     if (kpad == 0) continue;
     if (!sw[q] || !xT[q] || !bsp[q]) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
     int64_t blocks = std::min<int64_t>((kpad + 255) / 256, int64_t(ctx.sm_count) * 8);
@@ -735,7 +751,7 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
 static void quad_sizes(int64_t npair, int nb, int precision, int64_t* nch, int64_t* kpad,
                        int64_t* nrowp, int* nbi, int* nbj) {
   const int64_t ch = chunk_rows(precision);
-  *nch = (2 * int64_t(nb) + ch - 1) / ch;
+  *nch = ((2 * int64_t(nb) + ch - 1) / ch + SUB - 1) / SUB * SUB;   // whole rounds
   *nbj = (2 * nb + TN - 1) / TN;
   *kpad = int64_t(*nbj) * TN;                 // multiple of 128 (>= every chunk end)
   *nbi = int((npair + TM - 1) / TM);
@@ -752,7 +768,7 @@ size_t quad_tc_workspace(int nq, const int64_t* npair, const int* nb, int nw, in
     int nbi, nbj;
     quad_sizes(npair[q], nb[q], precision, &nch, &kpad, &nrowp, &nbi, &nbj);
     b += ws_round(size_t(nrowp) * size_t(kpad) * sizeof(float));
-    b += ws_round(size_t(nw) * size_t(nbj) * size_t(nch) * STAGE_BYTES);
+    b += ws_round(size_t(nw) * size_t(nbj) * size_t(nch) * CHUNK_BYTES);
   }
   return b;
 }
@@ -777,7 +793,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
     nbiv[q] = nbi;
     nbjv[q] = nbj;
     xp[q] = static_cast<float*>(cur.take(size_t(nrowp) * size_t(kpad) * sizeof(float)));
-    bsp[q] = static_cast<char*>(cur.take(size_t(nw) * size_t(nbj) * size_t(nch) * STAGE_BYTES));
+    bsp[q] = static_cast<char*>(cur.take(size_t(nw) * size_t(nbj) * size_t(nch) * CHUNK_BYTES));
     if (npair[q] == 0) continue;
     if (!xp[q] || !bsp[q]) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
     GW_CUDA_TRY(cudaMemsetAsync(c[q], 0, sizeof(double) * size_t(nw) * size_t(npair[q]), s));
@@ -793,7 +809,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
     const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbj));
     for (int j = 0; j < nw; ++j) {
       const double2* W = reinterpret_cast<const double2*>(Wc[q]) + size_t(j) * nb[q] * nb[q];
-      char* dst = bsp[q] + size_t(j) * nbj * nch * STAGE_BYTES;
+      char* dst = bsp[q] + size_t(j) * nbj * nch * CHUNK_BYTES;
       if (bf)
         k_prep_quad<true><<<pg, 128, 0, s>>>(W, nb[q], nch, dst);
       else
@@ -814,7 +830,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
       L.bsp[q] = bsp[Q];
       L.s[q] = nullptr;
       L.cq[q] = c[Q];
-      L.bsp_jstride[q] = int64_t(nbjv[Q]) * nchv[Q] * STAGE_BYTES;
+      L.bsp_jstride[q] = int64_t(nbjv[Q]) * nchv[Q] * CHUNK_BYTES;
       L.nrow[q] = npair[Q];
       L.K[q] = npair[Q] > 0 ? 2 * int64_t(nb[Q]) : 0;
       L.kpad[q] = kp[Q];
