@@ -206,6 +206,9 @@ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
 __device__ __forceinline__ double cabs_(cplx a) { return hypot(a.x, a.y); }
 __device__ __forceinline__ cplx clog_(cplx a) { return mk(log(hypot(a.x, a.y)), atan2(a.y, a.x)); }
 
+// 1/k for k = 1..60 (the series below multiply by these instead of dividing)
+__constant__ double kInvInt[60] = {1.0, 0.5, 0.3333333333333333, 0.25, 0.2, 0.16666666666666666, 0.14285714285714285, 0.125, 0.1111111111111111, 0.1, 0.09090909090909091, 0.08333333333333333, 0.07692307692307693, 0.07142857142857142, 0.06666666666666667, 0.0625, 0.058823529411764705, 0.05555555555555555, 0.05263157894736842, 0.05, 0.047619047619047616, 0.045454545454545456, 0.043478260869565216, 0.041666666666666664, 0.04, 0.038461538461538464, 0.037037037037037035, 0.03571428571428571, 0.034482758620689655, 0.03333333333333333, 0.03225806451612903, 0.03125, 0.030303030303030304, 0.029411764705882353, 0.02857142857142857, 0.027777777777777776, 0.02702702702702703, 0.02631578947368421, 0.02564102564102564, 0.025, 0.024390243902439025, 0.023809523809523808, 0.023255813953488372, 0.022727272727272728, 0.022222222222222223, 0.021739130434782608, 0.02127659574468085, 0.020833333333333332, 0.02040816326530612, 0.02, 0.0196078431372549, 0.019230769230769232, 0.018867924528301886, 0.018518518518518517, 0.01818181818181818, 0.017857142857142856, 0.017543859649122806, 0.017241379310344827, 0.01694915254237288, 0.016666666666666666};
+
 constexpr double SERIES_R = 0.3;
 constexpr int SERIES_N = 36;
 
@@ -216,12 +219,16 @@ __device__ void moments(cplx z0, cplx b, double H, cplx I[4]) {
     cplx term = mk(1.0, 0.0);
     cplx nr = mk(-r.x, -r.y);
     cplx s0 = mk(0, 0), s1 = mk(0, 0), s2 = mk(0, 0), s3 = mk(0, 0);
+    const double rr = cabs_(r);
+    double tmag = 1.0;
     for (int m = 0; m < SERIES_N; ++m) {
-      s0 = s0 + (1.0 / (m + 1)) * term;
-      s1 = s1 + (1.0 / (m + 2)) * term;
-      s2 = s2 + (1.0 / (m + 3)) * term;
-      s3 = s3 + (1.0 / (m + 4)) * term;
+      s0 = s0 + kInvInt[m] * term;
+      s1 = s1 + kInvInt[m + 1] * term;
+      s2 = s2 + kInvInt[m + 2] * term;
+      s3 = s3 + kInvInt[m + 3] * term;
       term = term * nr;
+      tmag *= rr;
+      if (tmag < 1e-18) break;     // |r|^(m+1) below the FP64 resolution of the sums (>= 1/4)
     }
     cplx iz = cdiv(mk(1.0, 0.0), z0);
     double h1 = H, h2 = H * H, h3 = h2 * H, h4 = h3 * H;
@@ -246,9 +253,13 @@ __device__ cplx tail_integral(cplx A, double sgn, double X) {
   cplx rho = cdiv(A, mk(0.0, sgn * X));
   if (cabs_(rho) < 0.5) {
     cplx term = mk(1.0, 0.0), nr = mk(-rho.x, -rho.y), s = mk(0, 0);
+    const double rr = cabs_(rho);
+    double tmag = 1.0;
     for (int m = 0; m < 56; ++m) {
-      s = s + (1.0 / (m + 2)) * term;
+      s = s + kInvInt[m + 1] * term;
       term = term * nr;
+      tmag *= rr;
+      if (tmag < 1e-18) break;     // |rho|^(m+1) below the FP64 resolution of the sum (>= 1/2)
     }
     return cdiv(s, mk(0.0, sgn * X * X));
   }
@@ -334,6 +345,7 @@ __device__ cplx pair_integral(const double* __restrict__ c, int64_t stride, int 
 
 constexpr int CTHREADS = 256;
 struct ConvLaunch {
+  int64_t item0[SMAXQ + 1];   // first (pair, output frequency) item of q
   const double* c[SMAXQ];
   const int* state[SMAXQ];
   const double* eps[SMAXQ];
@@ -342,57 +354,38 @@ struct ConvLaunch {
   int nq;
 };
 
+// One thread per (pair, output frequency): the pair's spline-and-tail integral, weighted by
+// w_q, added into Sigma of the pair's state by FP64 atomics (Sigma zeroed first unless
+// accumulating).
 __global__ void __launch_bounds__(CTHREADS) k_convolve(ConvLaunch L, int nw, OmegaArr om,
-                                                       OmegaArr om_out, int nw_out,
-                                                       double* __restrict__ sigma, int accumulate,
+                                                       OmegaArr om_out, int nw_out, int nsig,
+                                                       double* __restrict__ sigma,
                                                        unsigned* status) {
-  const int sidx = blockIdx.x, i = blockIdx.y;
   __shared__ double lam[GW_MAX_NW], h[GW_MAX_NW];
-  __shared__ double red_x[CTHREADS], red_y[CTHREADS];
   if (threadIdx.x < nw) lam[threadIdx.x] = om.v[threadIdx.x] / (1.0 + om.v[threadIdx.x]);
   __syncthreads();
   if (threadIdx.x < nw - 1) h[threadIdx.x] = lam[threadIdx.x + 1] - lam[threadIdx.x];
   __syncthreads();
-  const double w = om_out.v[i];
   const double wN = om.v[nw - 1];
-  double sx = 0.0, sy = 0.0;
-  for (int q = 0; q < L.nq; ++q) {
-    const int64_t np = L.npair[q];
-    double px = 0.0, py = 0.0;
-    for (int64_t p = threadIdx.x; p < np; p += CTHREADS) {
-      if (L.state[q][p] != sidx) continue;
-      double e = L.eps[q][p];
-      if (!(e != 0.0) || !isfinite(e)) {
-        raise_status(status, ST_EINVAL);
-        continue;
-      }
-      cplx v = pair_integral(L.c[q] + p, np, nw, lam, h, wN, w, e);
-      px += v.x;
-      py += v.y;
+  const double f = -1.0 / (2.0 * 3.14159265358979323846);
+  const int64_t total = L.item0[L.nq];
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    int q = 0;
+    while (q + 1 < L.nq && e >= L.item0[q + 1]) ++q;
+    const int64_t loc = e - L.item0[q];
+    const int64_t p = loc / nw_out;
+    const int i = int(loc % nw_out);
+    const int st = L.state[q][p];
+    const double ep = L.eps[q][p];
+    if (!(ep != 0.0) || !isfinite(ep) || st < 0 || st >= nsig) {
+      raise_status(status, ST_EINVAL);
+      continue;
     }
-    sx += L.wq[q] * px;
-    sy += L.wq[q] * py;
-  }
-  red_x[threadIdx.x] = sx;
-  red_y[threadIdx.x] = sy;
-  __syncthreads();
-  for (int off = CTHREADS / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off) {
-      red_x[threadIdx.x] += red_x[threadIdx.x + off];
-      red_y[threadIdx.x] += red_y[threadIdx.x + off];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double f = -1.0 / (2.0 * 3.14159265358979323846);
-    double2* out = reinterpret_cast<double2*>(sigma) + size_t(sidx) * nw_out + i;
-    double2 v = make_double2(f * red_x[0], f * red_y[0]);
-    if (accumulate) {
-      double2 o = *out;
-      v.x += o.x;
-      v.y += o.y;
-    }
-    *out = v;
+    const cplx v = pair_integral(L.c[q] + p, L.npair[q], nw, lam, h, wN, om_out.v[i], ep);
+    double2* out = reinterpret_cast<double2*>(sigma) + size_t(st) * nw_out + i;
+    atomicAdd(&out->x, f * L.wq[q] * v.x);
+    atomicAdd(&out->y, f * L.wq[q] * v.y);
   }
 }
 
@@ -410,20 +403,26 @@ int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const O
                  const double* const* c, const int* const* pair_state, const double* const* eps,
                  int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
                  cudaStream_t s, const DeviceCtx& ctx) {
+  if (!accumulate)
+    GW_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * 2 * size_t(nsig) * nw_out, s));
   for (int q0 = 0; q0 < nq; q0 += SMAXQ) {
     int n = std::min(SMAXQ, nq - q0);
     ConvLaunch L{};
     L.nq = n;
+    L.item0[0] = 0;
     for (int q = 0; q < n; ++q) {
       L.c[q] = c[q0 + q];
       L.state[q] = pair_state[q0 + q];
       L.eps[q] = eps[q0 + q];
       L.npair[q] = npair[q0 + q];
       L.wq[q] = wq[q0 + q];
+      L.item0[q + 1] = L.item0[q] + npair[q0 + q] * nw_out;
     }
-    dim3 grid(nsig, nw_out);
-    k_convolve<<<grid, CTHREADS, 0, s>>>(L, nw, om, om_out, nw_out, sigma,
-                                         (accumulate || q0 > 0) ? 1 : 0, ctx.status);
+    const int64_t total = L.item0[n];
+    if (total == 0) continue;
+    const int64_t blocks = std::min<int64_t>((total + CTHREADS - 1) / CTHREADS, int64_t(ctx.sm_count) * 16);
+    k_convolve<<<unsigned(blocks), CTHREADS, 0, s>>>(L, nw, om, om_out, nw_out, nsig, sigma,
+                                                     ctx.status);
     GW_LAUNCH_CHECK("k_convolve");
   }
   return GW_OK;
