@@ -220,3 +220,30 @@ def test_tc_batched_uneven_full_size_sampled(gw):
         ref = OP.polarization(Mc, wl.delta(iq), om, wl.prefactor)
         err = rel_fro(got, ref)
         assert err <= 1e-6, (iq, nb, K, err)
+
+
+@pytest.mark.slow
+def test_tc_supercell_one_kpoint_sampled(gw):
+    """The supercell workload (N_b = 4096, 20 frequencies, BF16x3): the transitions of one of
+    its 8 k points (K = 768,000, the sub-problem the oracle can afford), projections
+    generated on the device, 48 sampled basis indices (their full cross block, diagonal
+    included) against the oracle."""
+    wl = S.supercell()
+    om = wl.omega()
+    nb = wl.nb[0]
+    K1 = wl.nocc * wl.nunocc[0]                       # transitions with k = 0
+    M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[0], 0, K1, nb, dtype=torch.complex64)
+    d = wl.delta(0)[:K1]
+    P = gw.polarization([M], [T(d)], om, wl.prefactor, "bf16x3")[0]
+    gw.check()
+    del M
+    rng = np.random.default_rng(4096)
+    cols = np.sort(rng.choice(nb, size=48, replace=False))
+    got = P[:, cols][:, :, cols].cpu().numpy()
+    del P
+    torch.cuda.empty_cache()
+    Mc = wl.m_rows(0, rows=np.arange(K1), cols=cols).astype(np.complex64).astype(np.complex128)
+    ref = OP.polarization(Mc, d, om, wl.prefactor)
+    err = rel_fro(got, ref)
+    assert err <= 1e-6, err
+    assert np.array_equal(got, np.conj(np.transpose(got, (0, 2, 1))))
