@@ -226,6 +226,22 @@ int gw_sigma_div(int nw, const double* omega_host, const double* head_dev, doubl
                  gw_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Exchange self-energy (Eq. HFterm_MB in the Coulomb eigenbasis, Sec. III.C, plus the
+ * divergent term of Eq. exchange_div in its erf form, Sec. III.D). FP64:
+ *   Sigma_x[s] = - sum_q w_q sum_{p: state(p) = s, eps_p < 0} sum_mu v_mu |Msig_p,mu|^2
+ *                - f_s (4 pi / volume) cbz,   f_s = 1 if eps_state[s] < 0, else 0.
+ *   Msig_dev[q] [npair_q][nb_q] complex (m_dtype), pair_state_dev[q] [npair_q] in [0, nsig),
+ *   eps_dev[q] [npair_q] energies of the partner bands n' (occupied when negative),
+ *   v_dev[q] [nb_q] Coulomb eigenvalues, eps_state_dev [nsig], cbz the BZ constant
+ *   (gw_bz_constant_sc), volume the crystal volume; sigma_x_dev [nsig] double output
+ *   (overwritten). A pair state outside [0, nsig) is reported by gw_check as GW_EINVAL. */
+int gw_sigma_x(int nq, const double* wq_host, const int64_t* npair_host, const int* nb_host,
+               const void* const* Msig_dev, int m_dtype, const int* const* pair_state_dev,
+               const double* const* eps_dev, const double* const* v_dev, int nsig,
+               const double* eps_state_dev, double cbz, double volume, double* sigma_x_dev,
+               gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * a7. Analytic continuation (Eq. modelf): fit f(z) = sum_p a_p / (z - w_p) to each
  * curve Sigma(i omega_j) by FP64 Levenberg-Marquardt (Marquardt's diagonal
  * scaling; cost 1/2 sum_j |f(i omega_j) - Sigma_j|^2).

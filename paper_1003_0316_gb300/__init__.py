@@ -74,6 +74,8 @@ _sig("gw_bz_constant_sc", _i32, _f64, _i32, _f64, _P(_f64), _vp, _sz, _vp)
 _sig("gw_sigma_div_workspace", _sz, _i32, _i32)
 _sig("gw_sigma_div", _i32, _i32, _P(_f64), _vp, _f64, _f64, _i32, _vp, _i32, _P(_f64), _vp, _vp,
      _sz, _vp)
+_sig("gw_sigma_x", _i32, _i32, _P(_f64), _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp), _P(_vp),
+     _i32, _vp, _f64, _f64, _vp, _vp)
 _sig("gw_synth_projections", _i32, _u64, _u32, _u32, _i64, _i64, _i32, _i32, _vp, _vp)
 
 
@@ -266,6 +268,22 @@ def sigma_c(wq, Msigs, pair_states, epss, Wcs, omega, omega_out, nsig, precision
     _raise(_lib.gw_sigma_c(nq, _arr(_f64, wq), _arr(_i64, npairs), _arr(_i32, nbs), _ptrs(Msigs),
                            _dtype_code(Msigs[0]), _ptrs(pair_states), _ptrs(epss), nw, om,
                            _ptrs(Wcs), nwo, omo, nsig, out.data_ptr(), prec, wsp, wsn, _stream()))
+    return out
+
+
+# ---------------------------------------------------------- exchange --------
+def sigma_x(wq, Msigs, pair_states, epss, vs, nsig, eps_state, cbz, volume, out=None):
+    """Exchange self-energy per state (FP64): the regular sum over occupied partners plus
+    the divergent term of occupied states."""
+    nq = len(Msigs)
+    dev = Msigs[0].device
+    if out is None:
+        out = torch.empty(nsig, dtype=torch.float64, device=dev)
+    _raise(_lib.gw_sigma_x(nq, _arr(_f64, wq), _arr(_i64, [m.shape[0] for m in Msigs]),
+                           _arr(_i32, [m.shape[1] for m in Msigs]), _ptrs(Msigs),
+                           _dtype_code(Msigs[0]), _ptrs(pair_states), _ptrs(epss), _ptrs(vs), nsig,
+                           eps_state.data_ptr(), float(cbz), float(volume), out.data_ptr(),
+                           _stream()))
     return out
 
 

@@ -460,3 +460,30 @@ int gw_sigma_div(int nw, const double* omega_host, const double* head_dev, doubl
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int gw_sigma_x(int nq, const double* wq_host, const int64_t* npair_host, const int* nb_host,
+               const void* const* Msig_dev, int m_dtype, const int* const* pair_state_dev,
+               const double* const* eps_dev, const double* const* v_dev, int nsig,
+               const double* eps_state_dev, double cbz, double volume, double* sigma_x_dev,
+               gw_stream_t stream) {
+  if (nq < 1 || !wq_host || !npair_host || !nb_host) return set_error(GW_EINVAL, "nq < 1 or NULL host array");
+  if (m_dtype != GW_C128 && m_dtype != GW_C64) return set_error(GW_EINVAL, "m_dtype=%d", m_dtype);
+  if (nsig < 1 || !sigma_x_dev || !eps_state_dev) return set_error(GW_EINVAL, "nsig < 1 or NULL output");
+  if (!std::isfinite(cbz) || !(volume > 0.0)) return set_error(GW_EINVAL, "bad BZ constant or volume");
+  if (!Msig_dev || !pair_state_dev || !eps_dev || !v_dev) return set_error(GW_EINVAL, "NULL pointer array");
+  for (int q = 0; q < nq; ++q) {
+    if (npair_host[q] < 0 || nb_host[q] < 1) return set_error(GW_EINVAL, "bad sizes for q=%d", q);
+    if (!std::isfinite(wq_host[q])) return set_error(GW_EINVAL, "wq[%d] not finite", q);
+    if (npair_host[q] > 0 && (!Msig_dev[q] || !pair_state_dev[q] || !eps_dev[q] || !v_dev[q]))
+      return set_error(GW_EINVAL, "NULL pointer for q=%d", q);
+  }
+  DeviceCtx ctx;
+  int rc = device_ctx(&ctx);
+  if (rc) return rc;
+  return sigma_x(nq, wq_host, npair_host, nb_host, Msig_dev, m_dtype, pair_state_dev, eps_dev, v_dev,
+                 nsig, eps_state_dev, cbz, volume, sigma_x_dev, stream, ctx);
+}
+
+}  // extern "C"

@@ -110,6 +110,12 @@ int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const O
                  int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
                  cudaStream_t s, const DeviceCtx& ctx);
 
+// exchange self-energy
+int sigma_x(int nq, const double* wq, const int64_t* npair, const int* nb, const void* const* M,
+            int dtype, const int* const* state, const double* const* eps, const double* const* v,
+            int nsig, const double* eps_state, double cbz, double volume, double* out,
+            cudaStream_t s, const DeviceCtx& ctx);
+
 // a4 (q = Gamma)
 size_t gamma_workspace(int nb, int nw);
 int gamma_screened_w(int nb, int nw, const double* v, const double* Paug, double* Wc,

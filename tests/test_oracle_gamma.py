@@ -104,3 +104,24 @@ def test_sigma_div_single_pole_closed_form():
             1j * om[None, :] - eps[:, None] - Om * np.sign(eps)[:, None])
         errs.append(np.abs(got - ref).max() / np.abs(ref).max())
     assert errs[1] < errs[0] and errs[1] < 2e-3, errs
+
+
+def test_exchange_oracle_pins():
+    """Eq. HFterm_MB in the eigenbasis: a pair with one nonzero projection component gives
+    -w v_mu |m_mu|^2; unoccupied n' and the divergent term of an unoccupied state vanish;
+    the divergent term of an occupied state is -(4 pi / V) C; scaling M by c scales the
+    regular part by |c|^2."""
+    from oracle import exchange as OX
+    v = np.array([3.0, 2.0, 0.5])
+    M = np.zeros((3, 3), dtype=np.complex128)
+    M[0, 1] = 0.3 - 0.4j                     # |m|^2 = 0.25 on mu = 1
+    M[1, 2] = 2.0j                           # unoccupied partner: excluded
+    M[2, 0] = 1.0                            # state 1, occupied partner
+    eps = np.array([-0.2, 0.7, -1.0])
+    st = np.array([0, 0, 1])
+    got = OX.sigma_x([0.5], [M], [st], [eps], [v], 2, np.array([0.3, 0.4]), 10.0, 100.0)
+    assert np.allclose(got, [-0.5 * 2.0 * 0.25, -0.5 * 3.0 * 1.0], rtol=1e-15)
+    div = OX.sigma_x([0.5], [np.zeros((3, 3))], [st], [eps], [v], 2, np.array([-0.3, 0.4]), 10.0, 100.0)
+    assert np.allclose(div, [-FOUR_PI / 100.0 * 10.0, 0.0], rtol=1e-15)
+    s2 = OX.sigma_x([0.5], [(1 - 2j) * M], [st], [eps], [v], 2, np.array([0.3, 0.4]), 10.0, 100.0)
+    assert np.allclose(s2, 5.0 * got, rtol=1e-14)
