@@ -475,6 +475,57 @@ def run_case_herk(args):
                       "tflops": fl / (ms * 1e-3) / 1e12}), flush=True)
 
 
+def run_case_fit(args):
+    """Analytic continuation at the scale of 2e5 self-energy curves on 24 frequencies: the
+    plain FP64 Levenberg-Marquardt fit, BF16 inference of the learned start, the fit from
+    the learned start alone and combined with the default start; the network is first trained
+    in FP32 on 20,000 other curves. Model curves (synth_inputs.model_sigma_curves) stand in for
+    the pipeline's. Prints one line of timings, not a bench line."""
+    import torch
+    import paper_1003_0316_gb300 as gw
+    om = S.omega_mesh(24)
+    n = 200000
+    y, sg = S.model_sigma_curves(S.SEED_BASE + 104, n, om)
+    ytr, _ = S.model_sigma_curves(S.SEED_BASE + 105, 20000, om)
+    Y = torch.as_tensor(y, device="cuda")
+    sign = torch.as_tensor(sg, device="cuda")
+    w = gw.mlp_init(11)
+    steps, batch = 2000, 512
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    losses = gw.train_mlp(torch.as_tensor(ytr, device="cuda"), om, w, steps=steps, batch=batch,
+                          lr=2e-3, seed=1)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    out = {"case": "fit", "curves": n, "n_omega": 24, "npole": 2,
+           "train": {"steps": steps, "batch": batch, "ms": train_ms,
+                     "samples_per_s": steps * batch / (train_ms * 1e-3),
+                     "loss_first50": float(losses[:50].mean()), "loss_last200": float(losses[-200:].mean())}}
+    gw.mlp_forward(Y[:1024], w)
+    torch.cuda.synchronize()
+    e0.record()
+    gw.mlp_forward(Y, w)
+    e1.record()
+    torch.cuda.synchronize()
+    out["mlp_inference"] = {"ms": e0.elapsed_time(e1), "curves_per_s": n / (e0.elapsed_time(e1) * 1e-3)}
+    for meth in ("plain", "mlp_only", "mlp"):
+        gw.continue_fit(Y[:256], om, npole=2, sign=sign[:256], method=meth, mlp=w)
+        torch.cuda.synchronize()
+        e0.record()
+        prm, cost, it, st = gw.continue_fit(Y, om, npole=2, sign=sign, method=meth, mlp=w)
+        e1.record()
+        torch.cuda.synchronize()
+        gw.check()
+        ms = e0.elapsed_time(e1)
+        out[meth] = {"ms": ms, "curves_per_s": n / (ms * 1e-3),
+                     "mean_lm_iterations": float(it.double().mean()),
+                     "median_cost": float(cost.median()),
+                     "status_counts": [int((st == k).sum()) for k in range(3)]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,11 +533,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
-    ap.add_argument("--case", default=None, choices=["herk"],
+    ap.add_argument("--case", default=None, choices=["herk", "fit"],
                     help="run one profiling case instead of the bench step")
     args = ap.parse_args()
     if args.case == "herk":
         run_case_herk(args)
+        return
+    if args.case == "fit":
+        run_case_fit(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
