@@ -108,6 +108,15 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host,
                     double* const* P_dev, int precision,
                     void* ws_dev, size_t ws_bytes, gw_stream_t stream);
 
+/* Memory waves for many q points (no counterpart in the paper: a scheduling aid for inputs
+ * larger than device memory). Assigns each q to a wave so that, per wave, the projections
+ * (complex128 for GW_FP64, complex64 otherwise), the gw_polarization workspace of the wave and
+ * the P outputs fit in budget_bytes; first-fit decreasing by footprint. Host only.
+ *   wave_of_q [nq] output (0-based), *nwaves_out the number of waves. GW_EINVAL if one q
+ *   alone exceeds the budget. */
+int gw_plan_waves(int nq, const int64_t* K_host, const int* nb_host, int nw, int precision,
+                  size_t budget_bytes, int* wave_of_q, int* nwaves_out);
+
 /* ---------------------------------------------------------------------------
  * a3. Dielectric matrix and correlation part of the screened interaction in the
  * Coulomb eigenbasis (Eqs. dielec_MB, screen_MB and W^c = W - v, Sec. III.C):

@@ -76,6 +76,7 @@ _sig("gw_sigma_div", _i32, _i32, _P(_f64), _vp, _f64, _f64, _i32, _vp, _i32, _P(
      _sz, _vp)
 _sig("gw_sigma_x", _i32, _i32, _P(_f64), _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp), _P(_vp),
      _i32, _vp, _f64, _f64, _vp, _vp)
+_sig("gw_plan_waves", _i32, _i32, _P(_i64), _P(_i32), _i32, _i32, _sz, _P(_i32), _P(_i32))
 _sig("gw_synth_projections", _i32, _u64, _u32, _u32, _i64, _i64, _i32, _i32, _vp, _vp)
 
 
@@ -173,6 +174,18 @@ def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=No
                                 _ptrs(deltas), fptr, float(prefactor), nw, om, _ptrs(out), prec,
                                 wsp, wsn, _stream()))
     return out
+
+
+def plan_waves(Ks, nbs, nw, precision, budget_bytes):
+    """Group q points into memory waves (first-fit decreasing); returns a list of waves, each
+    a list of q indices in increasing order."""
+    nq = len(Ks)
+    wave = (_i32 * nq)()
+    nwaves = _i32(0)
+    _raise(_lib.gw_plan_waves(nq, _arr(_i64, Ks), _arr(_i32, nbs), nw,
+                              PRECISIONS.get(precision, precision), int(budget_bytes), wave,
+                              ctypes.byref(nwaves)))
+    return [[q for q in range(nq) if wave[q] == w] for w in range(nwaves.value)]
 
 
 # ---------------------------------------------------------------- a3 --------

@@ -487,3 +487,16 @@ int gw_sigma_x(int nq, const double* wq_host, const int64_t* npair_host, const i
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int gw_plan_waves(int nq, const int64_t* K_host, const int* nb_host, int nw, int precision,
+                  size_t budget_bytes, int* wave_of_q, int* nwaves_out) {
+  int rc = validate_pol(nq, K_host, nb_host, precision);
+  if (rc) return rc;
+  if (nw < 1 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [1, %d]", nw, GW_MAX_NW);
+  if (!wave_of_q || !nwaves_out) return set_error(GW_EINVAL, "NULL output");
+  return plan_waves(nq, K_host, nb_host, nw, precision, budget_bytes, wave_of_q, nwaves_out);
+}
+
+}  // extern "C"

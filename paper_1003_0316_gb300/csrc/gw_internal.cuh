@@ -110,6 +110,10 @@ int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const O
                  int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
                  cudaStream_t s, const DeviceCtx& ctx);
 
+// memory waves
+int plan_waves(int nq, const int64_t* K, const int* nb, int nw, int precision, size_t budget,
+               int* wave_of_q, int* nwaves);
+
 // exchange self-energy
 int sigma_x(int nq, const double* wq, const int64_t* npair, const int* nb, const void* const* M,
             int dtype, const int* const* state, const double* const* eps, const double* const* v,
