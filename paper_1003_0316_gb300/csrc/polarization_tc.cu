@@ -120,10 +120,13 @@ __device__ __forceinline__ uint32_t sw64_off(int n, int kc) {
   return uint32_t((n >> 3) * 512 + (n & 7) * 64 + ((kc ^ ((n & 7) >> 1)) << 4));
 }
 
+// Round an FP32 value to TF32 (10 explicit mantissa bits), to nearest with ties away from
+// zero, on the bit pattern: adding half a TF32 unit in the last place (bit 12) and clearing the
+// 13 dropped bits rounds the magnitude up exactly when the dropped part is at least half a unit
+// (a carry into the exponent is the correct result). Valid for every finite value below the
+// FP32 maximum, which covers the scaled projections.
 __device__ __forceinline__ uint32_t tf32_rna(float y) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(y));
-  return r;
+  return (__float_as_uint(y) + 0x1000u) & 0xFFFFE000u;
 }
 
 // y -> (hi, lo) pieces packed as 32-bit TMEM / shared-memory words.

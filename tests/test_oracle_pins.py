@@ -291,3 +291,27 @@ def test_bf16_rounding_matches_torch_and_packing_round_trips():
     q = OM.unpack(OM.pack(p))
     assert all(np.array_equal(p[k], q[k]) for k in OM.ORDER)
     assert OM.pack(p).size == 128 * 48 + 128 + 128 * 128 + 128 + 8 * 128 + 8
+
+
+def test_tf32_rounding_rule_by_bits_matches_definition():
+    """The split-precision kernel rounds FP32 to TF32 by (bits + 0x1000) & 0xFFFFE000. Checked
+    here against the definition (nearest TF32 value, ties away from zero), computed exactly
+    with rationals, on random values, exact ties and values next to powers of two."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    x = (rng.normal(size=2000) * 10.0 ** rng.uniform(-20, 20, size=2000)).astype(np.float32)
+    b = x.view(np.uint32)
+    ties = ((b & np.uint32(0xFFFFE000)) | np.uint32(0x1000)).view(np.float32)
+    below2 = np.nextafter(np.float32(2.0) ** np.arange(-10, 10, dtype=np.float32), np.float32(0))
+    vals = np.concatenate([x, ties, below2, -ties])
+    got = ((vals.view(np.uint32).astype(np.uint64) + 0x1000) & 0xFFFFE000).astype(np.uint32).view(np.float32)
+    for v, g in zip(vals, got):
+        f = Fraction(float(v))
+        e = np.frexp(np.float32(abs(v)))[1]          # |v| in [2^(e-1), 2^e)
+        ulp = Fraction(2) ** (int(e) - 1 - 10)       # TF32 spacing there
+        q = abs(f) / ulp
+        n = int(q)
+        if q - n >= Fraction(1, 2):
+            n += 1
+        ref = n * ulp * (1 if f >= 0 else -1)
+        assert Fraction(float(g)) == ref, (v, g, float(ref))
