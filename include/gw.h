@@ -290,6 +290,13 @@ int gw_mlp_train_step(int n, const double* omega_host, const double* sigma_dev,
                       float* mlp_dev, float* grad_dev, float* m_dev, float* v_dev,
                       float lr, int step, float* loss_dev, gw_stream_t stream);
 
+/* Diagnostic (no counterpart in the paper): one device thread waits, with a wall-time limit
+ * of limit_ms (0 < limit_ms <= 1000), on an mbarrier that nothing arrives on, the same bounded
+ * wait that the pipelined kernels use; on expiry it records a timeout in the status word and
+ * returns. The next gw_check then returns GW_ETIMEOUT (and clears the word); the context stays
+ * usable. For testing the timeout path without hanging the GPU. */
+int gw_selftest_bounded_wait(double limit_ms, gw_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Synthetic-input generator (not part of the method): fills projections with
  * complex normals (Philox4x32-10 keyed by seed, counter (element index, q, tid),

@@ -77,6 +77,7 @@ _sig("gw_sigma_div", _i32, _i32, _P(_f64), _vp, _f64, _f64, _i32, _vp, _i32, _P(
 _sig("gw_sigma_x", _i32, _i32, _P(_f64), _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp), _P(_vp),
      _i32, _vp, _f64, _f64, _vp, _vp)
 _sig("gw_plan_waves", _i32, _i32, _P(_i64), _P(_i32), _i32, _i32, _sz, _P(_i32), _P(_i32))
+_sig("gw_selftest_bounded_wait", _i32, _f64, _vp)
 _sig("gw_synth_projections", _i32, _u64, _u32, _u32, _i64, _i64, _i32, _i32, _vp, _vp)
 
 
@@ -122,6 +123,11 @@ def _ws(nbytes, device):
         return None, _vp(None), 0
     buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
     return buf, _vp(buf.data_ptr()), int(nbytes)
+
+
+def selftest_bounded_wait(limit_ms=5.0):
+    """Launch a wait that nothing ends; the next check() raises GW_ETIMEOUT."""
+    _raise(_lib.gw_selftest_bounded_wait(float(limit_ms), _stream()))
 
 
 def check(stream=None):

@@ -500,3 +500,16 @@ int gw_plan_waves(int nq, const int64_t* K_host, const int* nb_host, int nw, int
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int gw_selftest_bounded_wait(double limit_ms, gw_stream_t stream) {
+  if (!(limit_ms > 0.0 && limit_ms <= 1000.0))
+    return set_error(GW_EINVAL, "limit_ms=%g outside (0, 1000]", limit_ms);
+  DeviceCtx ctx;
+  int rc = device_ctx(&ctx);
+  if (rc) return rc;
+  return selftest_bounded_wait(limit_ms, stream, ctx);
+}
+
+}  // extern "C"

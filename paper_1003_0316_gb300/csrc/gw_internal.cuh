@@ -110,6 +110,9 @@ int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const O
                  int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
                  cudaStream_t s, const DeviceCtx& ctx);
 
+// diagnostic of the bounded waits
+int selftest_bounded_wait(double limit_ms, cudaStream_t s, const DeviceCtx& ctx);
+
 // memory waves
 int plan_waves(int nq, const int64_t* K, const int* nb, int nw, int precision, size_t budget,
                int* wave_of_q, int* nwaves);
