@@ -452,6 +452,8 @@ def run_case_herk(args):
     iq, K, nb = 1, 102400, wl.nb[1]
     cdt = torch.complex128 if args.precision == "fp64" else torch.complex64
     M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[iq], 0, K, nb, dtype=cdt)
+    if args.real:
+        M = M.real.contiguous()          # real projections of an inversion-symmetric system
     d = torch.as_tensor(wl.delta(iq)[:K], device="cuda")
     om = wl.omega()
     P = [torch.empty((wl.nw, nb, nb), dtype=torch.complex128, device="cuda")]
@@ -469,9 +471,10 @@ def run_case_herk(args):
     torch.cuda.synchronize()
     gw.check()
     ms = e0.elapsed_time(e1) / args.steps
-    fl = 4.0 * K * nb * (nb + 1) * wl.nw
+    # algorithmic flop: complex Hermitian 4 K N_b (N_b + 1), real symmetric K N_b (N_b + 1)
+    fl = (1.0 if args.real else 4.0) * K * nb * (nb + 1) * wl.nw
     print(json.dumps({"case": "herk", "K": K, "N_b": nb, "n_omega": wl.nw,
-                      "precision": args.precision, "ms": ms,
+                      "precision": args.precision, "real_projections": bool(args.real), "ms": ms,
                       "tflops": fl / (ms * 1e-3) / 1e12}), flush=True)
 
 
@@ -593,6 +596,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
+    ap.add_argument("--real", action="store_true",
+                    help="--case herk with real projections (inversion-symmetric systems)")
     ap.add_argument("--case", default=None, choices=["herk", "fit", "batched"],
                     help="run one profiling case instead of the bench step")
     args = ap.parse_args()

@@ -50,7 +50,10 @@ enum gw_status {
   GW_EUNSUPPORTED = 8   /* combination not built (e.g. precision for this dtype) */
 };
 
-enum gw_dtype { GW_C128 = 0, GW_C64 = 1 };
+/* GW_R32: real float32 projections (inversion-symmetric systems, Sec. II: real basis and
+ * wave functions), for the tensor-core precisions of gw_polarization; P is then real
+ * symmetric, computed as one real SYRK of half the size and stored with zero imaginary parts. */
+enum gw_dtype { GW_C128 = 0, GW_C64 = 1, GW_R32 = 2 };
 
 /* Arithmetic of the P and Sigma contractions. GW_FP64: double precision on the
  * FP64 pipe (M must be GW_C128). GW_TF32X3 ("FP32-split"): tensor-core products of

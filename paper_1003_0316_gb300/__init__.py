@@ -19,7 +19,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 GW_OK, GW_EINVAL, GW_EWORKSPACE, GW_ECUDA, GW_ENONFINITE, GW_ENOTHPD, GW_ETIMEOUT, \
     GW_ENOCONV, GW_EUNSUPPORTED = range(9)
-GW_C128, GW_C64 = 0, 1
+GW_C128, GW_C64, GW_R32 = 0, 1, 2
 GW_FP64, GW_TF32X3, GW_BF16X3 = 0, 1, 2
 GW_FIT_PLAIN, GW_FIT_MLP, GW_FIT_MLP_ONLY = 0, 1, 2
 FIT_METHODS = {"plain": GW_FIT_PLAIN, "mlp": GW_FIT_MLP, "mlp_only": GW_FIT_MLP_ONLY}
@@ -140,7 +140,9 @@ def _dtype_code(t):
         return GW_C128
     if t.dtype == torch.complex64:
         return GW_C64
-    raise TypeError(f"projections must be complex128 or complex64, got {t.dtype}")
+    if t.dtype == torch.float32:
+        return GW_R32
+    raise TypeError(f"projections must be complex128, complex64 or float32, got {t.dtype}")
 
 
 # ---------------------------------------------------------------- a1 --------

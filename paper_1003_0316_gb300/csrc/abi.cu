@@ -154,8 +154,8 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const voi
     return set_error(GW_EINVAL, "NULL M_dev, delta_dev or P_dev array");
   if (precision == GW_FP64 && m_dtype != GW_C128)
     return set_error(GW_EUNSUPPORTED, "GW_FP64 needs complex128 projections");
-  if (precision != GW_FP64 && m_dtype != GW_C64)
-    return set_error(GW_EUNSUPPORTED, "tensor-core precisions need complex64 projections");
+  if (precision != GW_FP64 && m_dtype != GW_C64 && m_dtype != GW_R32)
+    return set_error(GW_EUNSUPPORTED, "tensor-core precisions need complex64 or real float32 projections");
   if (!std::isfinite(prefactor)) return set_error(GW_EINVAL, "prefactor not finite");
   std::vector<PolQ> qs(nq);
   for (int q = 0; q < nq; ++q) {
@@ -177,7 +177,8 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const voi
   if ((rc = device_ctx(&ctx))) return rc;
   if (precision == GW_FP64)
     return pol_fp64(nq, qs.data(), prefactor, nw, om, ws_dev, ws_bytes, stream, ctx);
-  return pol_tc(nq, qs.data(), prefactor, nw, om, precision, ws_dev, ws_bytes, stream, ctx);
+  return pol_tc(nq, qs.data(), prefactor, nw, om, precision, m_dtype == GW_R32, ws_dev, ws_bytes,
+                stream, ctx);
 }
 
 size_t gw_screened_w_workspace(int nq, const int* nb_host, int nw) {
@@ -228,8 +229,8 @@ static int validate_pairs(int nq, const int64_t* npair, const int* nb, int preci
     return set_error(GW_EINVAL, "unknown precision %d", precision);
   if (precision == GW_FP64 && m_dtype != GW_C128)
     return set_error(GW_EUNSUPPORTED, "GW_FP64 needs complex128 projections");
-  if (precision != GW_FP64 && m_dtype != GW_C64)
-    return set_error(GW_EUNSUPPORTED, "tensor-core precisions need complex64 projections");
+  if (precision != GW_FP64 && m_dtype != GW_C64 && m_dtype != GW_R32)
+    return set_error(GW_EUNSUPPORTED, "tensor-core precisions need complex64 or real float32 projections");
   return GW_OK;
 }
 

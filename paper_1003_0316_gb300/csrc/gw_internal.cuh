@@ -84,7 +84,7 @@ int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, vo
              size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
 size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision);
 int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
-           void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
+           bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
 
 // a3
 size_t dielectric_workspace(int nq, const int* nb, int nw);

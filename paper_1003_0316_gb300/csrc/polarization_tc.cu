@@ -163,9 +163,12 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-template <bool BF16, bool QF>
+// MODE: 0 complex polarization, 1 quadratic form (Sigma pair coefficients), 2 real
+// polarization (real projections, inversion-symmetric systems: P = -G directly).
+template <bool BF16, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_herk_tc(const __grid_constant__ TcLaunch L, double* __restrict__ acc64, unsigned* status) {
+  constexpr bool QF = MODE == 1;
   constexpr int CH = BF16 ? 32 : 16;          // transitions per chunk (64 bytes of K)
   constexpr int CH4 = CH / 4;                 // float4 per chunk column
   constexpr uint32_t IDESC = tc::instr_desc(BF16 ? 1u : 2u, TM, TN);
@@ -468,6 +471,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           part = fma(double(xv), acc[size_t(i) * TM], part);
         }
         if (p < L.nrow[q]) atomicAdd(L.cq[q] + size_t(j) * L.nrow[q] + p, part);
+      } else if (MODE == 2) {
+        // real projections: P_IJ = -G_IJ (real symmetric)
+        const int I = bi * TM + r;
+        double2* P = L.P[q] + size_t(j) * nb * nb;
+#pragma unroll 4
+        for (int i = 0; i < TN; ++i) {
+          const int J = bj * TN + i;
+          if (I < nb && J < nb && I <= J) {
+            const double g = -acc[size_t(i) * TM];
+            P[size_t(I) * nb + J] = make_double2(g, 0.0);
+            if (I != J) P[size_t(J) * nb + I] = make_double2(g, 0.0);
+          }
+        }
       } else {
         // complex combination of rows (2I, 2I+1) held by lanes (2l, 2l+1)
         const int R = bi * TM + r;
@@ -514,14 +530,22 @@ __global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, in
   const int cb = blockIdx.y;               // column block (grid.y <= 65535)
   const int64_t c = blockIdx.x;             // chunk (grid.x: up to 2^31 - 1)
   const int tid = threadIdx.x;
-  // float2 loads: a row of the FP32 view has 2 N_b floats, so 8-byte alignment always holds
-  // (16-byte alignment only for even N_b)
+  // pairs of columns: one 8-byte load when the row length ncol is even (the FP32 view of
+  // complex projections: 2 N_b floats per row), two 4-byte loads when it is odd (real
+  // projections with odd N_b, rows only 4-byte aligned)
   for (int idx = tid; idx < CH * (TM / 2); idx += 128) {
     const int t = idx / (TM / 2), c2 = idx % (TM / 2);
     const int64_t row = c * CH + t;
     const int col = cb * TM + 2 * c2;
     float2 v = make_float2(0.f, 0.f);
-    if (row < K && col < ncol) v = __ldg(reinterpret_cast<const float2*>(x + row * ncol + col));
+    if (row < K && col < ncol) {
+      if ((ncol & 1) == 0) {
+        v = __ldg(reinterpret_cast<const float2*>(x + row * ncol + col));
+      } else {
+        v.x = __ldg(x + row * ncol + col);
+        if (col + 1 < ncol) v.y = __ldg(x + row * ncol + col + 1);
+      }
+    }
     *reinterpret_cast<float2*>(&tile[t][2 * c2]) = v;
   }
   __syncthreads();
@@ -631,8 +655,9 @@ __global__ void k_abs_weights_f32(int64_t K, int64_t kpad, const double* __restr
   }
 }
 
-int tile_count(int nb, int* nbi_out) {
-  int nbi = (2 * nb + TM - 1) / TM;   // TM == TN: square tiles, upper triangle
+// ncol: columns of the real operand x (2 N_b for complex projections, N_b for real ones)
+int tile_count(int ncol, int* nbi_out) {
+  int nbi = (ncol + TM - 1) / TM;     // TM == TN: square tiles, upper triangle
   if (nbi_out) *nbi_out = nbi;
   return nbi * (nbi + 1) / 2;
 }
@@ -641,11 +666,11 @@ int tile_count(int nb, int* nbi_out) {
 
 static int64_t chunk_rows(int precision) { return precision == GW_BF16X3 ? 32 : 16; }
 
-static void q_sizes(int64_t K, int nb, int precision, int64_t* nch, int64_t* kpad, int* nbi) {
+static void q_sizes(int64_t K, int ncol, int precision, int64_t* nch, int64_t* kpad, int* nbi) {
   const int64_t ch = chunk_rows(precision);
   *nch = ((K + ch - 1) / ch + SUB - 1) / SUB * SUB;   // whole rounds (padding chunks are zero)
   *kpad = *nch * ch;
-  *nbi = (2 * nb + TM - 1) / TM;
+  *nbi = (ncol + TM - 1) / TM;
 }
 
 size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision) {
@@ -656,7 +681,7 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
   for (int q = 0; q < nq; ++q) {
     int64_t nch, kpad;
     int nbi;
-    q_sizes(K[q], nb[q], precision, &nch, &kpad, &nbi);
+    q_sizes(K[q], 2 * nb[q], precision, &nch, &kpad, &nbi);   // complex size: an upper bound
     b += ws_round(size_t(nw) * size_t(kpad) * sizeof(float));            // weights
     b += ws_round(size_t(nbi) * TM * size_t(kpad) * sizeof(float));       // chunk-major copy
     b += ws_round(size_t(nbi) * size_t(nch) * CHUNK_BYTES);              // pre-split B tiles
@@ -664,32 +689,33 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
   return b;
 }
 
-template <bool BF16, bool QF>
+template <bool BF16, int MODE>
 static int prepare_kernel(const DeviceCtx& ctx, size_t smem) {
   static bool done[64] = {};
   if (done[ctx.device]) return GW_OK;
-  GW_CUDA_TRY(cudaFuncSetAttribute(k_herk_tc<BF16, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  GW_CUDA_TRY(cudaFuncSetAttribute(k_herk_tc<BF16, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    int(smem)));
   done[ctx.device] = true;
   return GW_OK;
 }
 
-template <bool QF>
+template <int MODE>
 static int launch_tc(const TcLaunch& L, bool bf, unsigned grid, size_t smem, double* acc64,
                      cudaStream_t s, const DeviceCtx& ctx) {
-  int rc = bf ? prepare_kernel<true, QF>(ctx, smem) : prepare_kernel<false, QF>(ctx, smem);
+  int rc = bf ? prepare_kernel<true, MODE>(ctx, smem) : prepare_kernel<false, MODE>(ctx, smem);
   if (rc) return rc;
   if (bf)
-    k_herk_tc<true, QF><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
+    k_herk_tc<true, MODE><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
   else
-    k_herk_tc<false, QF><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
+    k_herk_tc<false, MODE><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
   GW_LAUNCH_CHECK("k_herk_tc");
   return GW_OK;
 }
 
 int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
-           void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
+           bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
   const bool bf = precision == GW_BF16X3;
+  const int cpb = real ? 1 : 2;          // real operand columns per basis function
   WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
   double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
   if (!acc64) return set_error(GW_EWORKSPACE, "internal: tensor-core workspace too small");
@@ -699,7 +725,7 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
   for (int q = 0; q < nq; ++q) {
     int64_t nch, kpad;
     int nbi;
-    q_sizes(qs[q].K, qs[q].nb, precision, &nch, &kpad, &nbi);
+    q_sizes(qs[q].K, cpb * qs[q].nb, precision, &nch, &kpad, &nbi);
     kp[q] = kpad;
     sw[q] = static_cast<float*>(cur.take(size_t(nw) * size_t(kpad) * sizeof(float)));
     xT[q] = static_cast<float*>(cur.take(size_t(nbi) * TM * size_t(kpad) * sizeof(float)));
@@ -713,11 +739,11 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbi));
     if (nch > 2147483647LL) return set_error(GW_EINVAL, "too many transitions for one q");
     if (bf)
-      k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K, 2 * qs[q].nb,
-                                         kpad, nch, xT[q], bsp[q]);
+      k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K,
+                                         cpb * qs[q].nb, kpad, nch, xT[q], bsp[q]);
     else
-      k_prep_tc<false><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K, 2 * qs[q].nb,
-                                          kpad, nch, xT[q], bsp[q]);
+      k_prep_tc<false><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K,
+                                          cpb * qs[q].nb, kpad, nch, xT[q], bsp[q]);
     GW_LAUNCH_CHECK("k_prep_tc");
   }
   const size_t smem = NSB * STAGE_STRIDE + 1024;
@@ -736,7 +762,7 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
       L.K[q] = Q.K;
       L.kpad[q] = kp[q0 + q];
       L.nb[q] = Q.nb;
-      L.ntile[q] = tile_count(Q.nb, &L.nbi[q]);
+      L.ntile[q] = tile_count(cpb * Q.nb, &L.nbi[q]);
       L.nbj[q] = L.nbi[q];
       L.item0[q] = item;
       item += int64_t(L.ntile[q]) * nw;
@@ -744,7 +770,8 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     L.item0[n] = item;
     if (item == 0) continue;
     unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
-    int rc = launch_tc<false>(L, bf, grid, smem, acc64, s, ctx);
+    int rc = real ? launch_tc<2>(L, bf, grid, smem, acc64, s, ctx)
+                  : launch_tc<0>(L, bf, grid, smem, acc64, s, ctx);
     if (rc) return rc;
   }
   return GW_OK;
@@ -847,7 +874,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
     L.item0[n] = item;
     if (item == 0) continue;
     unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
-    int rc = launch_tc<true>(L, bf, grid, smem, acc64, s, ctx);
+    int rc = launch_tc<1>(L, bf, grid, smem, acc64, s, ctx);
     if (rc) return rc;
   }
   return GW_OK;

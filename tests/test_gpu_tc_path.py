@@ -247,3 +247,20 @@ def test_tc_supercell_one_kpoint_sampled(gw):
     err = rel_fro(got, ref)
     assert err <= 1e-6, err
     assert np.array_equal(got, np.conj(np.transpose(got, (0, 2, 1))))
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("nb", [64, 150, 37])
+def test_tc_real_projections(gw, prec, nb):
+    """Inversion-symmetric systems (real projections, float32): P real symmetric from one real
+    SYRK of half the width, against the oracle on the same data."""
+    wl = S.tiny(nb=nb, nocc=4, nunocc=30, mesh=(2, 2, 2), nw=5, seed=nb + 7)
+    om = wl.omega()
+    Mr = wl.m_full(0).real.astype(np.float32)
+    P = gw.polarization([T(Mr)], [T(wl.delta(0))], om, wl.prefactor, prec)[0]
+    gw.check()
+    P = P.cpu().numpy()
+    ref = OP.polarization(Mr.astype(np.float64).astype(np.complex128), wl.delta(0), om, wl.prefactor)
+    assert np.all(P.imag == 0)
+    assert np.array_equal(P, np.transpose(P, (0, 2, 1)))
+    assert rel_fro(P, ref) <= BOUND[prec]
