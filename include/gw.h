@@ -275,6 +275,17 @@ int gw_continue(int ncurve, int nw, const double* omega_host, const double* sigm
                 double* params_dev, double* cost_dev, int* iters_dev, int* status_dev,
                 gw_stream_t stream);
 
+/* Quasiparticle energies (Eq. quasipart_corr with the continued Sigma^c of Eq. modelf), FP64:
+ * E = eps + Sigma_x + Re f(E) - v_xc by Newton's method from E = eps (|dE| <= 1e-14 max(1,|E|),
+ * at most 100 steps), f(E) = sum_p a_p / (E - w_p) (the real part is the same for the conjugated
+ * form that Eq. modelf prescribes for Re w < 0).
+ *   params_dev [n][npole][4] (Re a, Im a, Re w, Im w) as written by gw_continue; eps_dev,
+ *   sigx_dev, vxc_dev [n]; outputs E_dev [n], Z_dev [n] = 1 / (1 - Re f'(E)) (or NULL),
+ *   status_dev [n] (0 converged, 1 step limit; or NULL). */
+int gw_qp_solve(int n, int npole, const double* params_dev, const double* eps_dev,
+                const double* sigx_dev, const double* vxc_dev, double* E_dev, double* Z_dev,
+                int* status_dev, gw_stream_t stream);
+
 /* Learned initialiser: MLP 48 -> 128 -> 128 -> 8 (SiLU), input the curve on 24 nodes
  * scaled by s = max |Sigma_j|, output (Re a/s, Im a/s, Re w, Im w) for 2 poles.
  * Packed FP32 parameter layout: W1[128][48], b1[128], W2[128][128], b2[128],

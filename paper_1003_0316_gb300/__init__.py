@@ -78,6 +78,7 @@ _sig("gw_sigma_x", _i32, _i32, _P(_f64), _P(_i64), _P(_i32), _P(_vp), _i32, _P(_
      _i32, _vp, _f64, _f64, _vp, _vp)
 _sig("gw_plan_waves", _i32, _i32, _P(_i64), _P(_i32), _i32, _i32, _sz, _P(_i32), _P(_i32))
 _sig("gw_selftest_bounded_wait", _i32, _f64, _vp)
+_sig("gw_qp_solve", _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("gw_synth_projections", _i32, _u64, _u32, _u32, _i64, _i64, _i32, _i32, _vp, _vp)
 
 
@@ -370,6 +371,19 @@ def continue_fit(sigma, omega, npole=2, sign=None, method="plain", mlp=None):
                             params.data_ptr(), cost.data_ptr(), iters.data_ptr(), status.data_ptr(),
                             _stream()))
     return params, cost, iters, status
+
+
+def qp_solve(params, eps, sigx, vxc):
+    """Quasiparticle energies by Newton's method on the continued self-energy; returns
+    (E, Z, status) per state."""
+    n, npole = params.shape[0], params.shape[1]
+    dev = params.device
+    E = torch.empty(n, dtype=torch.float64, device=dev)
+    Z = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    _raise(_lib.gw_qp_solve(n, npole, params.data_ptr(), eps.data_ptr(), sigx.data_ptr(),
+                            vxc.data_ptr(), E.data_ptr(), Z.data_ptr(), st.data_ptr(), _stream()))
+    return E, Z, st
 
 
 def mlp_param_count():

@@ -514,3 +514,19 @@ int gw_selftest_bounded_wait(double limit_ms, gw_stream_t stream) {
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int gw_qp_solve(int n, int npole, const double* params_dev, const double* eps_dev,
+                const double* sigx_dev, const double* vxc_dev, double* E_dev, double* Z_dev,
+                int* status_dev, gw_stream_t stream) {
+  if (n < 0) return set_error(GW_EINVAL, "n < 0");
+  if (npole < 1 || npole > 5) return set_error(GW_EINVAL, "npole=%d outside [1, 5]", npole);
+  if (n == 0) return GW_OK;
+  if (!params_dev || !eps_dev || !sigx_dev || !vxc_dev || !E_dev)
+    return set_error(GW_EINVAL, "NULL params, eps, sigx, vxc or E pointer");
+  return qp_solve(n, npole, params_dev, eps_dev, sigx_dev, vxc_dev, E_dev, Z_dev, status_dev,
+                  stream);
+}
+
+}  // extern "C"

@@ -110,6 +110,10 @@ int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const O
                  int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
                  cudaStream_t s, const DeviceCtx& ctx);
 
+// quasiparticle energies
+int qp_solve(int n, int npole, const double* params, const double* eps, const double* sigx,
+             const double* vxc, double* E, double* Z, int* status, cudaStream_t s);
+
 // diagnostic of the bounded waits
 int selftest_bounded_wait(double limit_ms, cudaStream_t s, const DeviceCtx& ctx);
 

@@ -315,3 +315,24 @@ def test_tf32_rounding_rule_by_bits_matches_definition():
             n += 1
         ref = n * ulp * (1 if f >= 0 else -1)
         assert Fraction(float(g)) == ref, (v, g, float(ref))
+
+
+def test_qp_newton_single_real_pole_closed_form():
+    """One pole with real residue a and real position w: E - c - a/(E - w) = 0 is the quadratic
+    (E - c)(E - w) = a, roots (c + w +- sqrt((c - w)^2 + 4a)) / 2; Newton from eps lands on the
+    root on eps's side of the pole; Z = 1 / (1 + a/(E - w)^2)."""
+    from oracle import qp as OQ
+    cases = [(-0.3, 0.1, 0.05, -1.2, 0.02), (0.4, -0.2, 0.1, 1.5, -0.03), (0.2, 0.0, 0.0, 2.0, 0.3)]
+    for eps, sx, vxc, w, a in cases:
+        c = eps + sx - vxc
+        disc = np.sqrt((c - w) ** 2 + 4 * a)
+        roots = np.array([(c + w + disc) / 2, (c + w - disc) / 2])
+        want = roots[np.argmin(np.abs(roots - eps))]
+        prm = np.array([[[a, 0.0, w, 0.0]]])
+        E, Z, st = OQ.qp_solve(prm, [eps], [sx], [vxc])
+        assert st[0] == 0
+        assert abs(E[0] - want) <= 1e-13 * max(1, abs(want))
+        assert np.isclose(Z[0], 1.0 / (1.0 + a / (want - w) ** 2), rtol=1e-12)
+    # no self-energy: E = eps + Sigma_x - v_xc, Z = 1
+    E, Z, _ = OQ.qp_solve(np.zeros((1, 2, 4)) + np.array([0, 0, 3.0, -1.0]), [0.3], [-0.5], [-0.4])
+    assert abs(E[0] - 0.2) <= 1e-15 and abs(Z[0] - 1.0) <= 1e-15
