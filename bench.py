@@ -589,6 +589,80 @@ def run_case_batched(args):
                       "algorithmic_flop": flops}), flush=True)
 
 
+def run_case_extrapolar(args):
+    """Extrapolar correction on one q of the 4x4x4-mesh workload with 600 unoccupied bands of
+    which 400 are kept (K = 409,600 kept transitions, N_b = 600, 1,024 occupied states, 16
+    frequencies, 16 Sigma states): the corrected polarization against the plain one on the
+    same kept transitions (the correction's overhead), and the Sigma^c correction. The
+    projections are generated on the device and the completeness integrals formed from them
+    there (outside the timed region). Prints one line of timings, not a bench line."""
+    import torch
+    import paper_1003_0316_gb300 as gw
+    base = S.medium_mixed()
+    wl = S.Workload(name="extrapolar_nk64_nb600", seed=base.seed, mesh=base.mesh,
+                    qs=(base.qs[1],), wq=(1.0,), nb=(600,), nocc=16, nunocc=(600,), nw=16)
+    wl.states = base.states
+    nb, nu, nkeep, prec = 600, 600, 400, args.precision
+    nkn = wl.nk * wl.nocc
+    om, pref = wl.omega(), wl.prefactor
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    Mf = gw.synth_projections(wl.seed, S.TID_M, wl.qs[0], 0, wl.K(0), nb, dtype=cdt)
+    M3 = Mf.view(nkn, nu, nb)
+    C = torch.matmul(M3.transpose(1, 2), M3.conj())
+    Mk = M3[:, :nkeep, :].reshape(nkn * nkeep, nb).contiguous()
+    del Mf, M3
+    ebar = float(wl.eps_unocc()[:, :nkeep].max()) + 8.0
+    dbar_kn = ebar - wl.eps_occ().reshape(-1)
+    t = np.arange(wl.K(0))
+    kept = t[(t % nu) < nkeep]
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    d, dbt, dbk = dev(wl.delta(0)[kept]), dev(dbar_kn[kept // nu]), dev(dbar_kn)
+    K = len(kept)
+    P = [torch.empty((wl.nw, nb, nb), dtype=torch.complex128, device="cuda")]
+    ws = torch.empty(gw.polarization_workspace([K], [nb], wl.nw, prec), dtype=torch.uint8,
+                     device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        gw.check()
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        gw.check()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_p = timed(lambda: gw.polarization([Mk], [d], om, pref, prec, out=P, ws=ws))
+    ms_ex = timed(lambda: gw.polarization_extrapolar([Mk], [d], [dbt], [C], [dbk], om, pref, prec,
+                                                     out=P, ws=ws))
+    # Sigma^c side: W^c from the corrected P, S^s from the pair projections of all 616 partners
+    Wc = gw.screened_w(P, [dev(wl.v(0))])[0]
+    ps, eps = wl.sigma_pairs(0)
+    nsig, nbnd = len(wl.sigma_states()), wl.n_pair_bands(0)
+    Msf = gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[0], 0, nsig * nbnd, nb,
+                               dtype=torch.complex128).view(nsig, nbnd, nb)
+    Sm = torch.matmul(Msf.conj().transpose(1, 2), Msf)
+    pk = np.arange(len(ps))[(np.arange(len(ps)) % nbnd) < wl.nocc + nkeep]
+    Msk = Msf.reshape(nsig * nbnd, nb)[dev(pk)].contiguous()
+    psk = dev(ps[pk].astype(np.int32))
+    ck = gw.sigma_pair_coeffs([Msk], [Wc], precision="fp64")[0]
+    sig = torch.zeros((nsig, wl.nw), dtype=torch.complex128, device="cuda")
+    ms_sx = timed(lambda: gw.sigma_extrapolar([1.0], [Sm], [Wc], [psk], [ck], [ebar], om, om,
+                                              sig))
+    ebytes = 1 if prec == "fp64" else 0.5
+    c_bytes = nkn * nb * (nb + 1) / 2 * 16 * ebytes + 2 * wl.nw * nb * nb * 16
+    print(json.dumps({"case": "extrapolar", "K_kept": K, "N_b": nb, "n_occ_states": nkn,
+                      "n_omega": wl.nw, "precision": prec, "polarization_ms": ms_p,
+                      "polarization_extrapolar_ms": ms_ex,
+                      "overhead_ms": ms_ex - ms_p, "overhead_frac": (ms_ex - ms_p) / ms_p,
+                      "completeness_algorithmic_bytes": c_bytes,
+                      "sigma_extrapolar_ms": ms_sx, "n_sigma_states": nsig}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,7 +672,7 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
     ap.add_argument("--real", action="store_true",
                     help="--case herk with real projections (inversion-symmetric systems)")
-    ap.add_argument("--case", default=None, choices=["herk", "fit", "batched"],
+    ap.add_argument("--case", default=None, choices=["herk", "fit", "batched", "extrapolar"],
                     help="run one profiling case instead of the bench step")
     args = ap.parse_args()
     if args.case == "herk":
@@ -609,6 +683,9 @@ def main():
         return
     if args.case == "batched":
         run_case_batched(args)
+        return
+    if args.case == "extrapolar":
+        run_case_extrapolar(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

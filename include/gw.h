@@ -111,6 +111,35 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host,
                     double* const* P_dev, int precision,
                     void* ws_dev, size_t ws_bytes, gw_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Extrapolar correction of the polarization (Sec. V, the paragraph on the convergence with
+ * the number of bands; the scheme of Bruneval and Gonze). The unoccupied sum of Eq. polar_MB
+ * is cut at a band N'; every band n' > N' is put at one energy e_bar (the paper takes 16 Ry
+ * above the highest kept band), and the completeness of the one-particle states turns the
+ * sum over those bands into a full-band integral minus the kept bands:
+ *   P^EX_IJ = sum_t [w_tj(Delta_t) - w_tj(Delta_bar_t)] M_{t,I} conj(M_{t,J})
+ *           + sum_kn w_j(Delta_bar_kn) C^kn_IJ,
+ * w the a1 weight (prefactor and symmetry weight included), kn an occupied state (k, n),
+ * Delta_bar_kn = e_bar - e_n(k), Delta_bar_t = Delta_bar of the occupied state of t, and
+ * C^kn_IJ = <phi_nk| M_I conj(M_J) |phi_nk>, the full-band sum of M_{kn n',I} conj(M_{kn n',J}).
+ * Arguments as gw_polarization, plus per q:
+ *   delta_bar_dev[q] [K_q] double > 0 (Delta_bar_t of each kept transition),
+ *   nkn_host[q] number of occupied states, C_dev[q] [nkn][N_b][N_b] Hermitian, of the
+ *   projections' element type (complex128 for GW_FP64, complex64, or float32 for GW_R32),
+ *   delta_bar_kn_dev[q] [nkn] double > 0, f_kn_dev (may be NULL, or f_kn_dev[q]) [nkn] double.
+ * P_dev[q] is overwritten with P^EX. The completeness term reads the upper triangle of each
+ * C^kn and adds it and its Hermitian mirror; complex128 input is summed in FP64, complex64
+ * and float32 input in FP32 per chunk of 32 states with an error-free two-float running sum.
+ * Workspace: gw_polarization_workspace(). Delta_bar <= 0 is reported by gw_check as GW_EINVAL. */
+int gw_polarization_extrapolar(int nq, const int64_t* K_host, const int* nb_host,
+                               const void* const* M_dev, int m_dtype,
+                               const double* const* delta_dev, const double* const* delta_bar_dev,
+                               const double* const* f_dev, const int64_t* nkn_host,
+                               const void* const* C_dev, const double* const* delta_bar_kn_dev,
+                               const double* const* f_kn_dev, double prefactor, int nw,
+                               const double* omega_host, double* const* P_dev, int precision,
+                               void* ws_dev, size_t ws_bytes, gw_stream_t stream);
+
 /* Memory waves for many q points (no counterpart in the paper: a scheduling aid for inputs
  * larger than device memory). Assigns each q to a wave so that, per wave, the projections
  * (complex128 for GW_FP64, complex64 otherwise), the gw_polarization workspace of the wave and
@@ -189,6 +218,26 @@ int gw_sigma_convolve(int nq, const double* wq_host, const int64_t* npair_host,
                       const int* const* pair_state_dev, const double* const* eps_dev,
                       int nw_out, const double* omega_out_host, int nsig,
                       double* sigma_dev, gw_stream_t stream);
+
+/* Extrapolar correction of Sigma^c (Sec. V, band convergence, with the full W^c rather than a
+ * plasmon-pole model): the partner bands n' > N' of every state s sit at e_bar_q, so they act
+ * as one extra pair per (q, s) with energy e_bar_q and coefficient
+ *   cbar_{q,j,s} = sum_IJ W^c_IJ(q, i omega_j) S^{q,s}_IJ - sum_{p: state(p) = s} c_{q,j,p},
+ * S^{q,s}_IJ = <phi_s| conj(M_I) M_J |phi_s> (the full-band sum of conj(m_I) m_J over the
+ * partners of s at k0 + q), which is convolved over frequency by the a6 rule and ADDED to
+ * sigma_dev. Per q: S_dev[q] [nsig][N_b][N_b] complex128 (Hermitian), Wc_dev[q]
+ * [nw][N_b][N_b] complex128, c_dev[q] [nw][npair_q] the kept pairs' coefficients
+ * (gw_sigma_pair_coeffs), pair_state_dev[q] [npair_q], ebar_host[q] > 0.
+ * sigma_dev [nsig][nw_out] complex128 (accumulated); cbar_dev [nq][nw][nsig] double output or
+ * NULL. FP64. Workspace: gw_sigma_extrapolar_workspace(). */
+size_t gw_sigma_extrapolar_workspace(int nq, int nw, int nsig);
+int gw_sigma_extrapolar(int nq, const double* wq_host, const int* nb_host, int nsig,
+                        const double* const* S_dev, int nw, const double* omega_host,
+                        const double* const* Wc_dev, const int64_t* npair_host,
+                        const int* const* pair_state_dev, const double* const* c_dev,
+                        const double* ebar_host, int nw_out, const double* omega_out_host,
+                        double* sigma_dev, double* cbar_dev, void* ws_dev, size_t ws_bytes,
+                        gw_stream_t stream);
 
 /* a5 + a6 in one call (the Sigma^c step of the hot path). */
 size_t gw_sigma_workspace(int nq, const int64_t* npair_host, const int* nb_host, int nw,

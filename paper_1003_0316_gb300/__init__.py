@@ -52,6 +52,12 @@ _sig("gw_transition_weights", _i32, _i64, _vp, _vp, _f64, _i32, _P(_f64), _vp, _
 _sig("gw_polarization_workspace", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32)
 _sig("gw_polarization", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp), _f64,
      _i32, _P(_f64), _P(_vp), _i32, _vp, _sz, _vp)
+_sig("gw_polarization_extrapolar", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp),
+     _P(_vp), _P(_i64), _P(_vp), _P(_vp), _P(_vp), _f64, _i32, _P(_f64), _P(_vp), _i32, _vp, _sz,
+     _vp)
+_sig("gw_sigma_extrapolar_workspace", _sz, _i32, _i32, _i32)
+_sig("gw_sigma_extrapolar", _i32, _i32, _P(_f64), _P(_i32), _i32, _P(_vp), _i32, _P(_f64),
+     _P(_vp), _P(_i64), _P(_vp), _P(_vp), _P(_f64), _i32, _P(_f64), _vp, _vp, _vp, _sz, _vp)
 _sig("gw_screened_w_workspace", _sz, _i32, _P(_i32), _i32)
 _sig("gw_screened_w", _i32, _i32, _P(_i32), _i32, _P(_vp), _P(_vp), _P(_vp), _vp, _sz, _vp)
 _sig("gw_screened_w_noalloc", _i32, _i32, _i32, _vp, _vp, _vp, _vp)
@@ -185,6 +191,35 @@ def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=No
     return out
 
 
+def polarization_extrapolar(Ms, deltas, dbars, Cs, dbar_kns, omega, prefactor, precision="fp64",
+                            fs=None, f_kns=None, out=None, ws=None):
+    """P^EX[q]: the kept transitions at their own energies and every band beyond the cutoff
+    at e_bar (extrapolar correction, Sec. V). dbars[q] [K_q] Delta_bar of each transition's
+    occupied state, Cs[q] [nkn][N_b][N_b] the completeness integrals (same element type as
+    Ms), dbar_kns[q] [nkn]."""
+    prec = PRECISIONS.get(precision, precision)
+    om, nw = _om(omega)
+    nq = len(Ms)
+    Ks = [m.shape[0] for m in Ms]
+    nbs = [m.shape[1] for m in Ms]
+    nkns = [c.shape[0] for c in Cs]
+    dev = Ms[0].device
+    if out is None:
+        out = [torch.empty((nw, nb, nb), dtype=torch.complex128, device=dev) for nb in nbs]
+    need = polarization_workspace(Ks, nbs, nw, prec)
+    if ws is None:
+        wsb, wsp, wsn = _ws(need, dev)
+    else:
+        wsb, wsp, wsn = ws, _vp(ws.data_ptr()), ws.numel()
+    fptr = _ptrs(fs) if fs is not None else None
+    fkptr = _ptrs(f_kns) if f_kns is not None else None
+    _raise(_lib.gw_polarization_extrapolar(
+        nq, _arr(_i64, Ks), _arr(_i32, nbs), _ptrs(Ms), _dtype_code(Ms[0]), _ptrs(deltas),
+        _ptrs(dbars), fptr, _arr(_i64, nkns), _ptrs(Cs), _ptrs(dbar_kns), fkptr,
+        float(prefactor), nw, om, _ptrs(out), prec, wsp, wsn, _stream()))
+    return out
+
+
 def plan_waves(Ks, nbs, nw, precision, budget_bytes):
     """Group q points into memory waves (first-fit decreasing); returns a list of waves, each
     a list of q indices in increasing order."""
@@ -291,6 +326,28 @@ def sigma_c(wq, Msigs, pair_states, epss, Wcs, omega, omega_out, nsig, precision
                            _dtype_code(Msigs[0]), _ptrs(pair_states), _ptrs(epss), nw, om,
                            _ptrs(Wcs), nwo, omo, nsig, out.data_ptr(), prec, wsp, wsn, _stream()))
     return out
+
+
+def sigma_extrapolar(wq, Ss, Wcs, pair_states, cs, ebars, omega, omega_out, sigma, cbar=None):
+    """Adds the extrapolar correction of Sigma^c (Sec. V) to sigma [nsig][nw_out]: per (q, s)
+    one extra pair at e_bar_q with coefficient sum_IJ W^c_IJ S^s_IJ minus the kept pairs'
+    coefficients cs[q] [nw][npair_q]. Ss[q] [nsig][N_b][N_b] complex128. Returns (sigma,
+    cbar [nq][nw][nsig])."""
+    om, nw = _om(omega)
+    omo, nwo = _om(omega_out)
+    nq = len(Ss)
+    nsig = Ss[0].shape[0]
+    nbs = [x.shape[1] for x in Ss]
+    npairs = [c.shape[1] for c in cs]
+    dev = Ss[0].device
+    if cbar is None:
+        cbar = torch.empty((nq, nw, nsig), dtype=torch.float64, device=dev)
+    wsb, wsp, wsn = _ws(_lib.gw_sigma_extrapolar_workspace(nq, nw, nsig), dev)
+    _raise(_lib.gw_sigma_extrapolar(nq, _arr(_f64, wq), _arr(_i32, nbs), nsig, _ptrs(Ss), nw, om,
+                                    _ptrs(Wcs), _arr(_i64, npairs), _ptrs(pair_states), _ptrs(cs),
+                                    _arr(_f64, ebars), nwo, omo, sigma.data_ptr(), cbar.data_ptr(),
+                                    wsp, wsn, _stream()))
+    return sigma, cbar
 
 
 # ---------------------------------------------------------- exchange --------

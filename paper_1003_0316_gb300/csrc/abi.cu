@@ -142,10 +142,12 @@ size_t gw_polarization_workspace(int nq, const int64_t* K_host, const int* nb_ho
   return pol_tc_workspace(nq, K_host, nb_host, nw, precision);
 }
 
-int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const void* const* M_dev,
-                    int m_dtype, const double* const* delta_dev, const double* const* f_dev,
-                    double prefactor, int nw, const double* omega_host, double* const* P_dev,
-                    int precision, void* ws_dev, size_t ws_bytes, gw_stream_t stream) {
+static int polarization_impl(int nq, const int64_t* K_host, const int* nb_host,
+                             const void* const* M_dev, int m_dtype, const double* const* delta_dev,
+                             const double* const* dbar_dev, const double* const* f_dev,
+                             double prefactor, int nw, const double* omega_host,
+                             double* const* P_dev, int precision, void* ws_dev, size_t ws_bytes,
+                             gw_stream_t stream) {
   int rc = validate_pol(nq, K_host, nb_host, precision);
   if (rc) return rc;
   OmegaArr om;
@@ -161,6 +163,7 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const voi
   for (int q = 0; q < nq; ++q) {
     qs[q].M = M_dev[q];
     qs[q].delta = delta_dev[q];
+    qs[q].dbar = dbar_dev ? dbar_dev[q] : nullptr;
     qs[q].f = f_dev ? f_dev[q] : nullptr;
     qs[q].P = P_dev[q];
     qs[q].K = K_host[q];
@@ -168,6 +171,8 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const voi
     if (qs[q].P == nullptr) return set_error(GW_EINVAL, "P_dev[%d] is NULL", q);
     if (qs[q].K > 0 && (qs[q].M == nullptr || qs[q].delta == nullptr))
       return set_error(GW_EINVAL, "M_dev[%d] or delta_dev[%d] is NULL", q, q);
+    if (dbar_dev && qs[q].K > 0 && qs[q].dbar == nullptr)
+      return set_error(GW_EINVAL, "delta_bar_dev[%d] is NULL", q);
     if (precision != GW_FP64 && (reinterpret_cast<uintptr_t>(qs[q].M) & 15u))
       return set_error(GW_EINVAL, "M_dev[%d] not 16-byte aligned", q);
   }
@@ -179,6 +184,49 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const voi
     return pol_fp64(nq, qs.data(), prefactor, nw, om, ws_dev, ws_bytes, stream, ctx);
   return pol_tc(nq, qs.data(), prefactor, nw, om, precision, m_dtype == GW_R32, ws_dev, ws_bytes,
                 stream, ctx);
+}
+
+int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const void* const* M_dev,
+                    int m_dtype, const double* const* delta_dev, const double* const* f_dev,
+                    double prefactor, int nw, const double* omega_host, double* const* P_dev,
+                    int precision, void* ws_dev, size_t ws_bytes, gw_stream_t stream) {
+  return polarization_impl(nq, K_host, nb_host, M_dev, m_dtype, delta_dev, nullptr, f_dev,
+                           prefactor, nw, omega_host, P_dev, precision, ws_dev, ws_bytes, stream);
+}
+
+int gw_polarization_extrapolar(int nq, const int64_t* K_host, const int* nb_host,
+                               const void* const* M_dev, int m_dtype,
+                               const double* const* delta_dev, const double* const* delta_bar_dev,
+                               const double* const* f_dev, const int64_t* nkn_host,
+                               const void* const* C_dev, const double* const* delta_bar_kn_dev,
+                               const double* const* f_kn_dev, double prefactor, int nw,
+                               const double* omega_host, double* const* P_dev, int precision,
+                               void* ws_dev, size_t ws_bytes, gw_stream_t stream) {
+  if (delta_bar_dev == nullptr || nkn_host == nullptr || C_dev == nullptr ||
+      delta_bar_kn_dev == nullptr)
+    return set_error(GW_EINVAL, "NULL delta_bar_dev, nkn_host, C_dev or delta_bar_kn_dev");
+  for (int q = 0; q < nq; ++q) {
+    if (nkn_host[q] < 0) return set_error(GW_EINVAL, "nkn[%d] < 0", q);
+    if (nkn_host[q] > 0 && (C_dev[q] == nullptr || delta_bar_kn_dev[q] == nullptr))
+      return set_error(GW_EINVAL, "C_dev[%d] or delta_bar_kn_dev[%d] is NULL", q, q);
+  }
+  int rc = polarization_impl(nq, K_host, nb_host, M_dev, m_dtype, delta_dev, delta_bar_dev, f_dev,
+                             prefactor, nw, omega_host, P_dev, precision, ws_dev, ws_bytes, stream);
+  if (rc) return rc;
+  OmegaArr om;
+  if ((rc = fill_omega(nw, omega_host, &om, false, false))) return rc;
+  std::vector<ComplQ> cq(nq);
+  for (int q = 0; q < nq; ++q) {
+    cq[q].C = C_dev[q];
+    cq[q].dbar = delta_bar_kn_dev[q];
+    cq[q].f = f_kn_dev ? f_kn_dev[q] : nullptr;
+    cq[q].P = P_dev[q];
+    cq[q].nkn = nkn_host[q];
+    cq[q].nb = nb_host[q];
+  }
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return completeness_add(nq, cq.data(), m_dtype, prefactor, nw, om, stream, ctx);
 }
 
 size_t gw_screened_w_workspace(int nq, const int* nb_host, int nw) {
@@ -285,6 +333,51 @@ int gw_sigma_convolve(int nq, const double* wq_host, const int64_t* npair_host, 
   if ((rc = device_ctx(&ctx))) return rc;
   return convolve(nq, wq_host, npair_host, nw, om, c_dev, pair_state_dev, eps_dev, nw_out, om_out,
                   nsig, sigma_dev, nullptr, 0, stream, ctx);
+}
+
+size_t gw_sigma_extrapolar_workspace(int nq, int nw, int nsig) {
+  if (nq < 1 || nw < 1 || nw > GW_MAX_NW || nsig < 1) return 0;
+  return sigma_extrapolar_workspace(nq, nw, nsig, 0);
+}
+
+int gw_sigma_extrapolar(int nq, const double* wq_host, const int* nb_host, int nsig,
+                        const double* const* S_dev, int nw, const double* omega_host,
+                        const double* const* Wc_dev, const int64_t* npair_host,
+                        const int* const* pair_state_dev, const double* const* c_dev,
+                        const double* ebar_host, int nw_out, const double* omega_out_host,
+                        double* sigma_dev, double* cbar_dev, void* ws_dev, size_t ws_bytes,
+                        gw_stream_t stream) {
+  if (nq < 1 || !wq_host || !nb_host || !npair_host || !ebar_host)
+    return set_error(GW_EINVAL, "nq < 1 or NULL host array");
+  if (nw < 4) return set_error(GW_EINVAL, "the convolution needs nw >= 4 nodes (nw=%d)", nw);
+  OmegaArr om, om_out;
+  int rc = fill_omega(nw, omega_host, &om, true, true);
+  if (rc) return rc;
+  if (nw_out < 1 || nw_out > GW_MAX_NW || !omega_out_host)
+    return set_error(GW_EINVAL, "nw_out=%d outside [1, %d] or NULL omega_out", nw_out, GW_MAX_NW);
+  memset(&om_out, 0, sizeof(om_out));
+  for (int i = 0; i < nw_out; ++i) {
+    if (!std::isfinite(omega_out_host[i])) return set_error(GW_EINVAL, "omega_out[%d] not finite", i);
+    om_out.v[i] = omega_out_host[i];
+  }
+  if (nsig < 1 || !sigma_dev) return set_error(GW_EINVAL, "nsig < 1 or NULL sigma_dev");
+  if (!S_dev || !Wc_dev || !pair_state_dev || !c_dev) return set_error(GW_EINVAL, "NULL pointer array");
+  for (int q = 0; q < nq; ++q) {
+    if (nb_host[q] < 1 || nb_host[q] > 8192) return set_error(GW_EINVAL, "nb[%d]=%d", q, nb_host[q]);
+    if (npair_host[q] < 0) return set_error(GW_EINVAL, "npair[%d] < 0", q);
+    if (!std::isfinite(wq_host[q])) return set_error(GW_EINVAL, "wq[%d] not finite", q);
+    if (!(ebar_host[q] > 0.0) || !std::isfinite(ebar_host[q]))
+      return set_error(GW_EINVAL, "ebar[%d] must be a finite positive energy", q);
+    if (!S_dev[q] || !Wc_dev[q]) return set_error(GW_EINVAL, "NULL S_dev or Wc_dev for q=%d", q);
+    if (npair_host[q] > 0 && (!c_dev[q] || !pair_state_dev[q]))
+      return set_error(GW_EINVAL, "NULL pair pointer for q=%d", q);
+  }
+  if ((rc = check_ws(ws_dev, ws_bytes, gw_sigma_extrapolar_workspace(nq, nw, nsig)))) return rc;
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return sigma_extrapolar(nq, wq_host, nb_host, nsig, S_dev, nw, om, Wc_dev, npair_host,
+                          pair_state_dev, c_dev, ebar_host, nw_out, om_out, sigma_dev, cbar_dev,
+                          ws_dev, ws_bytes, stream, ctx);
 }
 
 size_t gw_sigma_workspace(int nq, const int64_t* npair_host, const int* nb_host, int nw,

@@ -74,6 +74,7 @@ int launch_weights(int64_t K, const double* delta, const double* f, double pref,
 struct PolQ {
   const void* M;
   const double* delta;
+  const double* dbar;   // extrapolar correction: Delta_bar per transition (NULL: none)
   const double* f;
   double* P;
   int64_t K;
@@ -85,6 +86,24 @@ int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, vo
 size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision);
 int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
            bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
+
+// extrapolar correction (completeness term of P, extra pair coefficients of Sigma^c)
+struct ComplQ {
+  const void* C;        // [nkn][nb][nb] complex128 / complex64 / float32
+  const double* dbar;   // [nkn]
+  const double* f;      // [nkn] or NULL
+  double* P;            // [nw][nb][nb] complex128, accumulated
+  int64_t nkn;
+  int nb;
+};
+int completeness_add(int nq, const ComplQ* qs, int dtype, double pref, int nw, const OmegaArr& om,
+                     cudaStream_t s, const DeviceCtx& ctx);
+size_t sigma_extrapolar_workspace(int nq, int nw, int nsig, int sm_count);
+int sigma_extrapolar(int nq, const double* wq, const int* nb, int nsig, const double* const* S,
+                     int nw, const OmegaArr& om, const double* const* Wc, const int64_t* npair,
+                     const int* const* pair_state, const double* const* c, const double* ebar,
+                     int nw_out, const OmegaArr& om_out, double* sigma, double* cbar, void* ws,
+                     size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
 
 // a3
 size_t dielectric_workspace(int nq, const int* nb, int nw);

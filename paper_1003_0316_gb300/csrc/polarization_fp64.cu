@@ -51,6 +51,7 @@ constexpr int MAXQ = 64; // q entries per launch
 struct PolLaunch {
   const double2* M[MAXQ];
   const double* delta[MAXQ];
+  const double* dbar[MAXQ];   // extrapolar correction (NULL: none)
   const double* f[MAXQ];
   double2* P[MAXQ];
   int64_t K[MAXQ];
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(256) k_herk_fp64(PolLaunch L, double pref, Ome
   const double2* __restrict__ M = L.M[q];
   const double* __restrict__ delta = L.delta[q];
   const double* __restrict__ fw = L.f[q];
+  const double* __restrict__ dbar = L.dbar[q];
   const double wj2 = om.v[j] * om.v[j];
   int64_t per = (K + S - 1) / S;
   int64_t t_beg = per * split;
@@ -118,6 +120,12 @@ __global__ void __launch_bounds__(256) k_herk_fp64(PolLaunch L, double pref, Ome
         if (!(d > 0.0)) raise_status(status, ST_EINVAL);
         double ft = fw ? fw[t] : 1.0;
         w = -2.0 * pref * ft * d / (d * d + wj2);
+        if (dbar) {
+          // extrapolar correction: the same projections at Delta_bar enter with minus sign
+          const double db = dbar[t];
+          if (!(db > 0.0)) raise_status(status, ST_EINVAL);
+          w += 2.0 * pref * ft * db / (db * db + wj2);
+        }
       }
       ws_[tid] = w;
     }
@@ -254,6 +262,7 @@ int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, vo
       const PolQ& Q = qs[q0 + q];
       L.M[q] = static_cast<const double2*>(Q.M);
       L.delta[q] = Q.delta;
+      L.dbar[q] = Q.dbar;
       L.f[q] = Q.f;
       L.P[q] = reinterpret_cast<double2*>(Q.P);
       L.K[q] = Q.K;

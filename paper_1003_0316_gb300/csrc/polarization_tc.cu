@@ -637,10 +637,12 @@ __global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W
   }
 }
 
-// s_tj = |w_tj| = prefactor f_t 2 Delta_t / (Delta_t^2 + omega_j^2), stored in FP32
+// s_tj = -w_tj = prefactor f_t 2 Delta_t / (Delta_t^2 + omega_j^2), stored in FP32; with the
+// extrapolar correction the same transition at Delta_bar_t is subtracted (s may then change sign)
 __global__ void k_abs_weights_f32(int64_t K, int64_t kpad, const double* __restrict__ delta,
-                                  const double* __restrict__ f, double pref, int nw, OmegaArr om,
-                                  float* __restrict__ s, unsigned* status) {
+                                  const double* __restrict__ dbar, const double* __restrict__ f,
+                                  double pref, int nw, OmegaArr om, float* __restrict__ s,
+                                  unsigned* status) {
   int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (; t < kpad; t += stride) {
@@ -650,8 +652,17 @@ __global__ void k_abs_weights_f32(int64_t K, int64_t kpad, const double* __restr
     }
     double d = delta[t];
     if (!(d > 0.0)) raise_status(status, ST_EINVAL);
-    double a = 2.0 * pref * (f ? f[t] : 1.0) * d;
-    for (int j = 0; j < nw; ++j) s[size_t(j) * kpad + t] = float(a / (d * d + om.v[j] * om.v[j]));
+    const double ft = 2.0 * pref * (f ? f[t] : 1.0);
+    if (dbar == nullptr) {
+      for (int j = 0; j < nw; ++j) s[size_t(j) * kpad + t] = float(ft * d / (d * d + om.v[j] * om.v[j]));
+    } else {
+      const double db = dbar[t];
+      if (!(db > 0.0)) raise_status(status, ST_EINVAL);
+      for (int j = 0; j < nw; ++j) {
+        const double w2 = om.v[j] * om.v[j];
+        s[size_t(j) * kpad + t] = float(ft * (d / (d * d + w2) - db / (db * db + w2)));
+      }
+    }
   }
 }
 
@@ -733,8 +744,8 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     if (kpad == 0) continue;
     if (!sw[q] || !xT[q] || !bsp[q]) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
     int64_t blocks = std::min<int64_t>((kpad + 255) / 256, int64_t(ctx.sm_count) * 8);
-    k_abs_weights_f32<<<unsigned(blocks), 256, 0, s>>>(qs[q].K, kpad, qs[q].delta, qs[q].f, pref,
-                                                       nw, om, sw[q], ctx.status);
+    k_abs_weights_f32<<<unsigned(blocks), 256, 0, s>>>(qs[q].K, kpad, qs[q].delta, qs[q].dbar,
+                                                       qs[q].f, pref, nw, om, sw[q], ctx.status);
     GW_LAUNCH_CHECK("k_abs_weights_f32");
     const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbi));
     if (nch > 2147483647LL) return set_error(GW_EINVAL, "too many transitions for one q");
