@@ -11,11 +11,12 @@
 //                  cbar_s(w') = sum_IJ W^c_IJ(w') S^s_IJ - sum_{n' <= N'} c_{s n'}(w')
 //                  (k_extrapolar_trace, k_extrapolar_finish), convolved like every pair.
 //
-// k_completeness: one CTA per (q, 16 x 16 upper tile, group of 16 frequencies), one matrix
+// Completeness term: one CTA per (q, 16 x 16 upper tile, group of 16 frequencies), one matrix
 // entry per thread; the occupied states kn stream through in chunks of 32 whose weights sit
-// in shared memory. Complex128 input is summed in FP64. Complex64 / float32 input (the
-// split-precision paths) is summed in FP32 over a chunk and the chunk sums are folded into
-// a two-float (hi, lo) running sum by an error-free two-sum, so the FP64 pipe is not used
+// in shared memory. Complex128 input is summed in FP64 (k_completeness_fp64). Complex64 /
+// float32 input (the split-precision paths, k_completeness_async) is staged through shared
+// memory by asynchronous copies, summed in FP32 over a chunk, and the chunk sums are folded
+// into a two-float (hi, lo) running sum by an error-free two-sum, so the FP64 pipe is not used
 // in the loop; the entry and its Hermitian mirror are added to P at the end.
 #include <vector>
 #include <algorithm>
@@ -30,6 +31,7 @@ constexpr int CJG = 16;       // frequencies per CTA
 constexpr int CKC = 32;       // occupied states per chunk
 constexpr int CUNR = 8;       // loads in flight per thread
 constexpr int CMAXQ = 64;
+constexpr int CNST = 2;       // FP32 kernels: shared-memory stages of CKC states
 
 struct ComplLaunch {
   const void* C[CMAXQ];
@@ -38,7 +40,7 @@ struct ComplLaunch {
   double2* P[CMAXQ];
   int64_t nkn[CMAXQ];
   int nb[CMAXQ];
-  int tside[CMAXQ];
+  int tside[CMAXQ];     // 16 x 16 tiles per side
   int64_t item0[CMAXQ + 1];
   int nq;
   int nw;
@@ -61,30 +63,37 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
   lo += e;
 }
 
+// element type of the FP32 paths' completeness input
 template <int DT> struct CTraits;
-template <> struct CTraits<GW_C128> { using T = double2; using W = double; static constexpr bool cplx = true; };
-template <> struct CTraits<GW_C64> { using T = float2; using W = float; static constexpr bool cplx = true; };
-template <> struct CTraits<GW_R32> { using T = float; using W = float; static constexpr bool cplx = false; };
+template <> struct CTraits<GW_C64> { using T = float2; static constexpr bool cplx = true; };
+template <> struct CTraits<GW_R32> { using T = float; static constexpr bool cplx = false; };
 
-__device__ __forceinline__ double2 ld_c(const double2* p) { return __ldg(p); }
-__device__ __forceinline__ float2 ld_c(const float2* p) { return __ldg(p); }
-__device__ __forceinline__ float ld_c(const float* p) { return __ldg(p); }
-__device__ __forceinline__ double re_of(double2 v) { return v.x; }
-__device__ __forceinline__ double im_of(double2 v) { return v.y; }
 __device__ __forceinline__ float re_of(float2 v) { return v.x; }
 __device__ __forceinline__ float im_of(float2 v) { return v.y; }
 __device__ __forceinline__ float re_of(float v) { return v; }
 __device__ __forceinline__ float im_of(float) { return 0.0f; }
 
-template <int DT>
-__global__ void __launch_bounds__(256) k_completeness(ComplLaunch L, double pref, OmegaArr om,
-                                                      unsigned* status) {
-  using Tr = CTraits<DT>;
-  using T = typename Tr::T;
-  using W = typename Tr::W;
-  constexpr bool FP64 = DT == GW_C128;
-  constexpr int NV = Tr::cplx ? 2 : 1;      // real values per entry
+// Adds re + i im to P_j[I][J] and its Hermitian mirror (a real diagonal).
+__device__ __forceinline__ void add_hermitian(double2* Pj, int nb, int I, int J, double re, double im) {
+  double2* up = Pj + size_t(I) * nb + J;
+  if (I == J) {
+    up->x += re;
+    return;
+  }
+  double2 a = *up;
+  a.x += re;
+  a.y += im;
+  *up = a;
+  double2* dn = Pj + size_t(J) * nb + I;
+  double2 b = *dn;
+  b.x += re;
+  b.y -= im;
+  *dn = b;
+}
 
+// FP64 path (complex128 input): the sums stay in FP64 registers; CUNR loads in flight.
+__global__ void __launch_bounds__(256) k_completeness_fp64(ComplLaunch L, double pref, OmegaArr om,
+                                                           unsigned* status) {
   const int64_t item = blockIdx.x;
   int q = 0;
   while (q + 1 < L.nq && item >= L.item0[q + 1]) ++q;
@@ -100,78 +109,176 @@ __global__ void __launch_bounds__(256) k_completeness(ComplLaunch L, double pref
   const int nj = min(CJG, L.nw - j0);
   const int64_t nkn = L.nkn[q];
   const size_t nb2 = size_t(nb) * nb;
-  const T* __restrict__ C = static_cast<const T*>(L.C[q]) + (act ? size_t(I) * nb + J : 0);
+  const double2* __restrict__ C =
+      static_cast<const double2*>(L.C[q]) + (act ? size_t(I) * nb + J : 0);
   const double* __restrict__ dbar = L.dbar[q];
   const double* __restrict__ fk = L.f[q];
 
-  __shared__ W wsh[CKC][CJG];
-  // FP64 path: acc holds the sums. FP32 paths: part is the chunk sum, (acc, lo) the
-  // two-float running sum.
-  W part[CJG][NV];
-  W acc[CJG][NV];
-  float lo[CJG][NV];
+  __shared__ double wsh[CKC][CJG];
+  double acc[CJG][2];
 #pragma unroll
-  for (int jj = 0; jj < CJG; ++jj)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      part[jj][v] = W(0);
-      acc[jj][v] = W(0);
-      lo[jj][v] = 0.0f;
-    }
+  for (int jj = 0; jj < CJG; ++jj) acc[jj][0] = acc[jj][1] = 0.0;
 
   for (int64_t k0 = 0; k0 < nkn; k0 += CKC) {
     const int kc = int(nkn - k0 < CKC ? nkn - k0 : CKC);
     __syncthreads();
     for (int e = threadIdx.x; e < CKC * CJG; e += blockDim.x) {
       const int kk = e / CJG, jj = e % CJG;
-      W w = W(0);
+      double w = 0.0;
       if (kk < kc && jj < nj) {
         const double db = dbar[k0 + kk];
         if (!(db > 0.0)) raise_status(status, ST_EINVAL);
-        const double a = -2.0 * pref * (fk ? fk[k0 + kk] : 1.0);
         const double wv = om.v[j0 + jj];
-        if (FP64) {
-          w = W(a * db / (db * db + wv * wv));
-        } else {
-          const float dbf = float(db), wf = float(wv);
-          w = W(float(a) * dbf / fmaf(dbf, dbf, wf * wf));
-        }
+        w = -2.0 * pref * (fk ? fk[k0 + kk] : 1.0) * db / (db * db + wv * wv);
       }
       wsh[kk][jj] = w;
     }
     __syncthreads();
     if (!act) continue;
     for (int kk = 0; kk < kc; kk += CUNR) {
-      T val[CUNR];
+      double2 val[CUNR];
 #pragma unroll
       for (int u = 0; u < CUNR; ++u)
-        val[u] = (kk + u < kc) ? ld_c(C + size_t(k0 + kk + u) * nb2) : T{};
+        val[u] = (kk + u < kc) ? __ldg(C + size_t(k0 + kk + u) * nb2) : make_double2(0.0, 0.0);
 #pragma unroll
       for (int u = 0; u < CUNR; ++u) {
-        const W cr = W(re_of(val[u]));
-        const W ci = W(im_of(val[u]));
 #pragma unroll
         for (int jj = 0; jj < CJG; ++jj) {
-          const W w = wsh[kk + u][jj];     // zero beyond kc and nj
-          if constexpr (FP64) {
-            acc[jj][0] = fma(w, cr, acc[jj][0]);
-            acc[jj][NV - 1] = fma(w, ci, acc[jj][NV - 1]);
-          } else {
-            part[jj][0] = fmaf(w, cr, part[jj][0]);
-            if constexpr (NV == 2) part[jj][NV - 1] = fmaf(w, ci, part[jj][NV - 1]);
-          }
+          const double w = wsh[kk + u][jj];     // zero beyond kc and nj
+          acc[jj][0] = fma(w, val[u].x, acc[jj][0]);
+          acc[jj][1] = fma(w, val[u].y, acc[jj][1]);
         }
       }
     }
-    if constexpr (!FP64) {
+  }
+  if (!act) return;
+#pragma unroll
+  for (int jj = 0; jj < CJG; ++jj) {
+    if (jj >= nj) break;
+    add_hermitian(L.P[q] + size_t(j0 + jj) * nb2, nb, I, J, acc[jj][0], acc[jj][1]);
+  }
+}
+
+// The FP32 paths (complex64 / float32 input) with the C entries staged through shared memory
+// by per-thread asynchronous copies: chunk c + 1 is in flight while chunk c is summed. Each
+// thread copies and reads only its own entry, so its own wait_group is the only data
+// dependence; the weights are shared and follow a block barrier.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int DT>
+__global__ void __launch_bounds__(256, 1) k_completeness_async(ComplLaunch L, double pref, OmegaArr om,
+                                                            unsigned* status) {
+  using Tr = CTraits<DT>;
+  using T = typename Tr::T;
+  constexpr int NV = Tr::cplx ? 2 : 1;
+  static_assert(DT != GW_C128, "FP32 paths only");
+
+  const int64_t item = blockIdx.x;
+  int q = 0;
+  while (q + 1 < L.nq && item >= L.item0[q + 1]) ++q;
+  const int64_t local = item - L.item0[q];
+  const int jg = int(local % L.njg);
+  int ti, tj;
+  upper_tile(int(local / L.njg), L.tside[q], &ti, &tj);
+  const int nb = L.nb[q];
+  const int tid = threadIdx.x;
+  const int I = ti * CT + (tid >> 4);
+  const int J = tj * CT + (tid & 15);
+  const bool act = I < nb && J < nb && I <= J;
+  const int j0 = jg * CJG;
+  const int nj = min(CJG, L.nw - j0);
+  const int64_t nkn = L.nkn[q];
+  const size_t nb2 = size_t(nb) * nb;
+  const T* __restrict__ C = static_cast<const T*>(L.C[q]) + (act ? size_t(I) * nb + J : 0);
+  const double* __restrict__ dbar = L.dbar[q];
+  const double* __restrict__ fk = L.f[q];
+
+  extern __shared__ __align__(16) unsigned char csm[];
+  T* stage = reinterpret_cast<T*>(csm);                     // [CNST][CKC][256]
+  __shared__ __align__(16) float wsh[CKC][CJG];
+
+  auto prefetch = [&](int64_t k0, int buf) {
+    if (act) {
+      const int kc = int(nkn - k0 < CKC ? nkn - k0 : CKC);
+      T* dst = stage + size_t(buf) * CKC * 256 + tid;
+      for (int kk = 0; kk < kc; ++kk) {
+        if (NV == 2) cp_async8(dst + kk * 256, C + size_t(k0 + kk) * nb2);
+        else cp_async4(dst + kk * 256, C + size_t(k0 + kk) * nb2);
+      }
+    }
+    cp_async_commit();
+  };
+
+  float part[CJG][NV], acc[CJG][NV], lo[CJG][NV];
+#pragma unroll
+  for (int jj = 0; jj < CJG; ++jj)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[jj][v] = acc[jj][v] = lo[jj][v] = 0.0f;
+
+  // CNST - 1 chunks in flight while one is summed; every iteration commits one group (empty
+  // past the end) so that wait_group CNST - 1 always means "the current chunk has landed"
+  for (int c = 0; c < CNST - 1; ++c) {
+    if (int64_t(c) * CKC < nkn) prefetch(int64_t(c) * CKC, c);
+    else cp_async_commit();
+  }
+  int buf = 0;
+  for (int64_t k0 = 0; k0 < nkn; k0 += CKC, buf = (buf + 1) % CNST) {
+    const int kc = int(nkn - k0 < CKC ? nkn - k0 : CKC);
+    const int64_t kn_next = k0 + int64_t(CNST - 1) * CKC;
+    if (kn_next < nkn) prefetch(kn_next, (buf + CNST - 1) % CNST);
+    else cp_async_commit();
+    __syncthreads();                            // the previous chunk's weights are consumed
+    for (int e = tid; e < CKC * CJG; e += blockDim.x) {
+      const int kk = e / CJG, jj = e % CJG;
+      float w = 0.0f;
+      if (kk < kc && jj < nj) {
+        const double db = dbar[k0 + kk];
+        if (!(db > 0.0)) raise_status(status, ST_EINVAL);
+        const float a = float(-2.0 * pref * (fk ? fk[k0 + kk] : 1.0));
+        const float dbf = float(db), wf = float(om.v[j0 + jj]);
+        w = a * dbf / fmaf(dbf, dbf, wf * wf);
+      }
+      wsh[kk][jj] = w;
+    }
+    cp_async_wait<CNST - 1>();                  // this thread's copies of chunk k0 landed
+    __syncthreads();
+    if (act) {
+      const T* src = stage + size_t(buf) * CKC * 256 + tid;
+      for (int kk = 0; kk < kc; ++kk) {
+        const T cv = src[kk * 256];
+        const float cr = float(re_of(cv)), ci = float(im_of(cv));
+        const float4* wrow = reinterpret_cast<const float4*>(wsh[kk]);
+#pragma unroll
+        for (int j4 = 0; j4 < CJG / 4; ++j4) {
+          const float4 w4 = wrow[j4];
+          const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            part[4 * j4 + t][0] = fmaf(ws[t], cr, part[4 * j4 + t][0]);
+            if constexpr (NV == 2) part[4 * j4 + t][NV - 1] = fmaf(ws[t], ci, part[4 * j4 + t][NV - 1]);
+          }
+        }
+      }
 #pragma unroll
       for (int jj = 0; jj < CJG; ++jj)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          float h = float(acc[jj][v]);
-          two_sum_acc(h, lo[jj][v], float(part[jj][v]));
-          acc[jj][v] = W(h);
-          part[jj][v] = W(0);
+          two_sum_acc(acc[jj][v], lo[jj][v], part[jj][v]);
+          part[jj][v] = 0.0f;
         }
     }
   }
@@ -179,30 +286,20 @@ __global__ void __launch_bounds__(256) k_completeness(ComplLaunch L, double pref
 #pragma unroll
   for (int jj = 0; jj < CJG; ++jj) {
     if (jj >= nj) break;
-    const double re = double(acc[jj][0]) + (FP64 ? 0.0 : double(lo[jj][0]));
-    const double im = NV == 2 ? double(acc[jj][NV - 1]) + (FP64 ? 0.0 : double(lo[jj][NV - 1])) : 0.0;
-    double2* Pj = L.P[q] + size_t(j0 + jj) * nb2;
-    double2* up = Pj + size_t(I) * nb + J;
-    if (I == J) {
-      up->x += re;                         // Hermitian: real diagonal
-    } else {
-      double2 a = *up;
-      a.x += re;
-      a.y += im;
-      *up = a;
-      double2* dn = Pj + size_t(J) * nb + I;
-      double2 b = *dn;
-      b.x += re;
-      b.y -= im;
-      *dn = b;
-    }
+    const double re = double(acc[jj][0]) + double(lo[jj][0]);
+    const double im = NV == 2 ? double(acc[jj][NV - 1]) + double(lo[jj][NV - 1]) : 0.0;
+    add_hermitian(L.P[q] + size_t(j0 + jj) * nb2, nb, I, J, re, im);
   }
+}
+
+constexpr size_t async_smem(int dt) {
+  return size_t(CNST) * CKC * 256 * (dt == GW_C64 ? 8 : 4);
 }
 
 // ------------------------------------------------------------ self-energy side
 constexpr int SJG = 8;       // frequencies per CTA
 constexpr int SSG = 4;       // states per CTA
-constexpr int SNCH = 32;     // element chunks per (q, group)
+constexpr int SNCH = 128;    // element chunks per (q, group)
 
 struct TraceLaunch {
   const double2* S[CMAXQ];
@@ -274,30 +371,37 @@ struct FinishLaunch {
   int nq, nw, nsig;
 };
 
-// cbar[q][j][s] = sum of the chunk traces (fixed order) - sum_{p: state(p) = s} c[q][j][p];
-// also the extra pairs' states and energies for the convolution
-__global__ void k_extrapolar_finish(FinishLaunch L, const double* __restrict__ part,
-                                    double* __restrict__ cbar, int* __restrict__ state_x,
-                                    double* __restrict__ eps_x, unsigned* status) {
+// cbar[q][j][s] = sum of the chunk traces (fixed order) - sum_{p: state(p) = s} c[q][j][p]:
+// one warp per (q, j, s), lanes striding over the pairs and a fixed shuffle tree, so the
+// result does not depend on scheduling; lane 0 also writes the extra pair's energy and state
+__global__ void __launch_bounds__(256) k_extrapolar_finish(FinishLaunch L,
+                                                           const double* __restrict__ part,
+                                                           double* __restrict__ cbar,
+                                                           int* __restrict__ state_x,
+                                                           double* __restrict__ eps_x,
+                                                           unsigned* status) {
   const int64_t n = int64_t(L.nq) * L.nw * L.nsig;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const int s = int(i % L.nsig);
-    const int j = int((i / L.nsig) % L.nw);
-    const int q = int(i / (int64_t(L.nsig) * L.nw));
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  if (i >= n) return;                         // whole warps
+  const int s = int(i % L.nsig);
+  const int j = int((i / L.nsig) % L.nw);
+  const int q = int(i / (int64_t(L.nsig) * L.nw));
+  const double* __restrict__ cj = L.c[q] + size_t(j) * L.npair[q];
+  const int* __restrict__ st = L.state[q];
+  double kept = 0.0;
+  bool bad = false;
+  for (int64_t p = lane; p < L.npair[q]; p += 32) {
+    const int sp = __ldg(st + p);
+    bad |= sp < 0 || sp >= L.nsig;
+    if (sp == s) kept += __ldg(cj + p);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+  if (bad && j == 0 && s == 0) raise_status(status, ST_EINVAL);
+  if (lane == 0) {
     double t = 0.0;
     for (int ch = 0; ch < SNCH; ++ch) t += part[((size_t(q) * SNCH + ch) * L.nw + j) * L.nsig + s];
-    const double* cj = L.c[q] + size_t(j) * L.npair[q];
-    const int* st = L.state[q];
-    double kept = 0.0;
-    for (int64_t p = 0; p < L.npair[q]; ++p) {
-      const int sp = st[p];
-      if (sp < 0 || sp >= L.nsig) {
-        if (j == 0 && s == 0) raise_status(status, ST_EINVAL);
-        continue;
-      }
-      if (sp == s) kept += cj[p];
-    }
     cbar[i] = t - kept;
     if (j == 0) {
       eps_x[size_t(q) * L.nsig + s] = L.ebar[q];
@@ -333,12 +437,29 @@ int completeness_add(int nq, const ComplQ* qs, int dtype, double pref, int nw, c
     L.item0[n] = item;
     if (item == 0) continue;
     if (item > 2147483647LL) return set_error(GW_EINVAL, "completeness term: too many tiles");
-    if (dtype == GW_C128)
-      k_completeness<GW_C128><<<unsigned(item), 256, 0, s>>>(L, pref, om, ctx.status);
-    else if (dtype == GW_C64)
-      k_completeness<GW_C64><<<unsigned(item), 256, 0, s>>>(L, pref, om, ctx.status);
-    else
-      k_completeness<GW_R32><<<unsigned(item), 256, 0, s>>>(L, pref, om, ctx.status);
+    if (dtype == GW_C128) {
+      k_completeness_fp64<<<unsigned(item), 256, 0, s>>>(L, pref, om, ctx.status);
+    } else if (dtype == GW_C64) {
+      static bool attr64[64] = {};
+      if (!attr64[ctx.device]) {
+        GW_CUDA_TRY(cudaFuncSetAttribute(k_completeness_async<GW_C64>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(async_smem(GW_C64))));
+        attr64[ctx.device] = true;
+      }
+      k_completeness_async<GW_C64><<<unsigned(item), 256, async_smem(GW_C64), s>>>(L, pref, om,
+                                                                                ctx.status);
+    } else {
+      static bool attr32[64] = {};
+      if (!attr32[ctx.device]) {
+        GW_CUDA_TRY(cudaFuncSetAttribute(k_completeness_async<GW_R32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(async_smem(GW_R32))));
+        attr32[ctx.device] = true;
+      }
+      k_completeness_async<GW_R32><<<unsigned(item), 256, async_smem(GW_R32), s>>>(L, pref, om,
+                                                                                ctx.status);
+    }
     GW_LAUNCH_CHECK("k_completeness");
   }
   return GW_OK;
@@ -393,8 +514,8 @@ int sigma_extrapolar(int nq, const double* wq, const int* nb, int nsig, const do
     const int64_t cnt = int64_t(n) * per;
     double* cb = cbar + size_t(q0) * per;
     double* ex = eps_x + size_t(q0) * nsig;
-    k_extrapolar_finish<<<unsigned(std::min<int64_t>((cnt + 255) / 256, 4096)), 256, 0, s>>>(
-        F, part, cb, state_x, ex, ctx.status);
+    k_extrapolar_finish<<<unsigned((cnt * 32 + 255) / 256), 256, 0, s>>>(F, part, cb, state_x, ex,
+                                                                         ctx.status);
     GW_LAUNCH_CHECK("k_extrapolar_finish");
   }
   std::vector<const double*> cq(nq), eq(nq);
