@@ -212,12 +212,18 @@ int gw_sigma_pair_coeffs(int nq, const int64_t* npair_host, const int* nb_host,
  *   pair_state_dev[q] [npair_q] int in [0, nsig); eps_dev[q] [npair_q] double != 0;
  *   omega_host [nw] (ascending, > 0); omega_out_host [nw_out] (any real values);
  *   sigma_dev [nsig][nw_out] complex128 output (overwritten).
+ * The closed-form integrals depend only on (e_p, omega_i) and the spline is linear in the node
+ * values, so pairs with the same energy (bit-identical e_p) share the weights T_ij(e_p): they
+ * are computed once per distinct energy of a q point (found by a hash of the energies in the
+ * workspace) and applied to every such pair.
+ * Workspace: gw_sigma_convolve_workspace() bytes.
  * e_p == 0 is reported by gw_check as GW_EINVAL. */
+size_t gw_sigma_convolve_workspace(int nq, const int64_t* npair_host);
 int gw_sigma_convolve(int nq, const double* wq_host, const int64_t* npair_host,
                       int nw, const double* omega_host, const double* const* c_dev,
                       const int* const* pair_state_dev, const double* const* eps_dev,
                       int nw_out, const double* omega_out_host, int nsig,
-                      double* sigma_dev, gw_stream_t stream);
+                      double* sigma_dev, void* ws_dev, size_t ws_bytes, gw_stream_t stream);
 
 /* Extrapolar correction of Sigma^c (Sec. V, band convergence, with the full W^c rather than a
  * plasmon-pole model): the partner bands n' > N' of every state s sit at e_bar_q, so they act

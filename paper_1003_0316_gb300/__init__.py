@@ -63,8 +63,9 @@ _sig("gw_screened_w", _i32, _i32, _P(_i32), _i32, _P(_vp), _P(_vp), _P(_vp), _vp
 _sig("gw_screened_w_noalloc", _i32, _i32, _i32, _vp, _vp, _vp, _vp)
 _sig("gw_sigma_pair_coeffs", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _i32, _P(_vp),
      _P(_vp), _i32, _vp, _sz, _vp)
+_sig("gw_sigma_convolve_workspace", _sz, _i32, _P(_i64))
 _sig("gw_sigma_convolve", _i32, _i32, _P(_f64), _P(_i64), _i32, _P(_f64), _P(_vp), _P(_vp),
-     _P(_vp), _i32, _P(_f64), _i32, _vp, _vp)
+     _P(_vp), _i32, _P(_f64), _i32, _vp, _vp, _sz, _vp)
 _sig("gw_sigma_workspace", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32)
 _sig("gw_sigma_c", _i32, _i32, _P(_f64), _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp),
      _i32, _P(_f64), _P(_vp), _i32, _P(_f64), _i32, _vp, _i32, _vp, _sz, _vp)
@@ -300,9 +301,10 @@ def sigma_convolve(wq, cs, pair_states, epss, omega, omega_out, nsig, out=None):
     dev = cs[0].device
     if out is None:
         out = torch.empty((nsig, nwo), dtype=torch.complex128, device=dev)
+    wsb, wsp, wsn = _ws(_lib.gw_sigma_convolve_workspace(nq, _arr(_i64, npairs)), dev)
     _raise(_lib.gw_sigma_convolve(nq, _arr(_f64, wq), _arr(_i64, npairs), nw, om, _ptrs(cs),
                                   _ptrs(pair_states), _ptrs(epss), nwo, omo, nsig, out.data_ptr(),
-                                  _stream()))
+                                  wsp, wsn, _stream()))
     return out
 
 

@@ -1,5 +1,6 @@
 // C ABI entry points of libgw: argument validation, the error model, workspace
 // sizing and dispatch to the kernels of the other translation units.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -304,11 +305,18 @@ int gw_sigma_pair_coeffs(int nq, const int64_t* npair_host, const int* nb_host,
                   ws_dev, ws_bytes, stream, ctx);
 }
 
+size_t gw_sigma_convolve_workspace(int nq, const int64_t* npair_host) {
+  if (nq < 1 || !npair_host) return 0;
+  for (int q = 0; q < nq; ++q)
+    if (npair_host[q] < 0) return 0;
+  return convolve_workspace(nq, npair_host, 0, 0);
+}
+
 int gw_sigma_convolve(int nq, const double* wq_host, const int64_t* npair_host, int nw,
                       const double* omega_host, const double* const* c_dev,
                       const int* const* pair_state_dev, const double* const* eps_dev,
                       int nw_out, const double* omega_out_host, int nsig, double* sigma_dev,
-                      gw_stream_t stream) {
+                      void* ws_dev, size_t ws_bytes, gw_stream_t stream) {
   if (nq < 1 || !wq_host || !npair_host) return set_error(GW_EINVAL, "nq < 1 or NULL host array");
   if (nw < 4) return set_error(GW_EINVAL, "the convolution needs nw >= 4 nodes (nw=%d)", nw);
   OmegaArr om, om_out;
@@ -329,10 +337,11 @@ int gw_sigma_convolve(int nq, const double* wq_host, const int64_t* npair_host, 
     if (npair_host[q] > 0 && (!c_dev[q] || !pair_state_dev[q] || !eps_dev[q]))
       return set_error(GW_EINVAL, "NULL pointer for q=%d", q);
   }
+  if ((rc = check_ws(ws_dev, ws_bytes, gw_sigma_convolve_workspace(nq, npair_host)))) return rc;
   DeviceCtx ctx;
   if ((rc = device_ctx(&ctx))) return rc;
   return convolve(nq, wq_host, npair_host, nw, om, c_dev, pair_state_dev, eps_dev, nw_out, om_out,
-                  nsig, sigma_dev, nullptr, 0, stream, ctx);
+                  nsig, sigma_dev, ws_dev, ws_bytes, stream, ctx);
 }
 
 size_t gw_sigma_extrapolar_workspace(int nq, int nw, int nsig) {
@@ -388,7 +397,9 @@ size_t gw_sigma_workspace(int nq, const int64_t* npair_host, const int* nb_host,
     if (npair_host[q] < 0) return 0;
     b += ws_round(sizeof(double) * size_t(nw) * size_t(npair_host[q]));
   }
-  return b + paircoef_workspace(nq, npair_host, nb_host, nw, precision);
+  // the pair-coefficient scratch and the convolution's share the space after the coefficients
+  return b + std::max(paircoef_workspace(nq, npair_host, nb_host, nw, precision),
+                      convolve_workspace(nq, npair_host, nw, 0));
 }
 
 int gw_sigma_c(int nq, const double* wq_host, const int64_t* npair_host, const int* nb_host,
@@ -412,7 +423,8 @@ int gw_sigma_c(int nq, const double* wq_host, const int64_t* npair_host, const i
   if (rc) return rc;
   std::vector<const double*> cc(cbuf.begin(), cbuf.end());
   return gw_sigma_convolve(nq, wq_host, npair_host, nw, omega_host, cc.data(), pair_state_dev,
-                           eps_dev, nw_out, omega_out_host, nsig, sigma_dev, stream);
+                           eps_dev, nw_out, omega_out_host, nsig, sigma_dev,
+                           static_cast<char*>(ws_dev) + off, ws_bytes - off, stream);
 }
 
 }  // extern "C"

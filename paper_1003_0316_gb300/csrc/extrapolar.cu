@@ -470,7 +470,8 @@ size_t sigma_extrapolar_workspace(int nq, int nw, int nsig, int) {
   return ws_round(size_t(nq) * SNCH * per * sizeof(double))     // chunk traces
          + ws_round(size_t(nq) * per * sizeof(double))          // cbar
          + ws_round(size_t(nsig) * sizeof(int))                 // extra pairs' states
-         + ws_round(size_t(nq) * nsig * sizeof(double)) + 1024; // extra pairs' energies
+         + ws_round(size_t(nq) * nsig * sizeof(double)) + 1024  // extra pairs' energies
+         + convolve_workspace(nq, std::vector<int64_t>(nq, nsig).data(), nw, 0);
 }
 
 int sigma_extrapolar(int nq, const double* wq, const int* nb, int nsig, const double* const* S,
@@ -525,8 +526,9 @@ int sigma_extrapolar(int nq, const double* wq, const int* nb, int nsig, const do
     cq[q] = cbar + size_t(q) * per;
     eq[q] = eps_x + size_t(q) * nsig;
   }
+  const size_t used = (cur.used + 255) & ~size_t(255);
   return convolve_acc(nq, wq, np.data(), nw, om, cq.data(), sq.data(), eq.data(), nw_out, om_out,
-                      nsig, sigma, true, s, ctx);
+                      nsig, sigma, true, static_cast<char*>(ws) + used, ws_bytes - used, s, ctx);
 }
 
 }  // namespace gw

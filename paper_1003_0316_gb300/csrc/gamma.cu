@@ -324,7 +324,9 @@ int bz_constant_sc(double a, int n, double beta, double* out, void* ws, size_t w
 }
 
 size_t sigma_div_workspace(int nw, int nsig) {
-  return ws_round(size_t(nw) * nsig * sizeof(double)) + ws_round(size_t(nsig) * sizeof(int)) + 256;
+  const int64_t np = nsig;
+  return ws_round(size_t(nw) * nsig * sizeof(double)) + ws_round(size_t(nsig) * sizeof(int)) + 256 +
+         convolve_workspace(1, &np, nw, 0);
 }
 
 int sigma_div(int nw, const OmegaArr& om, const double* head, double cbz, double volume, int nsig,
@@ -341,8 +343,9 @@ int sigma_div(int nw, const OmegaArr& om, const double* head, double cbz, double
   const int64_t np = nsig;
   const double* cc = c;
   const int* sc = st;
+  const size_t used = (cur.used + 255) & ~size_t(255);
   return convolve_acc(1, &wq, &np, nw, om, &cc, &sc, &eps_state, nw_out, om_out, nsig, sigma, true,
-                      s, ctx);
+                      static_cast<char*>(ws) + used, ws_bytes - used, s, ctx);
 }
 
 }  // namespace gw

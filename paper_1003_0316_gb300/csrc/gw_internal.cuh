@@ -123,11 +123,11 @@ int convolve(int nq, const double* wq, const int64_t* npair, int nw, const Omega
              const double* const* c, const int* const* pair_state, const double* const* eps,
              int nw_out, const OmegaArr& om_out, int nsig, double* sigma, void* ws,
              size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
-// the same, adding into sigma when accumulate is set
+// the same, adding into sigma when accumulate is set (workspace: convolve_workspace)
 int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const OmegaArr& om,
                  const double* const* c, const int* const* pair_state, const double* const* eps,
                  int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
-                 cudaStream_t s, const DeviceCtx& ctx);
+                 void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
 
 // quasiparticle energies
 int qp_solve(int n, int npole, const double* params, const double* eps, const double* sigx,

@@ -269,161 +269,377 @@ __device__ cplx tail_integral(cplx A, double sgn, double X) {
   return cdiv(mk(1.0, 0.0), mk(A.x * X, A.y * X)) + cdiv(isg * L, a2);
 }
 
-__device__ cplx pair_integral(const double* __restrict__ c, int64_t stride, int nw,
-                              const double* lam, const double* h, double wN, double w,
-                              double e) {
-  // node values and secant slopes
-  double y[GW_MAX_NW], m[GW_MAX_NW], cp[GW_MAX_NW];
-  for (int j = 0; j < nw; ++j) y[j] = c[j * stride];
-  const int n = nw;
-  // tridiagonal system for the slopes (not-a-knot left, clamped right)
-  {
-    double d0 = (y[1] - y[0]) / h[0], d1 = (y[2] - y[1]) / h[1];
-    double b0 = h[1], c0 = h[0] + h[1];
-    double r0 = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * d0 + h[0] * h[0] * d1) / (h[0] + h[1]);
-    cp[0] = c0 / b0;
-    m[0] = r0 / b0;
-    for (int i = 1; i < n - 1; ++i) {
-      double dl = (y[i] - y[i - 1]) / h[i - 1], dr = (y[i + 1] - y[i]) / h[i];
-      double a = h[i], b = 2.0 * (h[i - 1] + h[i]), cc = h[i - 1];
-      double r = 3.0 * (h[i] * dl + h[i - 1] * dr);
-      double den = b - a * cp[i - 1];
-      cp[i] = cc / den;
-      m[i] = (r - a * m[i - 1]) / den;
-    }
-    double sig = -2.0 * (1.0 + wN) * (1.0 + wN) / wN;
-    m[n - 1] = sig * y[n - 1];
-    for (int i = n - 2; i >= 0; --i) m[i] = m[i] - cp[i] * m[i + 1];
+// Coefficients C[k] (k = 0..3, powers of t = lambda - la) of spline piece s for the node values
+// y: piece 0 is [0, lam_0] (segment 0 extrapolated, re-centred at lambda = 0), piece s >= 1 is
+// segment s - 1. Slopes: not-a-knot at the first node, clamped at the last to the tail's
+// dc/dw = -2 c_N / w_N (dc/dlambda = -2 c_N (1 + w_N)^2 / w_N).
+__device__ void spline_slopes(const double* y, int n, const double* h, double wN, double* m,
+                              double* cp) {
+  double d0 = (y[1] - y[0]) / h[0], d1 = (y[2] - y[1]) / h[1];
+  double b0 = h[1], c0 = h[0] + h[1];
+  double r0 = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * d0 + h[0] * h[0] * d1) / (h[0] + h[1]);
+  cp[0] = c0 / b0;
+  m[0] = r0 / b0;
+  for (int i = 1; i < n - 1; ++i) {
+    double dl = (y[i] - y[i - 1]) / h[i - 1], dr = (y[i + 1] - y[i]) / h[i];
+    double a = h[i], b = 2.0 * (h[i - 1] + h[i]), cc = h[i - 1];
+    double r = 3.0 * (h[i] * dl + h[i - 1] * dr);
+    double den = b - a * cp[i - 1];
+    cp[i] = cc / den;
+    m[i] = (r - a * m[i - 1]) / den;
   }
-  const cplx A = mk(-e, w);
-  const cplx bp = mk(A.x * -1.0, 1.0 - A.y);    // i - A
-  const cplx bm = mk(A.x * -1.0, -1.0 - A.y);   // -i - A
-  cplx total = mk(0, 0);
-  for (int s = 0; s < n; ++s) {
-    // piece s: s = 0 is [0, lam0] with segment 0 extrapolated; s >= 1 is segment s-1
-    int g = s == 0 ? 0 : s - 1;
-    double dlt = (y[g + 1] - y[g]) / h[g];
-    double C[4];
-    C[0] = y[g];
-    C[1] = m[g];
-    C[2] = (3.0 * dlt - 2.0 * m[g] - m[g + 1]) / h[g];
-    C[3] = (m[g] + m[g + 1] - 2.0 * dlt) / (h[g] * h[g]);
-    double la, H;
-    if (s == 0) {
-      // re-centre the cubic at lambda = 0: t = u - lam0
-      double x0 = -lam[0];
-      double D0 = C[0] + x0 * (C[1] + x0 * (C[2] + x0 * C[3]));
-      double D1 = C[1] + x0 * (2.0 * C[2] + 3.0 * x0 * C[3]);
-      double D2 = C[2] + 3.0 * x0 * C[3];
-      C[0] = D0;
-      C[1] = D1;
-      C[2] = D2;
-      la = 0.0;
-      H = lam[0];
-    } else {
-      la = lam[g];
-      H = h[g];
-    }
-    cplx Ip[4], Im[4];
-    moments(A + la * bp, bp, H, Ip);
-    moments(A + la * bm, bm, H, Im);
-    cplx acc_p = mk(0, 0), acc_m = mk(0, 0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      acc_p = acc_p + C[k] * Ip[k];
-      acc_m = acc_m + C[k] * Im[k];
-    }
-    // -i b+ acc_p + i b- acc_m
-    cplx t1 = mk(0.0, -1.0) * (bp * acc_p);
-    cplx t2 = mk(0.0, 1.0) * (bm * acc_m);
-    total = total + t1 + t2;
-  }
-  cplx tl = tail_integral(A, 1.0, wN) + tail_integral(A, -1.0, wN);
-  total = total + (y[n - 1] * wN * wN) * tl;
-  return total;
+  double sig = -2.0 * (1.0 + wN) * (1.0 + wN) / wN;
+  m[n - 1] = sig * y[n - 1];
+  for (int i = n - 2; i >= 0; --i) m[i] = m[i] - cp[i] * m[i + 1];
 }
 
+__device__ void piece_coeffs(const double* y, const double* m, const double* lam, const double* h,
+                             int s, double C[4]) {
+  const int g = s == 0 ? 0 : s - 1;
+  const double dlt = (y[g + 1] - y[g]) / h[g];
+  C[0] = y[g];
+  C[1] = m[g];
+  C[2] = (3.0 * dlt - 2.0 * m[g] - m[g + 1]) / h[g];
+  C[3] = (m[g] + m[g + 1] - 2.0 * dlt) / (h[g] * h[g]);
+  if (s == 0) {
+    const double x0 = -lam[0];
+    const double D0 = C[0] + x0 * (C[1] + x0 * (C[2] + x0 * C[3]));
+    const double D1 = C[1] + x0 * (2.0 * C[2] + 3.0 * x0 * C[3]);
+    const double D2 = C[2] + 3.0 * x0 * C[3];
+    C[0] = D0;
+    C[1] = D1;
+    C[2] = D2;
+  }
+}
+
+// Pairs with the same energy share the convolution weights T_ij(e): the spline is linear in the
+// node values, so sum_j T_ij(e) c_j with T_ij = sum_{piece, k} K_{piece,k}(e, w_i) S_{piece,k,j}
+// (S: the cardinal spline coefficients of the node mesh, K: the closed-form integrals of
+// t^k against the kernel on the piece) plus the tail on the last node. The closed forms run
+// once per distinct energy of a q point:
+//   k_conv_init / k_conv_hash: every pair inserts the bit pattern of its energy into an
+//     open-addressing table (atomicCAS), records its slot and counts the slot's pairs;
+//   k_conv_scan: per q, the offsets of the slots' pair lists and the occupied slots;
+//   k_conv_scatter: every pair writes its index into its slot's list;
+//   k_conv_slot: one CTA per (occupied slot, 16 output frequencies): S (once per CTA), K (one
+//     thread per output frequency and piece), T, then Sigma_s(i w_i) += w_q f sum_j T_ij c_jp
+//     over the slot's pairs (FP64 atomics).
 constexpr int CTHREADS = 256;
+constexpr int CIC = 16;                       // output frequencies per slot CTA
+constexpr unsigned long long EMPTY_KEY = ~0ull;   // a NaN pattern: never a valid energy
+
+struct ConvQ {
+  const double* c;        // [nw][npair]
+  const int* state;
+  const double* eps;
+  int64_t npair;
+  double wq;
+  unsigned long long* keys;   // [tsize]
+  int* cnt;                   // [tsize]
+  int* off;                   // [tsize]
+  int* fill;                  // [tsize]
+  int* occ;                   // [tsize] occupied slots, compact
+  int* nocc;                  // [1]
+  int* slot_of;               // [npair]
+  int* list;                  // [npair]
+  int tsize;
+};
+
 struct ConvLaunch {
-  int64_t item0[SMAXQ + 1];   // first (pair, output frequency) item of q
-  const double* c[SMAXQ];
-  const int* state[SMAXQ];
-  const double* eps[SMAXQ];
-  int64_t npair[SMAXQ];
-  double wq[SMAXQ];
+  ConvQ Q[SMAXQ];
+  int64_t item0[SMAXQ + 1];   // prefix of pairs (hash, scatter) or of table slots (init)
   int nq;
 };
 
-// One thread per (pair, output frequency): the pair's spline-and-tail integral, weighted by
-// w_q, added into Sigma of the pair's state by FP64 atomics (Sigma zeroed first unless
-// accumulating).
-__global__ void __launch_bounds__(CTHREADS) k_convolve(ConvLaunch L, int nw, OmegaArr om,
-                                                       OmegaArr om_out, int nw_out, int nsig,
-                                                       double* __restrict__ sigma,
-                                                       unsigned* status) {
-  __shared__ double lam[GW_MAX_NW], h[GW_MAX_NW];
-  if (threadIdx.x < nw) lam[threadIdx.x] = om.v[threadIdx.x] / (1.0 + om.v[threadIdx.x]);
-  __syncthreads();
-  if (threadIdx.x < nw - 1) h[threadIdx.x] = lam[threadIdx.x + 1] - lam[threadIdx.x];
-  __syncthreads();
-  const double wN = om.v[nw - 1];
-  const double f = -1.0 / (2.0 * 3.14159265358979323846);
+__device__ __forceinline__ uint32_t mix64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return uint32_t(k);
+}
+
+__device__ __forceinline__ int find_q(const ConvLaunch& L, int64_t e) {
+  int q = 0;
+  while (q + 1 < L.nq && e >= L.item0[q + 1]) ++q;
+  return q;
+}
+
+__global__ void k_conv_init(ConvLaunch L) {
   const int64_t total = L.item0[L.nq];
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
-    int q = 0;
-    while (q + 1 < L.nq && e >= L.item0[q + 1]) ++q;
-    const int64_t loc = e - L.item0[q];
-    const int64_t p = loc / nw_out;
-    const int i = int(loc % nw_out);
-    const int st = L.state[q][p];
-    const double ep = L.eps[q][p];
-    if (!(ep != 0.0) || !isfinite(ep) || st < 0 || st >= nsig) {
-      raise_status(status, ST_EINVAL);
-      continue;
-    }
-    const cplx v = pair_integral(L.c[q] + p, L.npair[q], nw, lam, h, wN, om_out.v[i], ep);
-    double2* out = reinterpret_cast<double2*>(sigma) + size_t(st) * nw_out + i;
-    atomicAdd(&out->x, f * L.wq[q] * v.x);
-    atomicAdd(&out->y, f * L.wq[q] * v.y);
+    const int q = find_q(L, e);
+    const int64_t i = e - L.item0[q];
+    const ConvQ& Q = L.Q[q];
+    Q.keys[i] = EMPTY_KEY;
+    Q.cnt[i] = 0;
+    Q.fill[i] = 0;
+    if (i == 0) *Q.nocc = 0;
   }
 }
 
-size_t convolve_workspace(int, const int64_t*, int, int) { return 0; }
+__global__ void k_conv_hash(ConvLaunch L, int nsig, unsigned* status) {
+  const int64_t total = L.item0[L.nq];
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int q = find_q(L, e);
+    const int64_t p = e - L.item0[q];
+    const ConvQ& Q = L.Q[q];
+    const double ep = Q.eps[p];
+    const int st = Q.state[p];
+    if (!(ep != 0.0) || !isfinite(ep) || st < 0 || st >= nsig) {
+      raise_status(status, ST_EINVAL);
+      Q.slot_of[p] = -1;
+      continue;
+    }
+    const unsigned long long key = static_cast<unsigned long long>(__double_as_longlong(ep));
+    const uint32_t mask = uint32_t(Q.tsize - 1);
+    uint32_t h = mix64(key) & mask;
+    // the table has at least twice as many slots as pairs: a free or matching slot exists
+    for (int probe = 0; probe < Q.tsize; ++probe) {
+      const unsigned long long prev = atomicCAS(Q.keys + h, EMPTY_KEY, key);
+      if (prev == EMPTY_KEY || prev == key) break;
+      h = (h + 1) & mask;
+    }
+    Q.slot_of[p] = int(h);
+    atomicAdd(Q.cnt + h, 1);
+  }
+}
+
+// one CTA of 1024 threads per q: exclusive scan of the counts (list offsets) and compaction of
+// the occupied slots, in slot order
+__global__ void __launch_bounds__(1024) k_conv_scan(ConvLaunch L) {
+  const ConvQ& Q = L.Q[blockIdx.x];
+  if (Q.npair == 0) return;
+  __shared__ int sc[1024], so[1024];
+  const int per = (Q.tsize + 1023) / 1024;
+  const int b = threadIdx.x * per, e = min(Q.tsize, b + per);
+  int lc = 0, lo = 0;
+  for (int i = b; i < e; ++i) {
+    lc += Q.cnt[i];
+    lo += Q.cnt[i] > 0;
+  }
+  sc[threadIdx.x] = lc;
+  so[threadIdx.x] = lo;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {        // inclusive Hillis-Steele scan
+    int vc = 0, vo = 0;
+    if (threadIdx.x >= d) {
+      vc = sc[threadIdx.x - d];
+      vo = so[threadIdx.x - d];
+    }
+    __syncthreads();
+    sc[threadIdx.x] += vc;
+    so[threadIdx.x] += vo;
+    __syncthreads();
+  }
+  int rc = sc[threadIdx.x] - lc, ro = so[threadIdx.x] - lo;
+  for (int i = b; i < e; ++i) {
+    Q.off[i] = rc;
+    rc += Q.cnt[i];
+    if (Q.cnt[i] > 0) Q.occ[ro++] = i;
+  }
+  if (threadIdx.x == 1023) *Q.nocc = so[1023];
+}
+
+__global__ void k_conv_scatter(ConvLaunch L) {
+  const int64_t total = L.item0[L.nq];
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int q = find_q(L, e);
+    const int64_t p = e - L.item0[q];
+    const ConvQ& Q = L.Q[q];
+    const int h = Q.slot_of[p];
+    if (h < 0) continue;
+    Q.list[Q.off[h] + atomicAdd(Q.fill + h, 1)] = int(p);
+  }
+}
+
+__global__ void __launch_bounds__(CTHREADS) k_conv_slot(ConvLaunch L, int nw, OmegaArr om,
+                                                        OmegaArr om_out, int nw_out,
+                                                        double* __restrict__ sigma) {
+  extern __shared__ __align__(16) double csh[];
+  const int n = nw;                                       // pieces
+  double* S = csh;                                        // [n][4][nw]
+  cplx* K = reinterpret_cast<cplx*>(S + 4 * n * nw);      // [CIC][n][4]
+  cplx* T = K + CIC * n * 4;                              // [CIC][nw]
+  cplx* tl = T + CIC * nw;                                // [CIC]
+  __shared__ double lam[GW_MAX_NW], h[GW_MAX_NW];
+  const int tid = threadIdx.x;
+  if (tid < nw) lam[tid] = om.v[tid] / (1.0 + om.v[tid]);
+  __syncthreads();
+  if (tid < nw - 1) h[tid] = lam[tid + 1] - lam[tid];
+  __syncthreads();
+  const double wN = om.v[nw - 1];
+  // cardinal spline coefficients: the spline of the unit node vector e_j, piece by piece
+  for (int j = tid; j < nw; j += blockDim.x) {
+    double y[GW_MAX_NW], m[GW_MAX_NW], cp[GW_MAX_NW];
+    for (int i = 0; i < nw; ++i) y[i] = i == j ? 1.0 : 0.0;
+    spline_slopes(y, n, h, wN, m, cp);
+    for (int s = 0; s < n; ++s) {
+      double C[4];
+      piece_coeffs(y, m, lam, h, s, C);
+      for (int k = 0; k < 4; ++k) S[(s * 4 + k) * nw + j] = C[k];
+    }
+  }
+  __syncthreads();
+  const double f = -1.0 / (2.0 * 3.14159265358979323846);
+  const int nich = (nw_out + CIC - 1) / CIC;
+  for (int q = 0; q < L.nq; ++q) {
+    const ConvQ& Q = L.Q[q];
+    if (Q.npair == 0) continue;
+    const int64_t items = int64_t(*Q.nocc) * nich;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+      const int slot = Q.occ[it / nich];
+      const int i0 = int(it % nich) * CIC;
+      const int ni = min(CIC, nw_out - i0);
+      const double e = __longlong_as_double(static_cast<long long>(Q.keys[slot]));
+      // closed-form integrals of t^k against the kernel on every piece, and the tail
+      for (int x = tid; x < ni * (n + 1); x += blockDim.x) {
+        const int i = x / (n + 1), s = x % (n + 1);
+        const cplx A = mk(-e, om_out.v[i0 + i]);
+        if (s == n) {
+          tl[i] = tail_integral(A, 1.0, wN) + tail_integral(A, -1.0, wN);
+          continue;
+        }
+        const cplx bp = mk(-A.x, 1.0 - A.y);    // i - A
+        const cplx bm = mk(-A.x, -1.0 - A.y);   // -i - A
+        const double la = s == 0 ? 0.0 : lam[s - 1];
+        const double H = s == 0 ? lam[0] : h[s - 1];
+        cplx Ip[4], Im[4];
+        moments(A + la * bp, bp, H, Ip);
+        moments(A + la * bm, bm, H, Im);
+        for (int k = 0; k < 4; ++k)
+          K[(i * n + s) * 4 + k] = mk(0.0, -1.0) * (bp * Ip[k]) + mk(0.0, 1.0) * (bm * Im[k]);
+      }
+      __syncthreads();
+      for (int x = tid; x < ni * nw; x += blockDim.x) {
+        const int i = x / nw, j = x % nw;
+        cplx t = mk(0.0, 0.0);
+        for (int s = 0; s < n; ++s)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) t = t + S[(s * 4 + k) * nw + j] * K[(i * n + s) * 4 + k];
+        if (j == nw - 1) t = t + (wN * wN) * tl[i];
+        T[i * nw + j] = t;
+      }
+      __syncthreads();
+      const int np = Q.cnt[slot], base = Q.off[slot];
+      for (int x = tid; x < np * ni; x += blockDim.x) {
+        const int r = x / ni, i = x % ni;
+        const int p = Q.list[base + r];
+        cplx v = mk(0.0, 0.0);
+        for (int j = 0; j < nw; ++j) v = v + Q.c[size_t(j) * Q.npair + p] * T[i * nw + j];
+        double2* out = reinterpret_cast<double2*>(sigma) + size_t(Q.state[p]) * nw_out + i0 + i;
+        atomicAdd(&out->x, f * Q.wq * v.x);
+        atomicAdd(&out->y, f * Q.wq * v.y);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+static int conv_tsize(int64_t np) {
+  int64_t t = 64;
+  while (t < 2 * np) t <<= 1;
+  return int(t);
+}
+
+static size_t conv_q_bytes(int64_t np) {
+  const size_t t = size_t(conv_tsize(np));
+  return ws_round(t * 8) + 4 * ws_round(t * 4) + ws_round(256) + 2 * ws_round(size_t(np) * 4);
+}
+
+static size_t conv_smem(int nw) {
+  return size_t(4) * nw * nw * sizeof(double) + size_t(CIC) * nw * 4 * sizeof(cplx) +
+         size_t(CIC) * nw * sizeof(cplx) + size_t(CIC) * sizeof(cplx);
+}
+
+size_t convolve_workspace(int nq, const int64_t* npair, int, int) {
+  size_t b = 0;
+  for (int q = 0; q < nq; ++q)
+    if (npair[q] > 0) b += conv_q_bytes(npair[q]);
+  return b + 256;
+}
 
 int convolve(int nq, const double* wq, const int64_t* npair, int nw, const OmegaArr& om,
              const double* const* c, const int* const* pair_state, const double* const* eps,
-             int nw_out, const OmegaArr& om_out, int nsig, double* sigma, void*, size_t,
-             cudaStream_t s, const DeviceCtx& ctx) {
+             int nw_out, const OmegaArr& om_out, int nsig, double* sigma, void* ws,
+             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
   return convolve_acc(nq, wq, npair, nw, om, c, pair_state, eps, nw_out, om_out, nsig, sigma,
-                      false, s, ctx);
+                      false, ws, ws_bytes, s, ctx);
 }
 
 int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const OmegaArr& om,
                  const double* const* c, const int* const* pair_state, const double* const* eps,
                  int nw_out, const OmegaArr& om_out, int nsig, double* sigma, bool accumulate,
-                 cudaStream_t s, const DeviceCtx& ctx) {
+                 void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
   if (!accumulate)
     GW_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * 2 * size_t(nsig) * nw_out, s));
+  const size_t smem = conv_smem(nw);
+  {
+    static bool attr[64] = {};
+    if (!attr[ctx.device]) {
+      GW_CUDA_TRY(cudaFuncSetAttribute(k_conv_slot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(conv_smem(GW_MAX_NW))));
+      attr[ctx.device] = true;
+    }
+  }
+  WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
   for (int q0 = 0; q0 < nq; q0 += SMAXQ) {
-    int n = std::min(SMAXQ, nq - q0);
+    const int n = std::min(SMAXQ, nq - q0);
     ConvLaunch L{};
     L.nq = n;
-    L.item0[0] = 0;
+    int64_t slots = 0, pairs = 0;
+    std::vector<int64_t> s0(n + 1), p0(n + 1);
     for (int q = 0; q < n; ++q) {
-      L.c[q] = c[q0 + q];
-      L.state[q] = pair_state[q0 + q];
-      L.eps[q] = eps[q0 + q];
-      L.npair[q] = npair[q0 + q];
-      L.wq[q] = wq[q0 + q];
-      L.item0[q + 1] = L.item0[q] + npair[q0 + q] * nw_out;
+      ConvQ& Q = L.Q[q];
+      const int64_t np = npair[q0 + q];
+      Q.c = c[q0 + q];
+      Q.state = pair_state[q0 + q];
+      Q.eps = eps[q0 + q];
+      Q.npair = np;
+      Q.wq = wq[q0 + q];
+      Q.tsize = np > 0 ? conv_tsize(np) : 0;
+      s0[q] = slots;
+      p0[q] = pairs;
+      if (np > 0) {
+        const size_t t = size_t(Q.tsize);
+        Q.keys = static_cast<unsigned long long*>(cur.take(t * 8));
+        Q.cnt = static_cast<int*>(cur.take(t * 4));
+        Q.off = static_cast<int*>(cur.take(t * 4));
+        Q.fill = static_cast<int*>(cur.take(t * 4));
+        Q.occ = static_cast<int*>(cur.take(t * 4));
+        Q.nocc = static_cast<int*>(cur.take(256));
+        Q.slot_of = static_cast<int*>(cur.take(size_t(np) * 4));
+        Q.list = static_cast<int*>(cur.take(size_t(np) * 4));
+        if (!Q.keys || !Q.cnt || !Q.off || !Q.fill || !Q.occ || !Q.nocc || !Q.slot_of || !Q.list)
+          return set_error(GW_EWORKSPACE, "convolution workspace too small");
+      }
+      slots += Q.tsize;
+      pairs += np;
     }
-    const int64_t total = L.item0[n];
-    if (total == 0) continue;
-    const int64_t blocks = std::min<int64_t>((total + CTHREADS - 1) / CTHREADS, int64_t(ctx.sm_count) * 16);
-    k_convolve<<<unsigned(blocks), CTHREADS, 0, s>>>(L, nw, om, om_out, nw_out, nsig, sigma,
-                                                     ctx.status);
-    GW_LAUNCH_CHECK("k_convolve");
+    s0[n] = slots;
+    p0[n] = pairs;
+    if (pairs == 0) continue;
+    const unsigned grid_cap = unsigned(ctx.sm_count) * 8;
+    for (int q = 0; q <= n; ++q) L.item0[q] = s0[q];
+    k_conv_init<<<unsigned(std::min<int64_t>((slots + 255) / 256, grid_cap)), 256, 0, s>>>(L);
+    GW_LAUNCH_CHECK("k_conv_init");
+    for (int q = 0; q <= n; ++q) L.item0[q] = p0[q];
+    const unsigned pg = unsigned(std::min<int64_t>((pairs + 255) / 256, grid_cap));
+    k_conv_hash<<<pg, 256, 0, s>>>(L, nsig, ctx.status);
+    GW_LAUNCH_CHECK("k_conv_hash");
+    k_conv_scan<<<unsigned(n), 1024, 0, s>>>(L);
+    GW_LAUNCH_CHECK("k_conv_scan");
+    k_conv_scatter<<<pg, 256, 0, s>>>(L);
+    GW_LAUNCH_CHECK("k_conv_scatter");
+    const int nich = (nw_out + CIC - 1) / CIC;
+    const int64_t est = pairs * nich;          // upper bound on the slot items
+    const unsigned sg = unsigned(std::max<int64_t>(1, std::min<int64_t>(est, int64_t(ctx.sm_count) * 4)));
+    k_conv_slot<<<sg, CTHREADS, smem, s>>>(L, nw, om, om_out, nw_out, sigma);
+    GW_LAUNCH_CHECK("k_conv_slot");
   }
   return GW_OK;
 }

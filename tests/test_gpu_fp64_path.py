@@ -176,6 +176,30 @@ def test_convolution_stagewise(gw, nw):
     assert max_rel(sg, ref) <= 1e-11
 
 
+@pytest.mark.parametrize("nw,nwo", [(8, 37), (40, 16)])
+def test_convolution_shared_energies(gw, nw, nwo):
+    """Pairs that share energies (the weights are computed once per distinct energy of a q
+    point) over three q points of different sizes, one of them empty; 37 output frequencies
+    span three blocks of 16 (ragged), 40 nodes the larger spline bases."""
+    rng = np.random.default_rng(nw + nwo)
+    om = S.omega_mesh(nw)
+    om_out = np.concatenate([S.omega_mesh(nwo - 2), [-0.3, 120.0]])
+    nsig = 5
+    cs, sts, es, wq = [], [], [], [0.2, 0.5, 0.3]
+    for npair, nlev in ((300, 7), (0, 1), (57, 12)):
+        levels = np.concatenate([rng.uniform(-0.6, -0.01, nlev), rng.uniform(0.05, 2.5, nlev)])
+        eps = levels[rng.integers(0, len(levels), size=npair)]
+        c = -np.exp(-om[:, None] / rng.uniform(0.5, 5, size=npair)[None, :]) * rng.uniform(0.1, 2, npair)
+        cs.append(c)
+        es.append(eps)
+        sts.append(rng.integers(0, nsig, size=npair).astype(np.int32))
+    sg = gw.sigma_convolve(wq, [T(c) for c in cs], [T(x) for x in sts], [T(e) for e in es], om,
+                           om_out, nsig).cpu().numpy()
+    gw.check()
+    ref = OE.sigma_c(om, om_out, wq, cs, sts, es, nsig)
+    assert max_rel(sg, ref) <= 1e-11
+
+
 def test_fit_recovers_poles(gw):
     om = S.omega_mesh(24)
     rng = np.random.default_rng(3)
