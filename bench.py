@@ -232,6 +232,26 @@ class Pipeline:
         self.dist.allreduce_sum_(self.sigma)
         return gw.continue_fit(self.sigma, self.om_out, npole=2, sign=self.sign)
 
+    def step_from_host(self, host_M, host_d, host_Ms, copy_stream):
+        """One step whose inputs start in pinned host memory: the projections stream in q by q on
+        the copy stream while the polarization of the q before runs (gw.polarization_streamed);
+        the Sigma projections follow on the same copy stream."""
+        gw, torch = self.gw, self.torch
+        gw.polarization_streamed(host_M, host_d, self.om, self.wl.prefactor, self.prec,
+                                 dev_Ms=self.M, dev_deltas=self.delta, out=self.P, ws=self.ws_p,
+                                 copy_stream=copy_stream)
+        with torch.cuda.stream(copy_stream):
+            for dst, src in zip(self.Msig, host_Ms):
+                dst.copy_(src, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(copy_stream)
+        gw.screened_w(self.P, self.v, out=self.P, ws=self.ws_w)
+        torch.cuda.current_stream().wait_event(ev)
+        gw.sigma_c(list(self.wl.wq), self.Msig, self.pair_state, self.eps, self.P, self.om,
+                   self.om_out, self.nsig, precision=self.sprec, out=self.sigma, ws=self.ws_s)
+        self.dist.allreduce_sum_(self.sigma)
+        return gw.continue_fit(self.sigma, self.om_out, npole=2, sign=self.sign)
+
     def launches_per_step(self):
         nq = self.wl.nq
         if self.prec == "fp64":
@@ -351,16 +371,11 @@ def e2e_measure(pipe, args, world):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    copy_stream = torch.cuda.Stream()
     e0.record()
     d2h = 0
     for _ in range(steps):
-        for dst, src in zip(pipe.M, host_M):
-            dst.copy_(src, non_blocking=True)
-        for dst, src in zip(pipe.Msig, host_Ms):
-            dst.copy_(src, non_blocking=True)
-        for dst, src in zip(pipe.delta, host_d):
-            dst.copy_(src, non_blocking=True)
-        params, cost, iters, status = pipe.step()
+        params, cost, iters, status = pipe.step_from_host(host_M, host_d, host_Ms, copy_stream)
         out_p = params.to("cpu", non_blocking=False)
         out_s = pipe.sigma.to("cpu", non_blocking=False)
         d2h = out_p.numel() * out_p.element_size() + out_s.numel() * out_s.element_size()

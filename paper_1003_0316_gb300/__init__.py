@@ -192,6 +192,46 @@ def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=No
     return out
 
 
+def polarization_streamed(host_Ms, host_deltas, omega, prefactor, precision="bf16x3",
+                          dev_Ms=None, dev_deltas=None, out=None, ws=None, copy_stream=None):
+    """P[q] for projections that live in (pinned) host memory: the host-to-device copies run on a
+    copy stream, one q after the other, and the polarization of each q starts on the current
+    stream as soon as its inputs have arrived, so the transfer of q + 1 overlaps the tensor-core
+    work of q. dev_Ms / dev_deltas: device buffers (allocated if None); ws: a workspace for the
+    largest single q. Returns the list of P (complex128 [nw][N_b][N_b])."""
+    om, nw = _om(omega)
+    nq = len(host_Ms)
+    cur = torch.cuda.current_stream()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=dev)
+    if dev_Ms is None:
+        dev_Ms = [torch.empty(m.shape, dtype=m.dtype, device=dev) for m in host_Ms]
+    if dev_deltas is None:
+        dev_deltas = [torch.empty(d.shape, dtype=d.dtype, device=dev) for d in host_deltas]
+    if out is None:
+        out = [torch.empty((nw, m.shape[1], m.shape[1]), dtype=torch.complex128, device=dev)
+               for m in host_Ms]
+    if ws is None:
+        prec = PRECISIONS.get(precision, precision)
+        need = max(polarization_workspace([m.shape[0]], [m.shape[1]], nw, prec) for m in host_Ms)
+        ws = torch.empty(max(int(need), 1), dtype=torch.uint8, device=dev)
+    cs.wait_stream(cur)               # earlier work on the current stream is done with the buffers
+    ready = []
+    with torch.cuda.stream(cs):
+        for q in range(nq):
+            dev_Ms[q].copy_(host_Ms[q], non_blocking=True)
+            dev_deltas[q].copy_(host_deltas[q], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(cs)
+            ready.append(ev)
+    for q in range(nq):
+        cur.wait_event(ready[q])
+        polarization([dev_Ms[q]], [dev_deltas[q]], omega, prefactor, precision, out=[out[q]], ws=ws)
+    for t in list(dev_Ms) + list(dev_deltas):
+        t.record_stream(cs)
+    return out
+
+
 def polarization_extrapolar(Ms, deltas, dbars, Cs, dbar_kns, omega, prefactor, precision="fp64",
                             fs=None, f_kns=None, out=None, ws=None):
     """P^EX[q]: the kept transitions at their own energies and every band beyond the cutoff
