@@ -684,20 +684,53 @@ static void q_sizes(int64_t K, int ncol, int precision, int64_t* nch, int64_t* k
   *nbi = (ncol + TM - 1) / TM;
 }
 
+// q points are processed in groups: preparation of the group's q, then one HERK launch over
+// them. A group closes once it holds GROUP_ITEMS_PER_SM work items per SM (or TQ q points), so
+// large q run one at a time (measured faster than one launch over many large q) and small q
+// share a launch; the workspace holds one group at a time. The grouping uses the complex tile
+// count for real and complex projections alike, so the workspace query and the call agree.
+constexpr int64_t GROUP_ITEMS_PER_SM = 4;
+
+static size_t q_bytes(int64_t K, int ncol, int nw, int precision) {
+  int64_t nch, kpad;
+  int nbi;
+  q_sizes(K, ncol, precision, &nch, &kpad, &nbi);
+  return ws_round(size_t(nw) * size_t(kpad) * sizeof(float))          // weights
+         + ws_round(size_t(nbi) * TM * size_t(kpad) * sizeof(float))  // chunk-major copy
+         + ws_round(size_t(nbi) * size_t(nch) * CHUNK_BYTES);         // pre-split B tiles
+}
+
+// first q of every group, and the end (nq)
+static void tc_groups(int nq, const int64_t* K, const int* nb, int nw, int sm,
+                      std::vector<int>& start) {
+  start.clear();
+  int64_t items = 0;
+  int n = 0;
+  for (int q = 0; q < nq; ++q) {
+    if (n == 0 || items >= GROUP_ITEMS_PER_SM * sm || n == TQ) {
+      start.push_back(q);
+      items = 0;
+      n = 0;
+    }
+    items += K[q] > 0 ? int64_t(tile_count(2 * nb[q], nullptr)) * nw : 0;
+    ++n;
+  }
+  start.push_back(nq);
+}
+
 size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision) {
   int sm = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
-  size_t b = ws_round(size_t(sm) * TN * TM * sizeof(double));
-  for (int q = 0; q < nq; ++q) {
-    int64_t nch, kpad;
-    int nbi;
-    q_sizes(K[q], 2 * nb[q], precision, &nch, &kpad, &nbi);   // complex size: an upper bound
-    b += ws_round(size_t(nw) * size_t(kpad) * sizeof(float));            // weights
-    b += ws_round(size_t(nbi) * TM * size_t(kpad) * sizeof(float));       // chunk-major copy
-    b += ws_round(size_t(nbi) * size_t(nch) * CHUNK_BYTES);              // pre-split B tiles
+  std::vector<int> start;
+  tc_groups(nq, K, nb, nw, sm, start);
+  size_t group_max = 0;
+  for (size_t g = 0; g + 1 < start.size(); ++g) {
+    size_t b = 0;
+    for (int q = start[g]; q < start[g + 1]; ++q) b += q_bytes(K[q], 2 * nb[q], nw, precision);
+    group_max = std::max(group_max, b);
   }
-  return b;
+  return ws_round(size_t(sm) * TN * TM * sizeof(double)) + group_max;
 }
 
 template <bool BF16, int MODE>
@@ -730,53 +763,58 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
   WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
   double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
   if (!acc64) return set_error(GW_EWORKSPACE, "internal: tensor-core workspace too small");
-  std::vector<float*> sw(nq), xT(nq);
-  std::vector<char*> bsp(nq);
-  std::vector<int64_t> kp(nq);
+  const size_t group_base = cur.used;
+  std::vector<int64_t> Ks(nq);
+  std::vector<int> nbs(nq);
   for (int q = 0; q < nq; ++q) {
-    int64_t nch, kpad;
-    int nbi;
-    q_sizes(qs[q].K, cpb * qs[q].nb, precision, &nch, &kpad, &nbi);
-    kp[q] = kpad;
-    sw[q] = static_cast<float*>(cur.take(size_t(nw) * size_t(kpad) * sizeof(float)));
-    xT[q] = static_cast<float*>(cur.take(size_t(nbi) * TM * size_t(kpad) * sizeof(float)));
-    bsp[q] = static_cast<char*>(cur.take(size_t(nbi) * size_t(nch) * CHUNK_BYTES));
-    if (kpad == 0) continue;
-    if (!sw[q] || !xT[q] || !bsp[q]) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
-    int64_t blocks = std::min<int64_t>((kpad + 255) / 256, int64_t(ctx.sm_count) * 8);
-    k_abs_weights_f32<<<unsigned(blocks), 256, 0, s>>>(qs[q].K, kpad, qs[q].delta, qs[q].dbar,
-                                                       qs[q].f, pref, nw, om, sw[q], ctx.status);
-    GW_LAUNCH_CHECK("k_abs_weights_f32");
-    const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbi));
-    if (nch > 2147483647LL) return set_error(GW_EINVAL, "too many transitions for one q");
-    if (bf)
-      k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K,
-                                         cpb * qs[q].nb, kpad, nch, xT[q], bsp[q]);
-    else
-      k_prep_tc<false><<<pg, 128, 0, s>>>(static_cast<const float*>(qs[q].M), qs[q].K,
-                                          cpb * qs[q].nb, kpad, nch, xT[q], bsp[q]);
-    GW_LAUNCH_CHECK("k_prep_tc");
+    Ks[q] = qs[q].K;
+    nbs[q] = qs[q].nb;
   }
+  std::vector<int> start;
+  tc_groups(nq, Ks.data(), nbs.data(), nw, ctx.sm_count, start);
   const size_t smem = NSB * STAGE_STRIDE + 1024;
-  for (int q0 = 0; q0 < nq; q0 += TQ) {
-    int n = std::min(TQ, nq - q0);
+  for (size_t g = 0; g + 1 < start.size(); ++g) {
+    const int q0 = start[g], n = start[g + 1] - start[g];
+    cur.used = group_base;               // the previous group's launch is ordered before this one
     TcLaunch L{};
     L.nq = n;
     L.nw = nw;
     int64_t item = 0;
-    for (int q = 0; q < n; ++q) {
-      const PolQ& Q = qs[q0 + q];
-      L.xT[q] = xT[q0 + q];
-      L.bsp[q] = bsp[q0 + q];
-      L.s[q] = sw[q0 + q];
-      L.P[q] = reinterpret_cast<double2*>(Q.P);
-      L.K[q] = Q.K;
-      L.kpad[q] = kp[q0 + q];
-      L.nb[q] = Q.nb;
-      L.ntile[q] = tile_count(cpb * Q.nb, &L.nbi[q]);
-      L.nbj[q] = L.nbi[q];
-      L.item0[q] = item;
-      item += int64_t(L.ntile[q]) * nw;
+    for (int i = 0; i < n; ++i) {
+      const PolQ& Q = qs[q0 + i];
+      int64_t nch, kpad;
+      int nbi;
+      q_sizes(Q.K, cpb * Q.nb, precision, &nch, &kpad, &nbi);
+      float* sw = static_cast<float*>(cur.take(size_t(nw) * size_t(kpad) * sizeof(float)));
+      float* xT = static_cast<float*>(cur.take(size_t(nbi) * TM * size_t(kpad) * sizeof(float)));
+      char* bsp = static_cast<char*>(cur.take(size_t(nbi) * size_t(nch) * CHUNK_BYTES));
+      if (kpad > 0) {
+        if (!sw || !xT || !bsp) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
+        int64_t blocks = std::min<int64_t>((kpad + 255) / 256, int64_t(ctx.sm_count) * 8);
+        k_abs_weights_f32<<<unsigned(blocks), 256, 0, s>>>(Q.K, kpad, Q.delta, Q.dbar, Q.f, pref,
+                                                           nw, om, sw, ctx.status);
+        GW_LAUNCH_CHECK("k_abs_weights_f32");
+        const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbi));
+        if (nch > 2147483647LL) return set_error(GW_EINVAL, "too many transitions for one q");
+        if (bf)
+          k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
+                                             kpad, nch, xT, bsp);
+        else
+          k_prep_tc<false><<<pg, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
+                                              kpad, nch, xT, bsp);
+        GW_LAUNCH_CHECK("k_prep_tc");
+      }
+      L.xT[i] = xT;
+      L.bsp[i] = bsp;
+      L.s[i] = sw;
+      L.P[i] = reinterpret_cast<double2*>(Q.P);
+      L.K[i] = Q.K;
+      L.kpad[i] = kpad;
+      L.nb[i] = Q.nb;
+      L.ntile[i] = tile_count(cpb * Q.nb, &L.nbi[i]);
+      L.nbj[i] = L.nbi[i];
+      L.item0[i] = item;
+      item += int64_t(L.ntile[i]) * nw;
     }
     L.item0[n] = item;
     if (item == 0) continue;
