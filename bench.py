@@ -253,14 +253,29 @@ class Pipeline:
         return gw.continue_fit(self.sigma, self.om_out, npole=2, sign=self.sign)
 
     def launches_per_step(self):
-        nq = self.wl.nq
+        """Kernel launches of the library in one step (the code paths of the step's calls)."""
+        import torch
+        nq, nw = self.wl.nq, self.wl.nw
         if self.prec == "fp64":
-            p = 2
+            p = 2                                   # FP64 HERK + fixed-order reduction
         else:
-            p = 2 * nq + 1          # weights + prep per q, one HERK launch
-        w = (nq * self.wl.nw + 255) // 256
-        s = 1 + nq + 1             # pair coefficients, reductions, convolution
-        return p + w + s + 1       # + LM fit
+            # weights + prep per q; one HERK launch per group of q (a group closes at 4 work
+            # items per SM; items = upper 128-tiles of the real 2 N_b x 2 N_b Gram x frequencies)
+            sm = torch.cuda.get_device_properties(self.dev).multi_processor_count
+            groups, items = 0, None
+            for nb in self.wl.nb:
+                t = (2 * nb + 127) // 128
+                if items is None or items >= 4 * sm:
+                    groups, items = groups + 1, 0
+                items += t * (t + 1) // 2 * nw
+            p = 2 * nq + groups
+        w = (nq * nw + 255) // 256                  # dielectric: 256 systems per launch
+        if self.sprec == "fp64":
+            s = 1 + nq                              # pair coefficients + per-q reductions
+        else:
+            s = 2 * nq + 1                          # A copy + B split per q, one HERK launch
+        s += 5                                      # convolution: init, hash, scan, scatter, slot
+        return p + w + s + 1                        # + LM fit
 
 
 def run_gpu(args, rank, world):

@@ -241,12 +241,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int u = int(k % SUB);
         const uint64_t gg = g0 + uint64_t(r_first + 2 * (k / SUB));
         const int slot = int(gg % NSA), st = int(gg % NSB);
-        if (u == 0 && (!warp_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, status) ||
-                       !warp_wait(&emptyA[slot], (uint32_t(gg / NSA) & 1) ^ 1, &s_abort, status)))
+        // the weights arrive with the round's B stage; the chunk is scaled and split before the
+        // wait for the A slot, so that work overlaps the MMAs still reading the slot
+        if (u == 0 && !warp_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, status))
           return false;
         const float4* sw =
             reinterpret_cast<const float4*>(ring + st * STAGE_STRIDE + STAGE_BYTES) + u * CH4;
-        const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * (SUB * 32) + u * 32;
+        uint32_t hw[2][8], lw[2][8];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {               // halves of the chunk: 8 TMEM words each
           float y[CH / 2];
@@ -259,10 +260,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             y[4 * e + 2] = wv.z * xv.z;
             y[4 * e + 3] = wv.w * xv.w;
           }
-          uint32_t hw[8], lw[8];
-          split_words<BF16>(y, hw, lw, 8);
-          tc::tmem_st8(base + h * 8, hw);
-          tc::tmem_st8(base + 16 + h * 8, lw);
+          split_words<BF16>(y, hw[h], lw[h], 8);
+        }
+        if (u == 0 && !warp_wait(&emptyA[slot], (uint32_t(gg / NSA) & 1) ^ 1, &s_abort, status))
+          return false;
+        const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * (SUB * 32) + u * 32;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tc::tmem_st8(base + h * 8, hw[h]);
+          tc::tmem_st8(base + 16 + h * 8, lw[h]);
         }
         if (u == SUB - 1) {
           tc::tmem_wait_st();
@@ -605,10 +611,14 @@ __global__ void k_prep_xpad(const float* __restrict__ x, int64_t nrow, int ncol,
 // Hermitian W^c (R[2I+a][2J+b] = Re W_IJ for a = b, -Im W_IJ for (a,b) = (0,1), Im W_IJ for
 // (1,0)), split and swizzled like the polarization's B tiles, [c block][k chunk].
 template <bool BF16>
-__global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W, int nb,
-                                                   int64_t nch, char* __restrict__ bsp) {
+__global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W0, int nb,
+                                                   int64_t nch, char* __restrict__ bsp0,
+                                                   int64_t jstride) {
   constexpr int CH = BF16 ? 32 : 16;
   constexpr int EPC = CH / 4;
+  // frequency j = blockIdx.z: its W^c and its own B tiles
+  const double2* __restrict__ W = W0 + size_t(blockIdx.z) * nb * nb;
+  char* __restrict__ bsp = bsp0 + size_t(blockIdx.z) * size_t(jstride);
   const int cb = blockIdx.y;
   const int64_t ch = blockIdx.x;
   const int n = threadIdx.x;
@@ -885,16 +895,14 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
       k_prep_xpad<16><<<xg, 256, 0, s>>>(static_cast<const float*>(Msig[q]), npair[q], 2 * nb[q],
                                          nrowp, kpad, xp[q]);
     GW_LAUNCH_CHECK("k_prep_xpad");
-    const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbj));
-    for (int j = 0; j < nw; ++j) {
-      const double2* W = reinterpret_cast<const double2*>(Wc[q]) + size_t(j) * nb[q] * nb[q];
-      char* dst = bsp[q] + size_t(j) * nbj * nch * CHUNK_BYTES;
-      if (bf)
-        k_prep_quad<true><<<pg, 128, 0, s>>>(W, nb[q], nch, dst);
-      else
-        k_prep_quad<false><<<pg, 128, 0, s>>>(W, nb[q], nch, dst);
-      GW_LAUNCH_CHECK("k_prep_quad");
-    }
+    const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbj), static_cast<unsigned>(nw));
+    const double2* W = reinterpret_cast<const double2*>(Wc[q]);
+    const int64_t jstride = int64_t(nbj) * nch * CHUNK_BYTES;
+    if (bf)
+      k_prep_quad<true><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
+    else
+      k_prep_quad<false><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
+    GW_LAUNCH_CHECK("k_prep_quad");
   }
   const size_t smem = NSB * STAGE_STRIDE + 1024;
   for (int q0 = 0; q0 < nq; q0 += TQ) {
