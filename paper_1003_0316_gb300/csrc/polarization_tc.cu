@@ -27,7 +27,7 @@
 //                lane quadrant; set g mod 2 (warps 4 (g mod 2) .. + 3) takes round g and
 //                owns slot g mod 2;
 //   warp 8       one thread issues the bulk copies of a round's pre-split B tiles and
-//                weights into a 6-stage shared-memory ring;
+//                weights into a 4-stage shared-memory ring;
 //   warps 9-10   one thread each issues the MMAs (A from TMEM, B from shared memory) of the
 //                rounds of one accumulator, and tcgen05.commit;
 //   warps 11-14  epilogue, one per lane quadrant: tcgen05.ld of the finished accumulator
@@ -55,7 +55,7 @@ constexpr int TM = 128;          // real Gram rows per tile (A operand, in TMEM)
 constexpr int TN = 128;          // real Gram columns per tile (B operand, in shared memory)
 constexpr int SWB = 64;          // bytes of K per B row per chunk (64-byte swizzle)
 constexpr int SUB = 2;           // 64-byte K chunks per barrier round
-constexpr int NSB = 6;           // B stages (rounds) in shared memory
+constexpr int NSB = 4;           // B stages (rounds) in shared memory
 constexpr int NSA = 2;           // A slots (rounds) in TMEM: one per A set
 constexpr int B_TILE = TN * SWB;                 // 8 KB: one chunk's hi (or lo) tile
 constexpr int CHUNK_BYTES = 2 * B_TILE;          // hi + lo of one chunk (pre-split layout)
