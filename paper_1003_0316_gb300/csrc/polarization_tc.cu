@@ -12,15 +12,16 @@
 //
 // Accuracy: the tensor core adds into its FP32 accumulator with truncation, which
 // biases a long chain of additions toward zero (about 2e-8 of the running value per
-// MMA). Every round of two 64-byte K chunks (2 x 16 TF32 or 2 x 32 BF16 transitions, 12
-// MMAs) therefore starts a fresh accumulator; the epilogue adds each round's result into
-// FP32 running sums kept in TMEM (round to nearest) and folds them into FP64 every 256
-// rounds (FP64 reductions performed at L2 into per-CTA sums), so no truncating chain is
-// longer than 12 MMAs; the round-to-nearest FP32 sums add only unbiased errors that
-// average out over the folds.
+// MMA). A round is two 64-byte K chunks (2 x 16 TF32 or 2 x 32 BF16 transitions, 12 MMAs);
+// every drain period of PL = 2 rounds on one accumulator therefore starts a fresh
+// accumulator; the epilogue adds each period's result into FP32 running sums kept in TMEM
+// (round to nearest) and folds them into FP64 every 256 periods (FP64 reductions performed
+// at L2 into per-CTA sums), so no truncating chain is longer than 24 MMAs (a bias of a few
+// 1e-7 of P); the round-to-nearest FP32 sums add only unbiased errors that average out
+// over the folds.
 //
 // Layout and roles (480 threads, one persistent CTA per SM; 512 TMEM columns):
-//   TMEM  cols [0,256): two accumulators (round g uses g mod 2);
+//   TMEM  cols [0,256): two accumulators (round g uses g mod 2, PL rounds per drain);
 //         cols [256,384): FP32 running sums;
 //         cols [384,512): two A slots of one round each (per chunk 16 columns hi + 16 lo).
 //   warps 0-7    A transform: scale x by s_tj, split, tcgen05.st into the A slot of their
@@ -71,6 +72,7 @@ constexpr int EPI_WARP0 = 11;    // warps 11-14: epilogue, one per lane quadrant
 constexpr int NEPI = 4;
 constexpr int NWARPS = EPI_WARP0 + NEPI;
 constexpr int NTHREADS = NWARPS * 32;
+constexpr int PL = 2;                            // own rounds per drain period and accumulator
 constexpr int FLUSH = 256;                       // periods per FP64 fold of the running sums
 constexpr int TQ = 64;
 constexpr uint64_t WAIT_LIMIT = 2000000000ull;   // ns: 2 s per bounded wait
@@ -347,12 +349,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int q, j, bi, bj;
         decode_item<QF>(L, item, q, j, bi, bj);
         const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
-        for (int64_t r = int64_t((mpar + 2 - uint32_t(g & 1)) & 1); r < nr; r += 2) {
+        const int64_t first = int64_t((mpar + 2 - uint32_t(g & 1)) & 1);
+        const int64_t nown = nr > first ? (nr - first + 1) / 2 : 0;   // own rounds of the item
+        for (int64_t i = 0; i < nown; ++i) {
+          const int64_t r = first + 2 * i;
+          // a drain period is PL own rounds (fewer at the end of the item)
+          const bool pstart = i % PL == 0, pend = i % PL == PL - 1 || i == nown - 1;
           const uint64_t gg = g + uint64_t(r);
           const int st = int(gg % NSB), slot = int(gg % NSA);
           if (!tc::mbar_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, WAIT_LIMIT) ||
               !tc::mbar_wait(&fullA[slot], uint32_t(gg / NSA) & 1, &s_abort, WAIT_LIMIT) ||
-              !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
+              (pstart && !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT))) {
             ok = false;
             break;
           }
@@ -367,7 +374,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const uint64_t dBh = dst + uint64_t((u * CHUNK_BYTES + ks * 32) >> 4);
               const uint64_t dBl = dst + uint64_t((u * CHUNK_BYTES + B_TILE + ks * 32) >> 4);
               const uint32_t ah = a0 + u * 32 + ks * 8, al = a0 + u * 32 + 16 + ks * 8;
-              const uint32_t acc0 = (u == 0 && ks == 0) ? 0u : 1u;
+              const uint32_t acc0 = (pstart && u == 0 && ks == 0) ? 0u : 1u;
               if (BF16) {
                 tc::mma_f16_ta(d, al, dBh, IDESC, acc0);
                 tc::mma_f16_ta(d, ah, dBl, IDESC, 1u);
@@ -381,8 +388,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc::mma_commit(&emptyB[st]);
           tc::mma_commit(&emptyA[slot]);
-          tc::mma_commit(&accf_bar[mpar]);
-          ++kb;
+          if (pend) {
+            tc::mma_commit(&accf_bar[mpar]);
+            ++kb;
+          }
         }
         g += uint64_t(nr);
       }
@@ -416,8 +425,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll 8
       for (int i = 0; i < TN; ++i) acc[size_t(i) * TM] = 0.0;
       bool sum_empty = true;
-      for (int64_t k = 0; k < nr; ++k, ++gp) {
-        const int buf = int((g0 + uint64_t(k)) & 1);
+      // drain periods in completion order: the accumulators alternate, starting with the one
+      // of the item's first round (its own-round count, and so its period count, is the larger)
+      const int buf0 = int(g0 & 1);
+      const int64_t np0 = ((nr + 1) / 2 + PL - 1) / PL, np1 = (nr / 2 + PL - 1) / PL;
+      for (int64_t k = 0; k < np0 + np1; ++k, ++gp) {
+        const int buf = (k & 1) ? buf0 ^ 1 : buf0;
         if (!warp_wait(&accf_bar[buf], kb[buf] & 1, &s_abort, status)) {
           stop = true;
           break;
