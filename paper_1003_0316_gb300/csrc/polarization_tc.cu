@@ -65,10 +65,11 @@ constexpr int STAGE_STRIDE = STAGE_BYTES + 1024; // + the round's weights slice,
 constexpr uint32_t ACC_COL = 0;                  // two accumulators: cols [0,128), [128,256)
 constexpr uint32_t SUM_COL = 2 * TN;             // FP32 running sums: cols [256,384)
 constexpr uint32_t A_COL = 3 * TN;               // A slots: [384,512), 64 columns each
-constexpr int A_WARPS = 8;       // warps 0-7: A transform, two sets of one warp per quadrant
-constexpr int PROD_WARP = 8;     // one thread: bulk copies of B tiles and weights
-constexpr int MMA_WARP = 9;      // warps 9 and 10 issue the MMAs of even and odd rounds
-constexpr int EPI_WARP0 = 11;    // warps 11-14: epilogue, one per lane quadrant
+constexpr int AH = 1;            // A-transform warps per lane quadrant and set (2: chunk halves)
+constexpr int A_WARPS = 8 * AH;  // warps 0-15: A transform, two sets of AH warps per quadrant
+constexpr int PROD_WARP = A_WARPS;       // one thread: bulk copies of B tiles and weights
+constexpr int MMA_WARP = A_WARPS + 1;    // two warps issue the MMAs of even and odd rounds
+constexpr int EPI_WARP0 = A_WARPS + 3;   // four warps: epilogue, one per lane quadrant
 constexpr int NEPI = 4;
 constexpr int NWARPS = EPI_WARP0 + NEPI;
 constexpr int NTHREADS = NWARPS * 32;
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mbar_init(&emptyB[i], 1);
     }
     for (int i = 0; i < NSA; ++i) {
-      tc::mbar_init(&fullA[i], 4);         // the 4 lane-quadrant warps handling the chunk
+      tc::mbar_init(&fullA[i], 4 * AH);    // the set's warps (AH per lane quadrant)
       tc::mbar_init(&emptyA[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -213,13 +214,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp < A_WARPS) {
     // ------------------------------------------------ A transform -> TMEM
-    // A set par (warps 4 par .. 4 par + 3, one per lane quadrant) takes the rounds g with
-    // g mod 2 == par (g counted over all items of this CTA) and owns A slot par. Each lane
-    // reads its column's values from the chunk-major copy (each float4 read of a warp is 512
-    // contiguous bytes; a ring of register buffers keeps the reads of the next chunks in
-    // flight while the current one is split) and the round's weights from the stage.
+    // A set par (warps 4 AH par .. 4 AH par + 4 AH - 1: AH per lane quadrant, each taking
+    // 1/AH of every chunk's K values) takes the rounds g with g mod 2 == par (g counted over
+    // all items of this CTA) and owns A slot par. Each lane reads its column's values from the
+    // chunk-major copy (each float4 read of a warp is 512 contiguous bytes; a ring of register
+    // buffers keeps the reads of the next chunks in flight while the current one is split) and
+    // the round's weights from the stage.
+    constexpr int CHW = CH4 / AH;               // float4 per lane and chunk for this warp
     constexpr int RA = BF16 ? 2 : 4;            // chunks of column reads in flight
-    const int qd = warp & 3, par = warp >> 2;
+    const int qd = warp & 3, hh = (warp >> 2) % AH, par = warp / (4 * AH);
     const int m = qd * 32 + lane;
     uint64_t g0 = 0;                  // rounds of the previous items
     bool stop = false;
@@ -232,14 +235,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t r_first = int64_t((par + 2 - int(g0 & 1)) & 1);
       const int64_t nown = nr > r_first ? (nr - r_first + 1) / 2 : 0;
       // own chunk k (k = 0 .. SUB nown - 1) is chunk SUB (r_first + 2 (k / SUB)) + k % SUB
-      auto load = [&](int64_t k, float4 (&rg)[CH4]) {
+      auto load = [&](int64_t k, float4 (&rg)[CHW]) {
         const int64_t c = SUB * (r_first + 2 * (k / SUB)) + k % SUB;
 #pragma unroll
-        for (int e = 0; e < CH4; ++e) rg[e] = __ldg(xc + size_t(c * CH4 + e) * TM);
+        for (int e = 0; e < CHW; ++e) rg[e] = __ldg(xc + size_t(c * CH4 + hh * CHW + e) * TM);
       };
       // chunk k of the own rounds: the first one of a round waits for the stage and the slot,
       // the last one signals the slot full
-      auto process = [&](int64_t k, const float4 (&xr)[CH4]) -> bool {
+      auto process = [&](int64_t k, const float4 (&xr)[CHW]) -> bool {
         const int u = int(k % SUB);
         const uint64_t gg = g0 + uint64_t(r_first + 2 * (k / SUB));
         const int slot = int(gg % NSA), st = int(gg % NSB);
@@ -249,28 +252,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           return false;
         const float4* sw =
             reinterpret_cast<const float4*>(ring + st * STAGE_STRIDE + STAGE_BYTES) + u * CH4;
-        uint32_t hw[2][8], lw[2][8];
+        constexpr int NH = 2 / AH;                  // chunk halves of this warp
+        uint32_t hw[NH][8], lw[NH][8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {               // halves of the chunk: 8 TMEM words each
+        for (int hl = 0; hl < NH; ++hl) {           // halves of the chunk: 8 TMEM words each
+          const int h = hh * NH + hl;
           float y[CH / 2];
 #pragma unroll
           for (int e = 0; e < CH4 / 2; ++e) {
-            const float4 xv = xr[h * (CH4 / 2) + e];
+            const float4 xv = xr[hl * (CH4 / 2) + e];
             const float4 wv = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : sw[h * (CH4 / 2) + e];
             y[4 * e + 0] = wv.x * xv.x;
             y[4 * e + 1] = wv.y * xv.y;
             y[4 * e + 2] = wv.z * xv.z;
             y[4 * e + 3] = wv.w * xv.w;
           }
-          split_words<BF16>(y, hw[h], lw[h], 8);
+          split_words<BF16>(y, hw[hl], lw[hl], 8);
         }
         if (u == 0 && !warp_wait(&emptyA[slot], (uint32_t(gg / NSA) & 1) ^ 1, &s_abort, status))
           return false;
         const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * (SUB * 32) + u * 32;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          tc::tmem_st8(base + h * 8, hw[h]);
-          tc::tmem_st8(base + 16 + h * 8, lw[h]);
+        for (int hl = 0; hl < NH; ++hl) {
+          const int h = hh * NH + hl;
+          tc::tmem_st8(base + h * 8, hw[hl]);
+          tc::tmem_st8(base + 16 + h * 8, lw[hl]);
         }
         if (u == SUB - 1) {
           tc::tmem_wait_st();
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       };
       const int64_t nk = SUB * nown;
       // ring of RA register buffers: the reads of the next RA - 1 own chunks are in flight
-      float4 X[RA][CH4];
+      float4 X[RA][CHW];
 #pragma unroll
       for (int v = 0; v < RA - 1; ++v)
         if (v < nk) load(v, X[v]);
@@ -438,16 +444,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ++kb[buf];
         tc::tc_fence_after();
 #pragma unroll 1
-        for (int cb = 0; cb < TN / 32; ++cb) {
-          uint32_t va[32], vs[32];
-          tc::tmem_ld32_nowait(lane_base + ACC_COL + buf * TN + cb * 32, va);
-          if (!sum_empty) tc::tmem_ld32_nowait(lane_base + SUM_COL + cb * 32, vs);
+        for (int cb = 0; cb < TN / 16; ++cb) {
+          uint32_t va[16], vs[16];
+          tc::tmem_ld16_nowait(lane_base + ACC_COL + buf * TN + cb * 16, va);
+          if (!sum_empty) tc::tmem_ld16_nowait(lane_base + SUM_COL + cb * 16, vs);
           tc::tmem_wait_ld();
-          float v[32];
+          float v[16];
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
+          for (int i = 0; i < 16; ++i)
             v[i] = sum_empty ? __uint_as_float(va[i]) : __uint_as_float(va[i]) + __uint_as_float(vs[i]);
-          tc::tmem_st32(lane_base + SUM_COL + cb * 32, v);
+          tc::tmem_st16(lane_base + SUM_COL + cb * 16, v);
         }
         tc::tmem_wait_st();
         sum_empty = false;
