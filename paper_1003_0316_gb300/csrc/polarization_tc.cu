@@ -13,12 +13,11 @@
 // Accuracy: the tensor core adds into its FP32 accumulator with truncation, which
 // biases a long chain of additions toward zero (about 2e-8 of the running value per
 // MMA). A round is two 64-byte K chunks (2 x 16 TF32 or 2 x 32 BF16 transitions, 12 MMAs);
-// every drain period of PL = 2 rounds on one accumulator therefore starts a fresh
-// accumulator; the epilogue adds each period's result into FP32 running sums kept in TMEM
-// (round to nearest) and folds them into FP64 every 256 periods (FP64 reductions performed
-// at L2 into per-CTA sums), so no truncating chain is longer than 24 MMAs (a bias of a few
-// 1e-7 of P); the round-to-nearest FP32 sums add only unbiased errors that average out
-// over the folds.
+// every drain period of PL rounds on one accumulator (PL = 1: one round) therefore starts a
+// fresh accumulator; the epilogue adds each period's result into FP32 running sums kept in
+// TMEM (round to nearest) and folds them into FP64 every 256 periods (FP64 reductions
+// performed at L2 into per-CTA sums), so no truncating chain is longer than 12 PL MMAs; the
+// round-to-nearest FP32 sums add only unbiased errors that average out over the folds.
 //
 // Layout and roles (480 threads, one persistent CTA per SM; 512 TMEM columns):
 //   TMEM  cols [0,256): two accumulators (round g uses g mod 2, PL rounds per drain);
@@ -73,7 +72,7 @@ constexpr int EPI_WARP0 = A_WARPS + 3;   // four warps: epilogue, one per lane q
 constexpr int NEPI = 4;
 constexpr int NWARPS = EPI_WARP0 + NEPI;
 constexpr int NTHREADS = NWARPS * 32;
-constexpr int PL = 2;                            // own rounds per drain period and accumulator
+constexpr int PL = 1;                            // own rounds per drain period and accumulator
 constexpr int FLUSH = 256;                       // periods per FP64 fold of the running sums
 constexpr int TQ = 64;
 constexpr uint64_t WAIT_LIMIT = 2000000000ull;   // ns: 2 s per bounded wait
