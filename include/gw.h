@@ -164,6 +164,16 @@ int gw_screened_w(int nq, const int* nb_host, int nw, const double* const* v_dev
                   const double* const* P_dev, double* const* Wc_dev,
                   void* ws_dev, size_t ws_bytes, gw_stream_t stream);
 
+/* The same for real symmetric P (inversion-symmetric systems, e.g. the GW_R32 polarization;
+ * Sec. II: with inversion symmetry the basis and the wave functions can be chosen real): the
+ * Cholesky factor and the inverse are real (a quarter of the FP64 work), the imaginary parts of
+ * P_dev are not read (taken as zero), W^c is written with zero imaginary parts. Same layouts
+ * and errors as gw_screened_w. Workspace: gw_screened_w_real_workspace() bytes. */
+size_t gw_screened_w_real_workspace(int nq, const int* nb_host, int nw);
+int gw_screened_w_real(int nq, const int* nb_host, int nw, const double* const* v_dev,
+                       const double* const* P_dev, double* const* Wc_dev,
+                       void* ws_dev, size_t ws_bytes, gw_stream_t stream);
+
 /* Variant of gw_screened_w that allocates nothing, for callers that cannot allocate
  * device memory when they call the library: for example a host application that has
  * already handed all device memory to its own pool, or a latency-critical loop in which a

@@ -61,6 +61,8 @@ _sig("gw_sigma_extrapolar", _i32, _i32, _P(_f64), _P(_i32), _i32, _P(_vp), _i32,
 _sig("gw_screened_w_workspace", _sz, _i32, _P(_i32), _i32)
 _sig("gw_screened_w", _i32, _i32, _P(_i32), _i32, _P(_vp), _P(_vp), _P(_vp), _vp, _sz, _vp)
 _sig("gw_screened_w_noalloc", _i32, _i32, _i32, _vp, _vp, _vp, _vp)
+_sig("gw_screened_w_real_workspace", _sz, _i32, _P(_i32), _i32)
+_sig("gw_screened_w_real", _i32, _i32, _P(_i32), _i32, _P(_vp), _P(_vp), _P(_vp), _vp, _sz, _vp)
 _sig("gw_sigma_pair_coeffs", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _i32, _P(_vp),
      _P(_vp), _i32, _vp, _sz, _vp)
 _sig("gw_sigma_convolve_workspace", _sz, _i32, _P(_i64))
@@ -278,21 +280,23 @@ def screened_w_workspace(nbs, nw):
     return _lib.gw_screened_w_workspace(len(nbs), _arr(_i32, nbs), nw)
 
 
-def screened_w(Ps, vs, out=None, ws=None):
-    """W^c[q] = v^1/2 (eps^-1 - 1) v^1/2, eps = 1 - v^1/2 P v^1/2 (complex128)."""
+def screened_w(Ps, vs, out=None, ws=None, real=False):
+    """W^c[q] = v^1/2 (eps^-1 - 1) v^1/2, eps = 1 - v^1/2 P v^1/2 (complex128). real=True: P is
+    real symmetric (inversion symmetry), solved with real arithmetic."""
     nq = len(Ps)
     nw = Ps[0].shape[0]
     nbs = [p.shape[1] for p in Ps]
     dev = Ps[0].device
     if out is None:
         out = [torch.empty_like(p) for p in Ps]
-    need = screened_w_workspace(nbs, nw)
+    wsq = _lib.gw_screened_w_real_workspace if real else _lib.gw_screened_w_workspace
+    need = wsq(nq, _arr(_i32, nbs), nw)
     if ws is None:
         wsb, wsp, wsn = _ws(need, dev)
     else:
         wsb, wsp, wsn = ws, _vp(ws.data_ptr()), ws.numel()
-    _raise(_lib.gw_screened_w(nq, _arr(_i32, nbs), nw, _ptrs(vs), _ptrs(Ps), _ptrs(out), wsp, wsn,
-                              _stream()))
+    fn = _lib.gw_screened_w_real if real else _lib.gw_screened_w
+    _raise(fn(nq, _arr(_i32, nbs), nw, _ptrs(vs), _ptrs(Ps), _ptrs(out), wsp, wsn, _stream()))
     return out
 
 

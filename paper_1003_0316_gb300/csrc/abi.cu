@@ -256,6 +256,31 @@ int gw_screened_w(int nq, const int* nb_host, int nw, const double* const* v_dev
   return dielectric_wc(nq, nb_host, nw, v_dev, P_dev, Wc_dev, ws_dev, ws_bytes, stream, ctx);
 }
 
+size_t gw_screened_w_real_workspace(int nq, const int* nb_host, int nw) {
+  if (nq < 1 || nb_host == nullptr || nw < 1 || nw > GW_MAX_NW) return 0;
+  for (int q = 0; q < nq; ++q)
+    if (nb_host[q] < 1 || nb_host[q] > 8192) return 0;
+  return dielectric_real_workspace(nq, nb_host, nw);
+}
+
+int gw_screened_w_real(int nq, const int* nb_host, int nw, const double* const* v_dev,
+                       const double* const* P_dev, double* const* Wc_dev, void* ws_dev,
+                       size_t ws_bytes, gw_stream_t stream) {
+  if (nq < 1 || nb_host == nullptr) return set_error(GW_EINVAL, "nq < 1 or NULL nb_host");
+  if (nw < 1 || nw > GW_MAX_NW) return set_error(GW_EINVAL, "nw=%d outside [1, %d]", nw, GW_MAX_NW);
+  if (v_dev == nullptr || P_dev == nullptr || Wc_dev == nullptr)
+    return set_error(GW_EINVAL, "NULL v_dev, P_dev or Wc_dev array");
+  for (int q = 0; q < nq; ++q) {
+    if (nb_host[q] < 1 || nb_host[q] > 8192) return set_error(GW_EINVAL, "nb[%d]=%d", q, nb_host[q]);
+    if (!v_dev[q] || !P_dev[q] || !Wc_dev[q]) return set_error(GW_EINVAL, "NULL pointer for q=%d", q);
+  }
+  int rc = check_ws(ws_dev, ws_bytes, dielectric_real_workspace(nq, nb_host, nw));
+  if (rc) return rc;
+  DeviceCtx ctx;
+  if ((rc = device_ctx(&ctx))) return rc;
+  return dielectric_wc_real(nq, nb_host, nw, v_dev, P_dev, Wc_dev, ws_dev, ws_bytes, stream, ctx);
+}
+
 int gw_screened_w_noalloc(int nb, int nw, const double* v_dev, const double* P_dev,
                           double* Wc_dev, gw_stream_t stream) {
   if (nb < 1 || nb > 8192) return set_error(GW_EINVAL, "nb=%d outside [1, 8192]", nb);

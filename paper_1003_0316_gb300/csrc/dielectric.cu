@@ -21,64 +21,95 @@ constexpr int DB = 32;        // tile edge
 constexpr int DLD = DB + 1;   // padded smem row
 constexpr int DTHREADS = 256;
 
-struct DieSys {
+// One system. P and W^c are complex128 in global memory; the factor, the inverse and the
+// panel (E, T) and the shared-memory tiles hold T: double2 for Hermitian systems, double for
+// real symmetric ones (inversion-symmetric systems: the imaginary parts of P are zero and are
+// not read, W^c is written with zero imaginary parts).
+template <typename T>
+struct DieSysT {
   const double2* P;
   double2* Wc;
   const double* v;
-  double2* E;      // N x N workspace (factor / inverse)
-  double2* T;      // N x DB workspace panel
+  T* E;      // N x N workspace (factor / inverse)
+  T* Tp;     // N x DB workspace panel
   int n;
 };
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
+// scalar operations for the complex and the real systems
+__device__ __forceinline__ double re_(double2 a) { return a.x; }
+__device__ __forceinline__ double re_(double a) { return a; }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double cconj(double a) { return a; }
 __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
   acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
   acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
 }
+__device__ __forceinline__ void cfma(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void csubmul(double2& x, double2 a, double2 b) {   // x -= a b
+  x.x -= a.x * b.x - a.y * b.y;
+  x.y -= a.x * b.y + a.y * b.x;
+}
+__device__ __forceinline__ void csubmul(double& x, double a, double b) { x -= a * b; }
+__device__ __forceinline__ double2 scal(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double scal(double a, double s) { return a * s; }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double csub(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 add_re(double2 a, double d) { return make_double2(a.x + d, a.y); }
+__device__ __forceinline__ double add_re(double a, double d) { return a + d; }
+__device__ __forceinline__ bool fin(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+__device__ __forceinline__ bool fin(double a) { return isfinite(a); }
+template <typename T> __device__ __forceinline__ T real_of(double d);
+template <> __device__ __forceinline__ double2 real_of<double2>(double d) { return make_double2(d, 0.0); }
+template <> __device__ __forceinline__ double real_of<double>(double d) { return d; }
+template <typename T> __device__ __forceinline__ T from_c(double2 p);
+template <> __device__ __forceinline__ double2 from_c<double2>(double2 p) { return p; }
+template <> __device__ __forceinline__ double from_c<double>(double2 p) { return p.x; }
+__device__ __forceinline__ double2 to_c(double2 a) { return a; }
+__device__ __forceinline__ double2 to_c(double a) { return make_double2(a, 0.0); }
 
 // Load a DB x DB tile of a row-major N x N (ld) matrix at (r0, c0) into smem.
 // mode 0: plain; mode 1: keep only the lower triangle (col <= row), zeros elsewhere.
-__device__ __forceinline__ void load_tile(double2* S, const double2* A, int ld, int n_rows,
-                                          int n_cols, int r0, int c0, int mode) {
+template <typename T>
+__device__ __forceinline__ void load_tile(T* S, const T* A, int ld, int n_rows, int n_cols, int r0,
+                                          int c0, int mode) {
   for (int e = threadIdx.x; e < DB * DB; e += DTHREADS) {
     int r = e / DB, c = e % DB;
     int R = r0 + r, C = c0 + c;
-    double2 v = make_double2(0.0, 0.0);
+    T v = T{};
     if (R < n_rows && C < n_cols && (mode == 0 || C <= R)) v = A[size_t(R) * ld + C];
     S[r * DLD + c] = v;
   }
 }
 
 // acc[b] += sum_k opA(tr, k) * SB[k][tc + 8 b]; opA = SA[tr][k] or conj(SA[k][tr]).
-template <bool A_CONJ_T>
-__device__ __forceinline__ void tile_mac(double2 acc[4], const double2* SA, const double2* SB,
-                                         int tr, int tc) {
+template <bool A_CONJ_T, typename T>
+__device__ __forceinline__ void tile_mac(T acc[4], const T* SA, const T* SB, int tr, int tc) {
 #pragma unroll 8
   for (int k = 0; k < DB; ++k) {
-    double2 a = A_CONJ_T ? cconj(SA[k * DLD + tr]) : SA[tr * DLD + k];
+    T a = A_CONJ_T ? cconj(SA[k * DLD + tr]) : SA[tr * DLD + k];
 #pragma unroll
     for (int b = 0; b < 4; ++b) cfma(acc[b], a, SB[k * DLD + tc + 8 * b]);
   }
 }
 
 constexpr int DMAXSYS = 256;   // systems per launch (descriptors passed by value)
-struct DieBatch {
-  DieSys s[DMAXSYS];
+template <typename T>
+struct DieBatchT {
+  DieSysT<T> s[DMAXSYS];
 };
 
-__global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, unsigned* status) {
-  extern __shared__ double2 smem[];
-  double2* SA = smem;
-  double2* SB = smem + DB * DLD;
-  double2* SD = smem + 2 * DB * DLD;
+template <typename T>
+__global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatchT<T> batch, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  T* smem = reinterpret_cast<T*>(dsm_raw);
+  T* SA = smem;
+  T* SB = smem + DB * DLD;
+  T* SD = smem + 2 * DB * DLD;
   __shared__ int s_fail;
 
-  const DieSys sys = batch.s[blockIdx.x];
+  const DieSysT<T> sys = batch.s[blockIdx.x];
   const int n = sys.n;
-  double2* E = sys.E;
+  T* E = sys.E;
   const int tid = threadIdx.x;
   const int tr = tid >> 3, tc = tid & 7;
   if (tid == 0) s_fail = 0;
@@ -87,10 +118,9 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
   for (size_t e = tid; e < size_t(n) * n; e += DTHREADS) {
     int r = int(e / n), c = int(e % n);
     double s = sqrt(sys.v[r] * sys.v[c]);
-    double2 p = sys.P[e];
-    double2 x = make_double2(-s * p.x, -s * p.y);
-    if (r == c) x.x += 1.0;
-    if (!isfinite(x.x) || !isfinite(x.y)) atomicOr(&s_fail, 2);
+    T x = scal(from_c<T>(sys.P[e]), -s);
+    if (r == c) x = add_re(x, 1.0);
+    if (!fin(x)) atomicOr(&s_fail, 2);
     E[e] = x;
   }
   __syncthreads();
@@ -104,27 +134,22 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
     __syncthreads();
     for (int c = 0; c < kb; ++c) {
       if (tid == 0) {
-        double d = SD[c * DLD + c].x;
+        double d = re_(SD[c * DLD + c]);
         if (!(d > 0.0) || !isfinite(d)) {
           atomicOr(&s_fail, 1);
           d = 1.0;
         }
-        SD[c * DLD + c] = make_double2(sqrt(d), 0.0);
+        SD[c * DLD + c] = real_of<T>(sqrt(d));
       }
       __syncthreads();
-      double dinv = 1.0 / SD[c * DLD + c].x;
-      for (int r = c + 1 + tid; r < kb; r += DTHREADS) {
-        double2 x = SD[r * DLD + c];
-        SD[r * DLD + c] = make_double2(x.x * dinv, x.y * dinv);
-      }
+      double dinv = 1.0 / re_(SD[c * DLD + c]);
+      for (int r = c + 1 + tid; r < kb; r += DTHREADS) SD[r * DLD + c] = scal(SD[r * DLD + c], dinv);
       __syncthreads();
       for (int e = tid; e < DB * DB; e += DTHREADS) {
         int r = e / DB, s = e % DB;
         if (r < kb && s > c && s <= r) {
-          double2 a = SD[r * DLD + c], b = cconj(SD[s * DLD + c]);
-          double2 x = SD[r * DLD + s];
-          x.x -= a.x * b.x - a.y * b.y;
-          x.y -= a.x * b.y + a.y * b.x;
+          T x = SD[r * DLD + s];
+          csubmul(x, SD[r * DLD + c], cconj(SD[s * DLD + c]));
           SD[r * DLD + s] = x;
         }
       }
@@ -137,22 +162,17 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
     __syncthreads();
     // panel: X L11^H = A21, one row per thread
     for (int r = k0 + kb + tid; r < n; r += DTHREADS) {
-      double2 x[DB];
-      double2* row = E + size_t(r) * n + k0;
+      T x[DB];
+      T* row = E + size_t(r) * n + k0;
 #pragma unroll
-      for (int c = 0; c < DB; ++c) x[c] = c < kb ? row[c] : make_double2(0.0, 0.0);
+      for (int c = 0; c < DB; ++c) x[c] = c < kb ? row[c] : T{};
 #pragma unroll
       for (int c = 0; c < DB; ++c) {
         if (c < kb) {
-          double2 s = x[c];
+          T s = x[c];
 #pragma unroll
-          for (int k = 0; k < c; ++k) {
-            double2 l = cconj(SD[c * DLD + k]);
-            s.x -= x[k].x * l.x - x[k].y * l.y;
-            s.y -= x[k].x * l.y + x[k].y * l.x;
-          }
-          double di = 1.0 / SD[c * DLD + c].x;
-          x[c] = make_double2(s.x * di, s.y * di);
+          for (int k = 0; k < c; ++k) csubmul(s, x[k], cconj(SD[c * DLD + k]));
+          x[c] = scal(s, 1.0 / re_(SD[c * DLD + c]));
         }
       }
 #pragma unroll
@@ -168,23 +188,19 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
         for (int e = tid; e < DB * DB; e += DTHREADS) {
           int k = e / DB, c = e % DB;
           int R = jt * DB + c;
-          double2 v = make_double2(0.0, 0.0);
+          T v = T{};
           if (R < n && k < kb) v = cconj(E[size_t(R) * n + k0 + k]);
           SB[k * DLD + c] = v;
         }
         __syncthreads();
-        double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0),
-                          make_double2(0, 0)};
+        T acc[4] = {T{}, T{}, T{}, T{}};
         tile_mac<false>(acc, SA, SB, tr, tc);
         int R = it * DB + tr;
         if (R < n) {
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             int C = jt * DB + tc + 8 * b;
-            if (C < n && C <= R) {
-              double2 x = E[size_t(R) * n + C];
-              E[size_t(R) * n + C] = make_double2(x.x - acc[b].x, x.y - acc[b].y);
-            }
+            if (C < n && C <= R) E[size_t(R) * n + C] = csub(E[size_t(R) * n + C], acc[b]);
           }
         }
         __syncthreads();
@@ -206,18 +222,17 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
     // invert the diagonal block: column c handled by thread c
     if (tid < DB) {
       int c = tid;
-      double2 z[DB];
+      T z[DB];
 #pragma unroll
-      for (int i = 0; i < DB; ++i) z[i] = make_double2(0.0, 0.0);
+      for (int i = 0; i < DB; ++i) z[i] = T{};
       if (c < kb) {
-        z[c] = make_double2(1.0 / SD[c * DLD + c].x, 0.0);
+        z[c] = real_of<T>(1.0 / re_(SD[c * DLD + c]));
 #pragma unroll
         for (int i = 0; i < DB; ++i) {
           if (i > c && i < kb) {
-            double2 s = make_double2(0.0, 0.0);
+            T s = T{};
             for (int k = c; k < i; ++k) cfma(s, SD[i * DLD + k], z[k]);
-            double di = 1.0 / SD[i * DLD + i].x;
-            z[i] = make_double2(-s.x * di, -s.y * di);
+            z[i] = scal(s, -1.0 / re_(SD[i * DLD + i]));
           }
         }
       }
@@ -235,8 +250,7 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
     if (k0 + kb < n) {
       // T[R] = Z22[R][:] * L21 over the trailing rows (Z22 already inverted)
       for (int it = kt + 1; it < nt; ++it) {
-        double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0),
-                          make_double2(0, 0)};
+        T acc[4] = {T{}, T{}, T{}, T{}};
         for (int st = kt + 1; st <= it; ++st) {
           load_tile(SA, E, n, n, n, it * DB, st * DB, st == it ? 1 : 0);   // Z22 block
           load_tile(SB, E, n, n, n, st * DB, k0, 0);                        // L21 block
@@ -247,26 +261,22 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
         int R = it * DB + tr;
         if (R < n) {
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            int C = tc + 8 * b;
-            sys.T[size_t(R) * DB + C] = acc[b];
-          }
+          for (int b = 0; b < 4; ++b) sys.Tp[size_t(R) * DB + tc + 8 * b] = acc[b];
         }
       }
       __syncthreads();
       // Z21 = -T * Z11
       for (int it = kt + 1; it < nt; ++it) {
-        load_tile(SA, sys.T, DB, n, DB, it * DB, 0, 0);
+        load_tile(SA, sys.Tp, DB, n, DB, it * DB, 0, 0);
         __syncthreads();
-        double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0),
-                          make_double2(0, 0)};
+        T acc[4] = {T{}, T{}, T{}, T{}};
         tile_mac<false>(acc, SA, SD, tr, tc);
         int R = it * DB + tr;
         if (R < n) {
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             int C = tc + 8 * b;
-            if (C < kb) E[size_t(R) * n + k0 + C] = make_double2(-acc[b].x, -acc[b].y);
+            if (C < kb) E[size_t(R) * n + k0 + C] = scal(acc[b], -1.0);
           }
         }
         __syncthreads();
@@ -282,8 +292,7 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
   // ---- phase 3: W^c = v^1/2 (Z^H Z - 1) v^1/2 ------------------------------
   for (int rt = 0; rt < nt; ++rt) {
     for (int ct = 0; ct <= rt; ++ct) {
-      double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0),
-                        make_double2(0, 0)};
+      T acc[4] = {T{}, T{}, T{}, T{}};
       for (int kt2 = rt; kt2 < nt; ++kt2) {
         load_tile(SA, E, n, n, n, kt2 * DB, rt * DB, 1);   // Z[K][R] (lower part)
         load_tile(SB, E, n, n, n, kt2 * DB, ct * DB, 1);   // Z[K][S]
@@ -298,15 +307,11 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
         for (int b = 0; b < 4; ++b) {
           int C = ct * DB + tc + 8 * b;
           if (C < n && C <= R) {
-            double2 x = acc[b];
-            if (C == R) {
-              x.x -= 1.0;
-              x.y = 0.0;
-            }
-            double s = sqrt(vr * sys.v[C]);
-            x = make_double2(s * x.x, s * x.y);
-            sys.Wc[size_t(R) * n + C] = x;
-            if (C != R) sys.Wc[size_t(C) * n + R] = cconj(x);
+            T x = acc[b];
+            if (C == R) x = real_of<T>(re_(x) - 1.0);
+            x = scal(x, sqrt(vr * sys.v[C]));
+            sys.Wc[size_t(R) * n + C] = to_c(x);
+            if (C != R) sys.Wc[size_t(C) * n + R] = to_c(cconj(x));
           }
         }
       }
@@ -314,52 +319,76 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatch batch, u
   }
 }
 
-size_t dielectric_workspace(int nq, const int* nb, int nw) {
-  size_t b = 0;
-  size_t nsys = 0;
-  for (int q = 0; q < nq; ++q) {
-    size_t n = size_t(nb[q]);
-    b += size_t(nw) * ws_round((n * n + n * DB) * sizeof(double2));
-    nsys += nw;
-  }
-  return b;
-}
-
-int dielectric_wc(int nq, const int* nb, int nw, const double* const* v, const double* const* P,
-                  double* const* Wc, void* ws, size_t ws_bytes, cudaStream_t s,
-                  const DeviceCtx& ctx) {
-  WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
-  std::vector<DieSys> sys;
-  for (int q = 0; q < nq; ++q) {
-    size_t n = size_t(nb[q]);
-    for (int j = 0; j < nw; ++j) {
-      DieSys d;
-      d.P = reinterpret_cast<const double2*>(P[q]) + size_t(j) * n * n;
-      d.Wc = reinterpret_cast<double2*>(Wc[q]) + size_t(j) * n * n;
-      d.v = v[q];
-      char* blk = static_cast<char*>(cur.take((n * n + n * DB) * sizeof(double2)));
-      if (!blk) return set_error(GW_EWORKSPACE, "internal: dielectric workspace too small");
-      d.E = reinterpret_cast<double2*>(blk);
-      d.T = d.E + n * n;
-      d.n = int(n);
-      sys.push_back(d);
-    }
-  }
-  size_t smem = 3 * DB * DLD * sizeof(double2);
+template <typename T>
+static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const DeviceCtx& ctx) {
+  const size_t smem = 3 * DB * DLD * sizeof(T);
   static bool attr_set[64] = {};
   if (!attr_set[ctx.device]) {
-    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(smem)));
     attr_set[ctx.device] = true;
   }
   for (size_t b0 = 0; b0 < sys.size(); b0 += DMAXSYS) {
     size_t nb_ = std::min<size_t>(DMAXSYS, sys.size() - b0);
-    DieBatch batch;
+    DieBatchT<T> batch;
     for (size_t i = 0; i < nb_; ++i) batch.s[i] = sys[b0 + i];
-    k_dielectric<<<unsigned(nb_), DTHREADS, smem, s>>>(batch, ctx.status);
+    k_dielectric<T><<<unsigned(nb_), DTHREADS, smem, s>>>(batch, ctx.status);
     GW_LAUNCH_CHECK("k_dielectric");
   }
   return GW_OK;
+}
+
+template <typename T>
+static size_t dielectric_ws_t(int nq, const int* nb, int nw) {
+  size_t b = 0;
+  for (int q = 0; q < nq; ++q) {
+    size_t n = size_t(nb[q]);
+    b += size_t(nw) * ws_round((n * n + n * DB) * sizeof(T));
+  }
+  return b;
+}
+
+template <typename T>
+static int dielectric_t(int nq, const int* nb, int nw, const double* const* v,
+                        const double* const* P, double* const* Wc, void* ws, size_t ws_bytes,
+                        cudaStream_t s, const DeviceCtx& ctx) {
+  WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
+  std::vector<DieSysT<T>> sys;
+  for (int q = 0; q < nq; ++q) {
+    size_t n = size_t(nb[q]);
+    for (int j = 0; j < nw; ++j) {
+      DieSysT<T> d;
+      d.P = reinterpret_cast<const double2*>(P[q]) + size_t(j) * n * n;
+      d.Wc = reinterpret_cast<double2*>(Wc[q]) + size_t(j) * n * n;
+      d.v = v[q];
+      char* blk = static_cast<char*>(cur.take((n * n + n * DB) * sizeof(T)));
+      if (!blk) return set_error(GW_EWORKSPACE, "internal: dielectric workspace too small");
+      d.E = reinterpret_cast<T*>(blk);
+      d.Tp = d.E + n * n;
+      d.n = int(n);
+      sys.push_back(d);
+    }
+  }
+  return launch_dielectric<T>(sys, s, ctx);
+}
+
+size_t dielectric_workspace(int nq, const int* nb, int nw) {
+  return dielectric_ws_t<double2>(nq, nb, nw);
+}
+size_t dielectric_real_workspace(int nq, const int* nb, int nw) {
+  return dielectric_ws_t<double>(nq, nb, nw);
+}
+
+int dielectric_wc(int nq, const int* nb, int nw, const double* const* v, const double* const* P,
+                  double* const* Wc, void* ws, size_t ws_bytes, cudaStream_t s,
+                  const DeviceCtx& ctx) {
+  return dielectric_t<double2>(nq, nb, nw, v, P, Wc, ws, ws_bytes, s, ctx);
+}
+
+int dielectric_wc_real(int nq, const int* nb, int nw, const double* const* v,
+                       const double* const* P, double* const* Wc, void* ws, size_t ws_bytes,
+                       cudaStream_t s, const DeviceCtx& ctx) {
+  return dielectric_t<double>(nq, nb, nw, v, P, Wc, ws, ws_bytes, s, ctx);
 }
 
 // ---------------------------------------------------------------- no-alloc variant
@@ -393,28 +422,21 @@ int dielectric_wc_noalloc(int nb, int nw, const double* v, const double* P, doub
   int rc = noalloc_scratch(ctx, &base);
   if (rc) return rc;
   const size_t fit = std::min<size_t>(GW_NOALLOC_SCRATCH_BYTES / per, DMAXSYS);
-  const size_t smem = 3 * DB * DLD * sizeof(double2);
-  static bool attr_set[64] = {};
-  if (!attr_set[ctx.device]) {
-    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(smem)));
-    attr_set[ctx.device] = true;
-  }
   for (int j0 = 0; j0 < nw; j0 += int(fit)) {
     const int cnt = std::min<int>(int(fit), nw - j0);
-    DieBatch batch;
+    std::vector<DieSysT<double2>> sys(cnt);
     for (int i = 0; i < cnt; ++i) {
-      DieSys& d = batch.s[i];
+      DieSysT<double2>& d = sys[i];
       const int j = j0 + i;
       d.P = reinterpret_cast<const double2*>(P) + size_t(j) * n * n;
       d.Wc = reinterpret_cast<double2*>(Wc) + size_t(j) * n * n;
       d.v = v;
       d.E = reinterpret_cast<double2*>(base + size_t(i) * per);
-      d.T = d.E + n * n;
+      d.Tp = d.E + n * n;
       d.n = nb;
     }
-    k_dielectric<<<unsigned(cnt), DTHREADS, smem, s>>>(batch, ctx.status);
-    GW_LAUNCH_CHECK("k_dielectric (no-alloc)");
+    rc = launch_dielectric<double2>(sys, s, ctx);
+    if (rc) return rc;
   }
   return GW_OK;
 }

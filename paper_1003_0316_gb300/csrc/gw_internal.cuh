@@ -110,6 +110,11 @@ size_t dielectric_workspace(int nq, const int* nb, int nw);
 int dielectric_wc(int nq, const int* nb, int nw, const double* const* v, const double* const* P,
                   double* const* Wc, void* ws, size_t ws_bytes, cudaStream_t s,
                   const DeviceCtx& ctx);
+// real symmetric systems (inversion symmetry): real factor and inverse, W^c imaginary parts 0
+size_t dielectric_real_workspace(int nq, const int* nb, int nw);
+int dielectric_wc_real(int nq, const int* nb, int nw, const double* const* v,
+                       const double* const* P, double* const* Wc, void* ws, size_t ws_bytes,
+                       cudaStream_t s, const DeviceCtx& ctx);
 
 // a5
 size_t paircoef_workspace(int nq, const int64_t* npair, const int* nb, int nw, int precision);

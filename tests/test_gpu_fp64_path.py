@@ -240,3 +240,33 @@ def test_end_to_end_small_fp64(gw):
     assert rel_fro(P[0].cpu().numpy(), Po) <= 1e-12
     assert rel_fro(W[0].cpu().numpy(), Wo) <= 1e-12
     assert max_rel(sig.cpu().numpy(), so) <= 1e-11
+
+
+@pytest.mark.parametrize("nb", [70, 33])
+def test_screened_w_real_symmetric(gw, nb):
+    """Inversion-symmetric systems: real projections give a real symmetric P; the real
+    dielectric solve (real Cholesky and inverse) matches the oracle and the complex solve."""
+    wl = S.tiny(nb=nb, nocc=3, nunocc=20, mesh=(2, 1, 2), nw=6, seed=nb + 3)
+    om = wl.omega()
+    Mr = wl.m_full(0).real
+    P = OP.polarization(Mr, wl.delta(0), om, wl.prefactor)
+    assert np.all(P.imag == 0)
+    v = wl.v(0)
+    Wr = gw.screened_w([T(P)], [T(v)], real=True)[0]
+    gw.check()
+    Wr = Wr.cpu().numpy()
+    ref = OS.screened_wc_all(P, v)
+    assert np.all(Wr.imag == 0)
+    assert max_rel(Wr, ref) <= 1e-12
+    Wc = gw.screened_w([T(P)], [T(v)])[0].cpu().numpy()
+    assert max_rel(Wr, Wc) <= 1e-13
+
+
+def test_screened_w_real_rejects_non_positive_definite(gw):
+    wl = S.tiny(nb=40, nocc=2, nunocc=6, mesh=(1, 1, 2), nw=4, seed=2)
+    P = np.zeros((4, 40, 40), dtype=np.complex128)
+    P[:, 5, 5] = 10.0          # eps_55 = 1 - 10 v_5 < 0: not positive definite
+    gw.screened_w([T(P)], [T(wl.v(0))], real=True)
+    with pytest.raises(gw.GWError) as e:
+        gw.check()
+    assert e.value.code == gw.GW_ENOTHPD
