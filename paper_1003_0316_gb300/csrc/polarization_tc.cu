@@ -443,16 +443,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ++kb[buf];
         tc::tc_fence_after();
 #pragma unroll 1
-        for (int cb = 0; cb < TN / 16; ++cb) {
-          uint32_t va[16], vs[16];
-          tc::tmem_ld16_nowait(lane_base + ACC_COL + buf * TN + cb * 16, va);
-          if (!sum_empty) tc::tmem_ld16_nowait(lane_base + SUM_COL + cb * 16, vs);
+        for (int cb = 0; cb < TN / 32; ++cb) {
+          uint32_t va[32], vs[32];
+          tc::tmem_ld32_nowait(lane_base + ACC_COL + buf * TN + cb * 32, va);
+          if (!sum_empty) tc::tmem_ld32_nowait(lane_base + SUM_COL + cb * 32, vs);
           tc::tmem_wait_ld();
-          float v[16];
+          float v[32];
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
+          for (int i = 0; i < 32; ++i)
             v[i] = sum_empty ? __uint_as_float(va[i]) : __uint_as_float(va[i]) + __uint_as_float(vs[i]);
-          tc::tmem_st16(lane_base + SUM_COL + cb * 16, v);
+          tc::tmem_st32(lane_base + SUM_COL + cb * 32, v);
         }
         tc::tmem_wait_st();
         sum_empty = false;
