@@ -40,7 +40,7 @@ METRIC = "P(iω)+Σ^c GFLOP/s and % of roofline, mixed vs FP64 on GB300 at ≤1e
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one bench launch of the
 # split-precision HERK, from the ncu capture summarised in profiles/ (one q cut to
 # K = 102,400, scaled by K x q to the 8 q of K = 409,600). Valid for the kernel as profiled.
-HERK_TRAFFIC_BYTES = {"tf32x3": 14.79e9 * 32, "bf16x3": 7.90e9 * 32}
+HERK_TRAFFIC_BYTES = {"tf32x3": 14.86e9 * 32, "bf16x3": 8.06e9 * 32}
 
 
 def workload_flops(wl):
