@@ -51,3 +51,53 @@ def test_host_side_argument_errors_without_gpu():
     assert rc == 1
     lib.gw_version.restype = ctypes.c_int
     assert lib.gw_version() >= 10000
+
+
+def test_extrapolar_and_real_entry_points_reject_bad_arguments_without_gpu():
+    """The extrapolar, real-dielectric and convolution entry points validate their host
+    arguments before any device call (GW_EINVAL = 1)."""
+    lib = _lib()
+    lib.gw_polarization_extrapolar.restype = ctypes.c_int
+    K = (ctypes.c_int64 * 1)(10)
+    nb = (ctypes.c_int * 1)(8)
+    om = (ctypes.c_double * 2)(0.5, 1.0)
+    # no Delta_bar / completeness arrays
+    rc = lib.gw_polarization_extrapolar(1, K, nb, None, 1, None, None, None, None, None, None,
+                                        None, ctypes.c_double(0.5), 2, om, None, 1, None,
+                                        ctypes.c_size_t(0), None)
+    assert rc == 1
+    lib.gw_sigma_extrapolar.restype = ctypes.c_int
+    rc = lib.gw_sigma_extrapolar(0, None, None, 4, None, 8, None, None, None, None, None, None,
+                                 8, None, None, None, None, ctypes.c_size_t(0), None)
+    assert rc == 1
+    lib.gw_screened_w_real.restype = ctypes.c_int
+    rc = lib.gw_screened_w_real(0, None, 4, None, None, None, None, ctypes.c_size_t(0), None)
+    assert rc == 1
+    lib.gw_sigma_convolve.restype = ctypes.c_int
+    wq = (ctypes.c_double * 1)(1.0)
+    npair = (ctypes.c_int64 * 1)(3)
+    rc = lib.gw_sigma_convolve(1, wq, npair, 3, om, None, None, None, 2, om, 1, None, None,
+                               ctypes.c_size_t(0), None)
+    assert rc == 1                       # fewer than 4 frequency nodes
+
+
+def test_polarization_workspace_holds_one_group_of_large_q():
+    """The tensor-core polarization prepares and launches q points group by group: eight q
+    that each fill the GPU need the workspace of one, while small q share a group."""
+    lib = _lib()
+    lib.gw_polarization_workspace.restype = ctypes.c_size_t
+    GW_BF16X3 = 2
+    big = lambda n: ((ctypes.c_int64 * n)(*([409600] * n)), (ctypes.c_int * n)(*([600] * n)))
+    K1, nb1 = big(1)
+    K8, nb8 = big(8)
+    w1 = lib.gw_polarization_workspace(1, K1, nb1, 16, GW_BF16X3)
+    w8 = lib.gw_polarization_workspace(8, K8, nb8, 16, GW_BF16X3)
+    assert w1 > 0 and w8 == w1
+    # small q: 2 x 2 upper tiles x 16 frequencies = 48 items each, so many share a group
+    Ks = (ctypes.c_int64 * 8)(*([1000] * 8))
+    nbs = (ctypes.c_int * 8)(*([100] * 8))
+    Ks1 = (ctypes.c_int64 * 1)(1000)
+    nbs1 = (ctypes.c_int * 1)(100)
+    ws8 = lib.gw_polarization_workspace(8, Ks, nbs, 16, GW_BF16X3)
+    ws1 = lib.gw_polarization_workspace(1, Ks1, nbs1, 16, GW_BF16X3)
+    assert ws8 > ws1
