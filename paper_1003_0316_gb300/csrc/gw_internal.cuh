@@ -180,8 +180,8 @@ int dielectric_wc_noalloc(int nb, int nw, const double* v, const double* P, doub
                           cudaStream_t s, const DeviceCtx& ctx);
 size_t quad_tc_workspace(int nq, const int64_t* npair, const int* nb, int nw, int precision);
 int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig, int nw,
-            const double* const* Wc, double* const* c, int precision, void* ws, size_t ws_bytes,
-            cudaStream_t s, const DeviceCtx& ctx);
+            const double* const* Wc, double* const* c, int precision, bool real, void* ws,
+            size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
 constexpr int MLP_NIN = 48, MLP_NH = 128, MLP_NOUT = 8;
 constexpr int MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NOUT * MLP_NH + MLP_NOUT;
 }  // namespace gw

@@ -609,16 +609,25 @@ __global__ void k_prep_xpad(const float* __restrict__ x, int64_t nrow, int ncol,
     const int64_t blk = e / (TM * (CH / 4) * nchp);
     const int64_t row = blk * TM + r;
     const int64_t c = ch * CH + g * 4;
-    // two float2 loads (8-byte aligned for any N_b; ncol = 2 N_b is even)
+    // two float2 loads when ncol is even (complex projections: 8-byte aligned for any N_b),
+    // four scalar loads when it is odd (real projections of an odd basis size)
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (row < nrow && c < ncol) {
-      const float2 a = __ldg(reinterpret_cast<const float2*>(x + row * ncol + c));
-      v.x = a.x;
-      v.y = a.y;
-      if (c + 2 < ncol) {
-        const float2 b = __ldg(reinterpret_cast<const float2*>(x + row * ncol + c + 2));
-        v.z = b.x;
-        v.w = b.y;
+      const float* src = x + row * ncol + c;
+      if ((ncol & 1) == 0) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(src));
+        v.x = a.x;
+        v.y = a.y;
+        if (c + 2 < ncol) {
+          const float2 b = __ldg(reinterpret_cast<const float2*>(src + 2));
+          v.z = b.x;
+          v.w = b.y;
+        }
+      } else {
+        v.x = __ldg(src);
+        if (c + 1 < ncol) v.y = __ldg(src + 1);
+        if (c + 2 < ncol) v.z = __ldg(src + 2);
+        if (c + 3 < ncol) v.w = __ldg(src + 3);
       }
     }
     reinterpret_cast<float4*>(xp)[e] = v;
@@ -627,8 +636,9 @@ __global__ void k_prep_xpad(const float* __restrict__ x, int64_t nrow, int ncol,
 
 // B operand of the quadratic form for one frequency: the real symmetric form R of the
 // Hermitian W^c (R[2I+a][2J+b] = Re W_IJ for a = b, -Im W_IJ for (a,b) = (0,1), Im W_IJ for
-// (1,0)), split and swizzled like the polarization's B tiles, [c block][k chunk].
-template <bool BF16>
+// (1,0)), or R = Re W^c for real projections (REAL), split and swizzled like the
+// polarization's B tiles, [c block][k chunk].
+template <bool BF16, bool REAL>
 __global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W0, int nb,
                                                    int64_t nch, char* __restrict__ bsp0,
                                                    int64_t jstride) {
@@ -641,7 +651,8 @@ __global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W
   const int64_t ch = blockIdx.x;
   const int n = threadIdx.x;
   const int c = cb * TN + n;
-  const int J = c >> 1, b = c & 1;
+  const int ncol = REAL ? nb : 2 * nb;
+  const int J = REAL ? c : c >> 1, b = c & 1;
   char* hi = bsp + (size_t(cb) * nch + ch) * CHUNK_BYTES;
 #pragma unroll
   for (int kc = 0; kc < 4; ++kc) {
@@ -649,11 +660,15 @@ __global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W
 #pragma unroll
     for (int e = 0; e < EPC; ++e) {
       const int64_t k = ch * CH + kc * EPC + e;
-      const int I = int(k >> 1), a = int(k & 1);
       float r = 0.0f;
-      if (c < 2 * nb && k < 2 * nb) {
-        const double2 w = W[size_t(I) * nb + J];
-        r = float(a == b ? w.x : (a == 0 ? -w.y : w.y));
+      if (c < ncol && k < ncol) {
+        if (REAL) {
+          r = float(W[size_t(k) * nb + J].x);
+        } else {
+          const int I = int(k >> 1), a = int(k & 1);
+          const double2 w = W[size_t(I) * nb + J];
+          r = float(a == b ? w.x : (a == 0 ? -w.y : w.y));
+        }
       }
       v[e] = r;
     }
@@ -855,11 +870,12 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
 }
 
 // ------------------------------------------------------------ pair coefficients
-static void quad_sizes(int64_t npair, int nb, int precision, int64_t* nch, int64_t* kpad,
+// ncol: columns of the real pair operand x (2 N_b for complex projections, N_b for real ones)
+static void quad_sizes(int64_t npair, int ncol, int precision, int64_t* nch, int64_t* kpad,
                        int64_t* nrowp, int* nbi, int* nbj) {
   const int64_t ch = chunk_rows(precision);
-  *nch = ((2 * int64_t(nb) + ch - 1) / ch + SUB - 1) / SUB * SUB;   // whole rounds
-  *nbj = (2 * nb + TN - 1) / TN;
+  *nch = ((int64_t(ncol) + ch - 1) / ch + SUB - 1) / SUB * SUB;   // whole rounds
+  *nbj = (ncol + TN - 1) / TN;
   *kpad = int64_t(*nbj) * TN;                 // multiple of 128 (>= every chunk end)
   *nbi = int((npair + TM - 1) / TM);
   *nrowp = int64_t(*nbi) * TM;
@@ -873,7 +889,7 @@ size_t quad_tc_workspace(int nq, const int64_t* npair, const int* nb, int nw, in
   for (int q = 0; q < nq; ++q) {
     int64_t nch, kpad, nrowp;
     int nbi, nbj;
-    quad_sizes(npair[q], nb[q], precision, &nch, &kpad, &nrowp, &nbi, &nbj);
+    quad_sizes(npair[q], 2 * nb[q], precision, &nch, &kpad, &nrowp, &nbi, &nbj);   // complex: a bound
     b += ws_round(size_t(nrowp) * size_t(kpad) * sizeof(float));
     b += ws_round(size_t(nw) * size_t(nbj) * size_t(nch) * CHUNK_BYTES);
   }
@@ -881,9 +897,10 @@ size_t quad_tc_workspace(int nq, const int64_t* npair, const int* nb, int nw, in
 }
 
 int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig, int nw,
-            const double* const* Wc, double* const* c, int precision, void* ws, size_t ws_bytes,
-            cudaStream_t s, const DeviceCtx& ctx) {
+            const double* const* Wc, double* const* c, int precision, bool real, void* ws,
+            size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
   const bool bf = precision == GW_BF16X3;
+  const int cpb = real ? 1 : 2;          // real operand columns per basis function
   WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
   double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
   if (!acc64) return set_error(GW_EWORKSPACE, "internal: tensor-core workspace too small");
@@ -894,7 +911,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
   for (int q = 0; q < nq; ++q) {
     int64_t nch, kpad, nrowp;
     int nbi, nbj;
-    quad_sizes(npair[q], nb[q], precision, &nch, &kpad, &nrowp, &nbi, &nbj);
+    quad_sizes(npair[q], cpb * nb[q], precision, &nch, &kpad, &nrowp, &nbi, &nbj);
     kp[q] = kpad;
     nchv[q] = nch;
     nbiv[q] = nbi;
@@ -907,19 +924,23 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
     const int64_t n4 = nrowp * (kpad / 4);
     const unsigned xg = unsigned(std::min<int64_t>((n4 + 255) / 256, int64_t(ctx.sm_count) * 16));
     if (bf)
-      k_prep_xpad<32><<<xg, 256, 0, s>>>(static_cast<const float*>(Msig[q]), npair[q], 2 * nb[q],
-                                         nrowp, kpad, xp[q]);
+      k_prep_xpad<32><<<xg, 256, 0, s>>>(static_cast<const float*>(Msig[q]), npair[q],
+                                         cpb * nb[q], nrowp, kpad, xp[q]);
     else
-      k_prep_xpad<16><<<xg, 256, 0, s>>>(static_cast<const float*>(Msig[q]), npair[q], 2 * nb[q],
-                                         nrowp, kpad, xp[q]);
+      k_prep_xpad<16><<<xg, 256, 0, s>>>(static_cast<const float*>(Msig[q]), npair[q],
+                                         cpb * nb[q], nrowp, kpad, xp[q]);
     GW_LAUNCH_CHECK("k_prep_xpad");
     const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbj), static_cast<unsigned>(nw));
     const double2* W = reinterpret_cast<const double2*>(Wc[q]);
     const int64_t jstride = int64_t(nbj) * nch * CHUNK_BYTES;
-    if (bf)
-      k_prep_quad<true><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
+    if (bf && real)
+      k_prep_quad<true, true><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
+    else if (bf)
+      k_prep_quad<true, false><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
+    else if (real)
+      k_prep_quad<false, true><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
     else
-      k_prep_quad<false><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
+      k_prep_quad<false, false><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
     GW_LAUNCH_CHECK("k_prep_quad");
   }
   const size_t smem = NSB * STAGE_STRIDE + 1024;
@@ -937,7 +958,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
       L.cq[q] = c[Q];
       L.bsp_jstride[q] = int64_t(nbjv[Q]) * nchv[Q] * CHUNK_BYTES;
       L.nrow[q] = npair[Q];
-      L.K[q] = npair[Q] > 0 ? 2 * int64_t(nb[Q]) : 0;
+      L.K[q] = npair[Q] > 0 ? int64_t(cpb) * nb[Q] : 0;
       L.kpad[q] = kp[Q];
       L.nb[q] = nb[Q];
       L.nbi[q] = nbiv[Q];

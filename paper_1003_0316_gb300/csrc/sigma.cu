@@ -143,7 +143,8 @@ int paircoef(int nq, const int64_t* npair, const int* nb, const void* const* Msi
              int nw, const double* const* Wc, double* const* c, int precision, void* ws,
              size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
   if (precision != GW_FP64)
-    return quad_tc(nq, npair, nb, Msig, nw, Wc, c, precision, ws, ws_bytes, s, ctx);
+    return quad_tc(nq, npair, nb, Msig, nw, Wc, c, precision, dtype == GW_R32, ws, ws_bytes, s,
+                   ctx);
   double* part = static_cast<double*>(ws);
   for (int q0 = 0; q0 < nq; q0 += SMAXQ) {
     int n = std::min(SMAXQ, nq - q0);

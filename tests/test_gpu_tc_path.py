@@ -281,3 +281,23 @@ def test_polarization_streamed_from_host(gw):
     gw.check()
     for a, b in zip(got, ref):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("nb", [37, 150])
+def test_tc_pair_coefficients_real(gw, prec, nb):
+    """Inversion-symmetric systems: real pair projections (float32) and a real symmetric W^c
+    (from the real dielectric solve): c_p = m_p^T W^c m_p with a real operand of width N_b
+    (odd N_b: unaligned rows), against the oracle on the same data."""
+    wl = S.tiny(nb=nb, nocc=3, nunocc=20, mesh=(2, 1, 2), nw=5, seed=nb + 11)
+    om = wl.omega()
+    P = OP.polarization(wl.m_full(0).real, wl.delta(0), om, wl.prefactor)
+    Wo = OS.screened_wc_all(P, wl.v(0))
+    Wd = gw.screened_w([T(P)], [T(wl.v(0))], real=True)[0]
+    Ms = wl.msig_rows(0).real.astype(np.float32)
+    c = gw.sigma_pair_coeffs([T(Ms)], [Wd], precision=prec)[0]
+    gw.check()
+    c = c.cpu().numpy()
+    ref = OE.pair_coefficients(Ms.astype(np.float64).astype(np.complex128), Wo)
+    err = float(np.abs(c - ref).max() / np.abs(ref).max())
+    assert err <= PAIR_BOUND[prec], err
