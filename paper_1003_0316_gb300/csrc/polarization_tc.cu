@@ -25,7 +25,8 @@
 //         cols [384,512): two A slots of one round each (per chunk 16 columns hi + 16 lo).
 //   warps 0-7    A transform: scale x by s_tj, split, tcgen05.st into the A slot of their
 //                lane quadrant; set g mod 2 (warps 4 (g mod 2) .. + 3) takes round g and
-//                owns slot g mod 2;
+//                owns slot g mod 2 (AH = 2 would give each quadrant two warps per set, each
+//                with half of every chunk: measured slower at the lower register cap);
 //   warp 8       one thread issues the bulk copies of a round's pre-split B tiles and
 //                weights into a 4-stage shared-memory ring;
 //   warps 9-10   one thread each issues the MMAs (A from TMEM, B from shared memory) of the
@@ -36,6 +37,9 @@
 // Every barrier is waited on only by threads that see each of its phases in order (a
 // parity wait cannot tell phase p from phase p + 2): stage and slot counts are even, so the
 // A set and the MMA issuer of round g also handled rounds g - NSB and g - NSA.
+// The same kernel forms the Sigma pair coefficients as a quadratic form (MODE 1: A = the pair
+// projections, B = the real form of W^c, c_p = row sums of (X R) o X) and the real polarization
+// of inversion-symmetric systems (MODE 2, real operand of width N_b).
 // Only tiles that meet the upper triangle (complex I <= J) are computed. Every mbarrier
 // wait is bounded; on expiry the CTA records a timeout in the status word and winds
 // down, waiting for its own MMAs before releasing TMEM.
