@@ -693,6 +693,74 @@ def run_case_extrapolar(args):
                       "sigma_extrapolar_ms": ms_sx, "n_sigma_states": nsig}), flush=True)
 
 
+def run_case_aux(args):
+    """Timings of the rows beside the main path, at the sizes of the 4x4x4-mesh workload
+    (N_b = 600, 16 frequencies, 16 Sigma states): the q = Gamma head/wings/body step on the
+    polarization of the augmented projections, the BZ constant (simple cubic, a = 10.26, 4x4x4),
+    the divergent Sigma^c term, the exchange self-energy over the 8 q (6,656 pairs each) and the
+    quasiparticle solve of 2e5 states. Prints one line of timings, not a bench line."""
+    import torch
+    import paper_1003_0316_gb300 as gw
+    wl = S.medium_mixed()
+    dev = lambda a, dt=None: torch.as_tensor(np.asarray(a), device="cuda", dtype=dt)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, n=None):
+        n = n or args.steps
+        for _ in range(args.warmup):
+            fn()
+        gw.check()
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        gw.check()
+        return e0.elapsed_time(e1) / n
+
+    nb, nw = wl.nb[0], wl.nw
+    om = wl.omega()
+    # q = Gamma: polarization of [p | M] for K = 102,400 transitions (BF16x3), then the FP64 step
+    K = 102400
+    M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[0], 0, K, nb + 3, dtype=torch.complex64)
+    Paug = gw.polarization([M], [dev(wl.delta(0)[:K])], om, wl.prefactor, "bf16x3")[0]
+    v = dev(wl.v(0))
+    ms_gamma = timed(lambda: gw.gamma_screened_w(Paug, v))
+    ms_bz = timed(lambda: gw.bz_constant_sc(10.26, 4), n=1)
+    cbz = gw.bz_constant_sc(10.26, 4)
+    Wc, head, _, _ = gw.gamma_screened_w(Paug, v)
+    est = dev(wl.state_energies())
+    sig = torch.zeros((len(wl.sigma_states()), nw), dtype=torch.complex128, device="cuda")
+    ms_div = timed(lambda: gw.sigma_div(om, head, cbz, (4 * 10.26) ** 3, est, om, sig))
+    # exchange over the 8 q
+    ps, es = zip(*[wl.sigma_pairs(i) for i in range(wl.nq)])
+    Ms = [gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[i], 0, len(ps[i]), wl.nb[i],
+                               dtype=torch.complex64) for i in range(wl.nq)]
+    pst = [dev(p, torch.int32) for p in ps]
+    eps = [dev(e) for e in es]
+    vs = [dev(wl.v(i)) for i in range(wl.nq)]
+    nsig = len(wl.sigma_states())
+    ms_x = timed(lambda: gw.sigma_x(list(wl.wq), Ms, pst, eps, vs, nsig, est, cbz,
+                                    (4 * 10.26) ** 3))
+    # quasiparticle solve of 2e5 states from model two-pole parameters
+    n = 200000
+    om24 = S.omega_mesh(24)
+    y, sg = S.model_sigma_curves(S.SEED_BASE + 107, 2048, om24)
+    prm, _, _, _ = gw.continue_fit(dev(y), om24, npole=2, sign=dev(sg))
+    prm = prm.repeat((n + 2047) // 2048, 1, 1)[:n].contiguous()
+    rng = np.random.default_rng(5)
+    sgn = np.tile(sg, (n + 2047) // 2048)[:n]
+    e_n = dev(np.where(sgn < 0, -rng.uniform(0.0, 0.5, n), rng.uniform(0.05, 2.0, n)))
+    sx = dev(np.where(sgn < 0, -rng.uniform(0.3, 1.0, n), -rng.uniform(0.0, 0.2, n)))
+    vx = dev(-rng.uniform(0.2, 0.8, n))
+    ms_qp = timed(lambda: gw.qp_solve(prm, e_n, sx, vx))
+    print(json.dumps({"case": "aux", "N_b": nb, "n_omega": nw, "gamma_screened_w_ms": ms_gamma,
+                      "bz_constant_ms": ms_bz, "sigma_div_ms": ms_div,
+                      "sigma_x_ms_8q": ms_x, "sigma_x_pairs_per_q": len(ps[0]),
+                      "qp_solve_ms": ms_qp, "qp_states": n}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -702,7 +770,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
     ap.add_argument("--real", action="store_true",
                     help="--case herk with real projections (inversion-symmetric systems)")
-    ap.add_argument("--case", default=None, choices=["herk", "fit", "batched", "extrapolar"],
+    ap.add_argument("--case", default=None,
+                    choices=["herk", "fit", "batched", "extrapolar", "aux"],
                     help="run one profiling case instead of the bench step")
     args = ap.parse_args()
     if args.case == "herk":
@@ -716,6 +785,9 @@ def main():
         return
     if args.case == "extrapolar":
         run_case_extrapolar(args)
+        return
+    if args.case == "aux":
+        run_case_aux(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
