@@ -218,12 +218,34 @@ static void plan_fp64(int nq, const int64_t* K, const int* nb, int nw, int sm_co
     tiles[q] = int64_t(T) * (T + 1) / 2;
     base += tiles[q] * nw;
   }
-  for (int q = 0; q < nq; ++q) {
-    // enough CTAs for two waves over the whole batch; at least 512 rows per split
-    int64_t want = (2LL * sm_count + base - 1) / std::max<int64_t>(base, 1);
-    int64_t maxs = std::max<int64_t>(1, K[q] / 512);
-    splits[q] = int(std::max<int64_t>(1, std::min<int64_t>(want, maxs)));
-  }
+  // K splits: at least four waves of CTAs (one CTA per SM: 136 registers x 256 threads) and
+  // whole waves as far as possible, since every CTA of a launch takes about the same time and a
+  // partly filled last wave idles the rest of the GPU; at least 512 rows per split. Among the
+  // split counts from the four-wave minimum to twice it, the smallest whose fill of the last
+  // wave is within 1 % of the best is taken.
+  const int64_t slots = std::max(1, sm_count);
+  const int64_t b = std::max<int64_t>(base, 1);
+  const int64_t s_lo = std::max<int64_t>(1, (4 * slots + b - 1) / b), s_hi = 2 * s_lo;
+  auto items_at = [&](int64_t sp) {
+    int64_t it = 0;
+    for (int q = 0; q < nq; ++q)
+      it += tiles[q] * nw * std::min<int64_t>(sp, std::max<int64_t>(1, K[q] / 512));
+    return it;
+  };
+  auto fill = [&](int64_t sp) {
+    const int64_t it = items_at(sp);
+    return double(it) / double((it + slots - 1) / slots * slots);
+  };
+  double best = 0.0;
+  for (int64_t sp = s_lo; sp <= s_hi; ++sp) best = std::max(best, fill(sp));
+  int64_t pick = s_lo;
+  for (int64_t sp = s_lo; sp <= s_hi; ++sp)
+    if (fill(sp) >= best - 0.01) {
+      pick = sp;
+      break;
+    }
+  for (int q = 0; q < nq; ++q)
+    splits[q] = int(std::max<int64_t>(1, std::min<int64_t>(pick, std::max<int64_t>(1, K[q] / 512))));
 }
 
 size_t pol_fp64_workspace(int nq, const int64_t* K, const int* nb, int nw) {
