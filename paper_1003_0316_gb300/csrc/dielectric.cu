@@ -5,9 +5,10 @@
 //   Z   = L^{-1}                  blocked triangular inversion
 //   W^c = v^1/2 (Z^H Z - 1) v^1/2
 //
-// One CTA per (q, frequency) system works through the three phases in place on a
-// workspace copy of eps, with 32x32 complex tiles staged in shared memory; each
-// thread owns one row and four columns of a tile. The phases are FP64-pipe bound:
+// One CTA per (q, frequency) system works through the factorisation and the inversion in
+// place on a workspace copy of eps, with 32x32 tiles staged in shared memory; each thread owns
+// one row and four columns of a tile. The last phase (W^c from the inverse factor) runs as a
+// second launch with one CTA per (system, 32-row block), so it uses every SM. The phases are FP64-pipe bound:
 // about 4 N^3 real flops per system (N^3/6 complex multiply-adds each).
 #include <vector>
 #include <algorithm>
@@ -289,30 +290,46 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatchT<T> batc
     __syncthreads();
   }
 
-  // ---- phase 3: W^c = v^1/2 (Z^H Z - 1) v^1/2 ------------------------------
-  for (int rt = 0; rt < nt; ++rt) {
-    for (int ct = 0; ct <= rt; ++ct) {
-      T acc[4] = {T{}, T{}, T{}, T{}};
-      for (int kt2 = rt; kt2 < nt; ++kt2) {
-        load_tile(SA, E, n, n, n, kt2 * DB, rt * DB, 1);   // Z[K][R] (lower part)
-        load_tile(SB, E, n, n, n, kt2 * DB, ct * DB, 1);   // Z[K][S]
-        __syncthreads();
-        tile_mac<true>(acc, SA, SB, tr, tc);
-        __syncthreads();
-      }
-      int R = rt * DB + tr;
-      if (R < n) {
-        double vr = sys.v[R];
+  // phase 3 (W^c from Z) runs as its own launch over (system, block row): k_dielectric_w
+}
+
+// ---- phase 3: W^c = v^1/2 (Z^H Z - 1) v^1/2, one CTA per (system, 32-row block rt) ---------
+// (the lower tiles ct <= rt of the block row and their Hermitian mirror)
+template <typename T>
+__global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> batch) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  T* smem = reinterpret_cast<T*>(dsm_raw);
+  T* SA = smem;
+  T* SB = smem + DB * DLD;
+  const DieSysT<T> sys = batch.s[blockIdx.x];
+  const int n = sys.n;
+  const int nt = (n + DB - 1) / DB;
+  const int rt = blockIdx.y;
+  if (rt >= nt) return;                      // whole CTA, before any barrier
+  const T* E = sys.E;
+  const int tid = threadIdx.x;
+  const int tr = tid >> 3, tc = tid & 7;
+  for (int ct = 0; ct <= rt; ++ct) {
+    T acc[4] = {T{}, T{}, T{}, T{}};
+    for (int kt2 = rt; kt2 < nt; ++kt2) {
+      load_tile(SA, E, n, n, n, kt2 * DB, rt * DB, 1);   // Z[K][R] (lower part)
+      load_tile(SB, E, n, n, n, kt2 * DB, ct * DB, 1);   // Z[K][S]
+      __syncthreads();
+      tile_mac<true>(acc, SA, SB, tr, tc);
+      __syncthreads();
+    }
+    int R = rt * DB + tr;
+    if (R < n) {
+      double vr = sys.v[R];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          int C = ct * DB + tc + 8 * b;
-          if (C < n && C <= R) {
-            T x = acc[b];
-            if (C == R) x = real_of<T>(re_(x) - 1.0);
-            x = scal(x, sqrt(vr * sys.v[C]));
-            sys.Wc[size_t(R) * n + C] = to_c(x);
-            if (C != R) sys.Wc[size_t(C) * n + R] = to_c(cconj(x));
-          }
+      for (int b = 0; b < 4; ++b) {
+        int C = ct * DB + tc + 8 * b;
+        if (C < n && C <= R) {
+          T x = acc[b];
+          if (C == R) x = real_of<T>(re_(x) - 1.0);
+          x = scal(x, sqrt(vr * sys.v[C]));
+          sys.Wc[size_t(R) * n + C] = to_c(x);
+          if (C != R) sys.Wc[size_t(C) * n + R] = to_c(cconj(x));
         }
       }
     }
@@ -322,18 +339,27 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatchT<T> batc
 template <typename T>
 static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const DeviceCtx& ctx) {
   const size_t smem = 3 * DB * DLD * sizeof(T);
+  const size_t smem_w = 2 * DB * DLD * sizeof(T);
   static bool attr_set[64] = {};
   if (!attr_set[ctx.device]) {
     GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(smem)));
+    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric_w<T>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_w)));
     attr_set[ctx.device] = true;
   }
   for (size_t b0 = 0; b0 < sys.size(); b0 += DMAXSYS) {
     size_t nb_ = std::min<size_t>(DMAXSYS, sys.size() - b0);
     DieBatchT<T> batch;
-    for (size_t i = 0; i < nb_; ++i) batch.s[i] = sys[b0 + i];
+    int ntmax = 1;
+    for (size_t i = 0; i < nb_; ++i) {
+      batch.s[i] = sys[b0 + i];
+      ntmax = std::max(ntmax, (batch.s[i].n + DB - 1) / DB);
+    }
     k_dielectric<T><<<unsigned(nb_), DTHREADS, smem, s>>>(batch, ctx.status);
     GW_LAUNCH_CHECK("k_dielectric");
+    k_dielectric_w<T><<<dim3(unsigned(nb_), unsigned(ntmax)), DTHREADS, smem_w, s>>>(batch);
+    GW_LAUNCH_CHECK("k_dielectric_w");
   }
   return GW_OK;
 }
