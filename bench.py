@@ -269,7 +269,7 @@ class Pipeline:
                     groups, items = groups + 1, 0
                 items += t * (t + 1) // 2 * nw
             p = 2 * nq + groups
-        w = (nq * nw + 255) // 256                  # dielectric: 256 systems per launch
+        w = 2 * ((nq * nw + 255) // 256)            # dielectric: factor/inverse + W^c launch
         if self.sprec == "fp64":
             s = 1 + nq                              # pair coefficients + per-q reductions
         else:
