@@ -269,7 +269,8 @@ class Pipeline:
                     groups, items = groups + 1, 0
                 items += t * (t + 1) // 2 * nw
             p = 2 * nq + groups
-        w = 2 * ((nq * nw + 255) // 256)            # dielectric: factor/inverse + W^c launch
+        w = 4 * ((nq * nw + 255) // 256)            # dielectric: factor, diagonal inverses,
+                                                    # inverse by block columns, W^c
         if self.sprec == "fp64":
             s = 1 + nq                              # pair coefficients + per-q reductions
         else:

@@ -5,10 +5,12 @@
 //   Z   = L^{-1}                  blocked triangular inversion
 //   W^c = v^1/2 (Z^H Z - 1) v^1/2
 //
-// One CTA per (q, frequency) system works through the factorisation and the inversion in
-// place on a workspace copy of eps, with 32x32 tiles staged in shared memory; each thread owns
-// one row and four columns of a tile. The last phase (W^c from the inverse factor) runs as a
-// second launch with one CTA per (system, 32-row block), so it uses every SM. The phases are FP64-pipe bound:
+// One CTA per (q, frequency) system factorises a workspace copy of eps in place, with 32x32
+// tiles staged in shared memory; each thread owns one row and four columns of a tile. The
+// inverse factor follows by block columns (the diagonal blocks inverted first, then one CTA
+// per (system, block column) for the forward substitution of that column), and W^c from the
+// inverse factor with one CTA per (system, 32-row block), so both use every SM. The
+// no-allocation entry point keeps the inverse inside the system's CTA (in place). The phases are FP64-pipe bound:
 // about 4 N^3 real flops per system (N^3/6 complex multiply-adds each).
 #include <vector>
 #include <algorithm>
@@ -32,7 +34,9 @@ struct DieSysT {
   double2* Wc;
   const double* v;
   T* E;      // N x N workspace (factor / inverse)
-  T* Tp;     // N x DB workspace panel
+  T* Tp;     // N x DB workspace panel (inverse inside the CTA)
+  T* Z;      // the inverse factor read by the W^c phase: E, or a buffer of its own
+  T* D;      // inverted diagonal blocks [nt][DB][DB] (inverse by block columns), or NULL
   int n;
 };
 
@@ -100,7 +104,8 @@ struct DieBatchT {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatchT<T> batch, unsigned* status) {
+__global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatchT<T> batch, unsigned* status,
+                                                         bool invert) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   T* smem = reinterpret_cast<T*>(dsm_raw);
   T* SA = smem;
@@ -213,6 +218,7 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatchT<T> batc
     if (tid == 0) raise_status(status, (s_fail & 1) ? ST_ENOTHPD : ST_ENONFINITE);
     return;
   }
+  if (!invert) return;   // the inverse follows by block columns (k_dielectric_dinv, _zcol)
 
   // ---- phase 2: Z = L^{-1}, lower, in place --------------------------------
   for (int kt = nt - 1; kt >= 0; --kt) {
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> ba
   const int nt = (n + DB - 1) / DB;
   const int rt = blockIdx.y;
   if (rt >= nt) return;                      // whole CTA, before any barrier
-  const T* E = sys.E;
+  const T* E = sys.Z;
   const int tid = threadIdx.x;
   const int tr = tid >> 3, tc = tid & 7;
   for (int ct = 0; ct <= rt; ++ct) {
@@ -336,6 +342,98 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> ba
   }
 }
 
+// ---- the inverse Z = L^{-1} by block columns (the columns of Z are independent forward
+// substitutions L Z_c = I_c): first every diagonal block inverted, one CTA per (system, block)
+template <typename T>
+__global__ void __launch_bounds__(DTHREADS) k_dielectric_dinv(const DieBatchT<T> batch) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  T* SD = reinterpret_cast<T*>(dsm_raw);
+  const DieSysT<T> sys = batch.s[blockIdx.x];
+  const int n = sys.n;
+  const int nt = (n + DB - 1) / DB;
+  const int r = blockIdx.y;
+  if (r >= nt) return;
+  const int k0 = r * DB;
+  const int kb = min(DB, n - k0);
+  load_tile(SD, sys.E, n, n, n, k0, k0, 1);
+  __syncthreads();
+  if (threadIdx.x < DB) {
+    const int c = threadIdx.x;
+    T z[DB];
+#pragma unroll
+    for (int i = 0; i < DB; ++i) z[i] = T{};
+    if (c < kb) {
+      z[c] = real_of<T>(1.0 / re_(SD[c * DLD + c]));
+#pragma unroll
+      for (int i = 0; i < DB; ++i) {
+        if (i > c && i < kb) {
+          T acc = T{};
+          for (int k = c; k < i; ++k) cfma(acc, SD[i * DLD + k], z[k]);
+          z[i] = scal(acc, -1.0 / re_(SD[i * DLD + i]));
+        }
+      }
+    }
+    T* Dr = sys.D + size_t(r) * DB * DB;
+#pragma unroll
+    for (int i = 0; i < DB; ++i) Dr[i * DB + c] = z[i];
+  }
+}
+
+// then one CTA per (system, block column c): for r = c, c + 1, ...
+//   Z[r][c] = D_r (delta_rc - sum_{k = c}^{r-1} L[r][k] Z[k][c])
+// with the earlier blocks Z[k][c] of the same column read back from global memory.
+template <typename T>
+__global__ void __launch_bounds__(DTHREADS) k_dielectric_zcol(const DieBatchT<T> batch) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  T* smem = reinterpret_cast<T*>(dsm_raw);
+  T* SA = smem;
+  T* SB = smem + DB * DLD;
+  const DieSysT<T> sys = batch.s[blockIdx.x];
+  const int n = sys.n;
+  const int nt = (n + DB - 1) / DB;
+  const int c = blockIdx.y;
+  if (c >= nt) return;                       // whole CTA, before any barrier
+  const int tid = threadIdx.x;
+  const int tr = tid >> 3, tc = tid & 7;
+  T* Z = sys.Z;
+  for (int r = c; r < nt; ++r) {
+    T out[4] = {T{}, T{}, T{}, T{}};
+    if (r == c) {
+      const T* Dr = sys.D + size_t(r) * DB * DB;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) out[b] = Dr[tr * DB + tc + 8 * b];
+    } else {
+      T acc[4] = {T{}, T{}, T{}, T{}};
+      for (int k = c; k < r; ++k) {
+        load_tile(SA, sys.E, n, n, n, r * DB, k * DB, 0);              // L[r][k]
+        load_tile(SB, Z, n, n, n, k * DB, c * DB, k == c ? 1 : 0);   // Z[k][c]
+        __syncthreads();
+        tile_mac<false>(acc, SA, SB, tr, tc);
+        __syncthreads();
+      }
+      // out = -D_r acc: the product tile in SB, D_r in SA
+#pragma unroll
+      for (int b = 0; b < 4; ++b) SB[tr * DLD + tc + 8 * b] = acc[b];
+      const T* Dr = sys.D + size_t(r) * DB * DB;
+      for (int e = tid; e < DB * DB; e += DTHREADS) SA[(e / DB) * DLD + e % DB] = Dr[e];
+      __syncthreads();
+      tile_mac<false>(out, SA, SB, tr, tc);
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < 4; ++b) out[b] = scal(out[b], -1.0);
+    }
+    const int R = r * DB + tr;
+    if (R < n) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int C = c * DB + tc + 8 * b;
+        if (C < n) Z[size_t(R) * n + C] = out[b];
+      }
+    }
+    __syncthreads();                          // this block row is read by the next ones
+  }
+}
+
 template <typename T>
 static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const DeviceCtx& ctx) {
   const size_t smem = 3 * DB * DLD * sizeof(T);
@@ -346,8 +444,11 @@ static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const
                                      int(smem)));
     GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric_w<T>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_w)));
+    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric_zcol<T>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_w)));
     attr_set[ctx.device] = true;
   }
+  const bool by_columns = !sys.empty() && sys[0].D != nullptr;
   for (size_t b0 = 0; b0 < sys.size(); b0 += DMAXSYS) {
     size_t nb_ = std::min<size_t>(DMAXSYS, sys.size() - b0);
     DieBatchT<T> batch;
@@ -356,8 +457,15 @@ static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const
       batch.s[i] = sys[b0 + i];
       ntmax = std::max(ntmax, (batch.s[i].n + DB - 1) / DB);
     }
-    k_dielectric<T><<<unsigned(nb_), DTHREADS, smem, s>>>(batch, ctx.status);
+    k_dielectric<T><<<unsigned(nb_), DTHREADS, smem, s>>>(batch, ctx.status, !by_columns);
     GW_LAUNCH_CHECK("k_dielectric");
+    if (by_columns) {
+      const dim3 g2(static_cast<unsigned>(nb_), static_cast<unsigned>(ntmax));
+      k_dielectric_dinv<T><<<g2, DTHREADS, DB * DLD * sizeof(T), s>>>(batch);
+      GW_LAUNCH_CHECK("k_dielectric_dinv");
+      k_dielectric_zcol<T><<<g2, DTHREADS, smem_w, s>>>(batch);
+      GW_LAUNCH_CHECK("k_dielectric_zcol");
+    }
     k_dielectric_w<T><<<dim3(unsigned(nb_), unsigned(ntmax)), DTHREADS, smem_w, s>>>(batch);
     GW_LAUNCH_CHECK("k_dielectric_w");
   }
@@ -369,7 +477,8 @@ static size_t dielectric_ws_t(int nq, const int* nb, int nw) {
   size_t b = 0;
   for (int q = 0; q < nq; ++q) {
     size_t n = size_t(nb[q]);
-    b += size_t(nw) * ws_round((n * n + n * DB) * sizeof(T));
+    const size_t nt = (n + DB - 1) / DB;
+    b += size_t(nw) * ws_round((2 * n * n + n * DB + nt * DB * DB) * sizeof(T));
   }
   return b;
 }
@@ -387,10 +496,13 @@ static int dielectric_t(int nq, const int* nb, int nw, const double* const* v,
       d.P = reinterpret_cast<const double2*>(P[q]) + size_t(j) * n * n;
       d.Wc = reinterpret_cast<double2*>(Wc[q]) + size_t(j) * n * n;
       d.v = v[q];
-      char* blk = static_cast<char*>(cur.take((n * n + n * DB) * sizeof(T)));
+      const size_t nt = (n + DB - 1) / DB;
+      char* blk = static_cast<char*>(cur.take((2 * n * n + n * DB + nt * DB * DB) * sizeof(T)));
       if (!blk) return set_error(GW_EWORKSPACE, "internal: dielectric workspace too small");
       d.E = reinterpret_cast<T*>(blk);
       d.Tp = d.E + n * n;
+      d.Z = d.Tp + n * DB;                    // the inverse by block columns
+      d.D = d.Z + n * n;
       d.n = int(n);
       sys.push_back(d);
     }
@@ -459,6 +571,8 @@ int dielectric_wc_noalloc(int nb, int nw, const double* v, const double* P, doub
       d.v = v;
       d.E = reinterpret_cast<double2*>(base + size_t(i) * per);
       d.Tp = d.E + n * n;
+      d.Z = d.E;                              // inverse in place, inside the CTA
+      d.D = nullptr;
       d.n = nb;
     }
     rc = launch_dielectric<double2>(sys, s, ctx);
