@@ -12,9 +12,11 @@ The metric is algorithmic GFLOP/s of P + the Sigma^c contraction per step:
 Inputs are synthetic (seeded Philox draws, see synth_inputs) and generated on the
 device; with N ranks each rank takes 8 further q points of the mesh (weak scaling) and the
 partial Sigma^c curves are summed over ranks before the fit.
-The default split precision is BF16x3; the sampled error of P against the oracle is
-measured in every run and reported beside the number, and the TF32x3 polarization is timed
-too (field "tf32x3_polarization").
+The default split precision of P is BF16x3 and that of the Sigma pair coefficients TF32x3
+(whose Sigma^c error at these sizes is 1e-6 Ha, against 2e-5 Ha for BF16x3); the error of P
+(sampled entries) and of one q's Sigma^c against the oracle are measured in every run and
+reported beside the number, and the TF32x3 polarization is timed too (field
+"tf32x3_polarization").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|tf32x3|fp64]
     python bench.py --impl reference ...   # the CPU FP64 oracle on a bounded sample
@@ -173,7 +175,7 @@ def run_reference(args, rank, world):
 class Pipeline:
     """Device-resident workload and one step of the hot path."""
 
-    def __init__(self, wl, precision, device):
+    def __init__(self, wl, precision, device, sigma_precision="tf32x3"):
         import torch
         import paper_1003_0316_gb300 as gw
         from paper_1003_0316_gb300 import distributed
@@ -193,7 +195,7 @@ class Pipeline:
         npair = [len(p) for p in ps]
         sig_cdt = torch.complex128 if precision == "fp64" else torch.complex64
         self.Msig = [gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[i], 0, npair[i], wl.nb[i],
-                                          dtype=sig_cdt) for i in range(wl.nq)]
+                                          dtype=sig_cdt).mul_(wl.msig_scale) for i in range(wl.nq)]
         self.nsig = len(wl.sigma_states())
         self.sign = torch.as_tensor(np.sign(wl.state_energies()), device=device)
         nw = wl.nw
@@ -204,7 +206,7 @@ class Pipeline:
                                 dtype=torch.uint8, device=device)
         self.ws_w = torch.empty(gw.screened_w_workspace(list(wl.nb), nw), dtype=torch.uint8,
                                 device=device)
-        sprec = precision if self._sigma_mixed_ok() else "fp64"
+        sprec = sigma_precision if (self._sigma_mixed_ok() and precision != "fp64") else "fp64"
         self.sprec = sprec
         if sprec == "fp64" and precision != "fp64":
             self.Msig = [m.to(torch.complex128) for m in self.Msig]
@@ -290,7 +292,7 @@ def run_gpu(args, rank, world):
     wl_all = S.medium_mixed_sharded(world)
     lo, hi = distributed.shard(wl_all.nq, rank, world)
     wl = wl_all.subset(range(lo, hi)) if world > 1 else wl_all
-    pipe = Pipeline(wl, args.precision, dev)
+    pipe = Pipeline(wl, args.precision, dev, sigma_precision=args.sigma_precision)
     gw = pipe.gw
     fp, fs = workload_flops(wl)
     step_flops = fp + fs
@@ -335,6 +337,7 @@ def run_gpu(args, rank, world):
     fp64 = fp64_sample(pipe) if args.precision != "fp64" else None
     tf32 = tf32_polarization(pipe) if args.precision == "bf16x3" else None
     err = sampled_error(pipe)
+    sig_err = sampled_sigma_error(pipe) if (rank == 0 and not args.no_sigma_check) else None
 
     if rank != 0:
         return
@@ -346,8 +349,8 @@ def run_gpu(args, rank, world):
         "metric": METRIC, "value": step_flops * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"tf32x3": "tf32x3+f32acc(P,Sigma)/f64(W,fit)",
-                  "bf16x3": "bf16x3+f32acc(P,Sigma)/f64(W,fit)", "fp64": "f64"}[args.precision],
+        "dtype": ("f64" if args.precision == "fp64" else
+                  f"{args.precision}+f32acc(P)/{pipe.sprec}+f32acc(Sigma)/f64(W,fit)"),
         "data": "synthetic (seeded Philox draws shaped like the paper's systems)",
         "config": {"workload": wl_all.name, "nq": wl_all.nq, "nq_per_rank": wl.nq,
                    "N_MPB": wl.nb[0], "K_per_q": wl.K(0),
@@ -370,6 +373,7 @@ def run_gpu(args, rank, world):
         "fp64_gpu_sample": fp64,
         "tf32x3_polarization": tf32,
         "sampled_rel_err_P": err,
+        "sampled_err_Sigma": sig_err,
     }
     if world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(wl)
@@ -470,6 +474,44 @@ def sampled_error(pipe, precision=None, rerun=True):
         Mc = Mc.astype(np.complex64).astype(np.complex128)
     ref = OP.polarization(Mc, wl.delta(iq), pipe.om, wl.prefactor)
     return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def sampled_sigma_error(pipe, iq=1):
+    """Sigma^c of one q (weight w_q) through the timed path's kernels and precisions against
+    the all-FP64 oracle chain on the same complex64-rounded projections (drawn on the host by
+    spawned worker processes, outside the timed region). Returns the largest absolute error in
+    Ha (the Sigma projections carry the workload's factor 2^-5, |Sigma^c| of physical size),
+    the same relative to max |Sigma|, and the relative Frobenius error of that q's P."""
+    import multiprocessing as mp
+    from oracle import chain as OCH
+    torch, gw, wl = pipe.torch, pipe.gw, pipe.wl
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, min(16, cores))) as pool:
+        Mh = S.m_rows_parallel(wl, iq, pool, dtype=np.complex64)
+        ps, eps = wl.sigma_pairs(iq)
+        Msh = wl.msig_rows(iq).astype(np.complex64)
+        nsig = pipe.nsig
+        Po, _, _, so = OCH.sigma_one_q(Mh.astype(np.complex128), wl.delta(iq), pipe.om,
+                                       wl.prefactor, wl.v(iq), Msh.astype(np.complex128), ps, eps,
+                                       wl.wq[iq], pipe.om_out, nsig, pool=pool)
+    t_oracle = time.perf_counter() - t0
+    dev = pipe.dev
+    P = gw.polarization([torch.as_tensor(Mh, device=dev)], [pipe.delta[iq]], pipe.om,
+                        wl.prefactor, pipe.prec)
+    eP = float(torch.linalg.vector_norm(P[0] - torch.as_tensor(Po, device=dev)) / np.linalg.norm(Po))
+    W = gw.screened_w(P, [pipe.v[iq]])
+    Ms = torch.as_tensor(Msh if pipe.sprec != "fp64" else Msh.astype(np.complex128), device=dev)
+    sig = gw.sigma_c([wl.wq[iq]], [Ms], [pipe.pair_state[iq]], [pipe.eps[iq]], W, pipe.om,
+                     pipe.om_out, nsig, precision=pipe.sprec)
+    gw.check()
+    sig = sig.cpu().numpy()
+    abs_err = float(np.abs(sig - so).max())
+    return {"abs_Ha": abs_err, "rel": abs_err / float(np.abs(so).max()),
+            "max_abs_sigma_Ha": float(np.abs(so).max()), "rel_fro_P": eP,
+            "q_index": iq, "oracle_s": round(t_oracle, 1),
+            "note": "one q (weight w_q) of the workload, all 16 states x 416 partner bands; oracle: "
+                    "all-FP64 chain on the same complex64 projections"}
 
 
 def run_case_herk(args):
@@ -737,7 +779,7 @@ def run_case_aux(args):
     # exchange over the 8 q
     ps, es = zip(*[wl.sigma_pairs(i) for i in range(wl.nq)])
     Ms = [gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[i], 0, len(ps[i]), wl.nb[i],
-                               dtype=torch.complex64) for i in range(wl.nq)]
+                               dtype=torch.complex64).mul_(wl.msig_scale) for i in range(wl.nq)]
     pst = [dev(p, torch.int32) for p in ps]
     eps = [dev(e) for e in es]
     vs = [dev(wl.v(i)) for i in range(wl.nq)]
@@ -769,6 +811,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
+    ap.add_argument("--sigma-precision", default="tf32x3", choices=["bf16x3", "tf32x3", "fp64"],
+                    help="precision of the Sigma pair coefficients (TF32x3 by default: its Sigma^c "
+                         "error at the workload's sizes is 1e-6 Ha against 2e-5 Ha for BF16x3)")
+    ap.add_argument("--no-sigma-check", action="store_true",
+                    help="skip the oracle comparison of one q's Sigma^c after the timed region")
     ap.add_argument("--real", action="store_true",
                     help="--case herk with real projections (inversion-symmetric systems)")
     ap.add_argument("--case", default=None,

@@ -32,7 +32,9 @@ def pair_coefficients(Msig, Wc):
     Msig = np.asarray(Msig, dtype=np.complex128)
     out = np.empty((Wc.shape[0], Msig.shape[0]))
     for j in range(Wc.shape[0]):
-        out[j] = np.einsum("pi,ij,pj->p", Msig.conj(), Wc[j], Msig).real
+        # the same double sum over (i, j) per pair; numpy picks the contraction order
+        # (a matrix product, then the row-wise dot)
+        out[j] = np.einsum("pi,ij,pj->p", Msig.conj(), Wc[j], Msig, optimize=True).real
     return out
 
 
@@ -102,14 +104,16 @@ def convolution_weights(omega, omega_out, eps, epsabs=1e-15, epsrel=1e-13):
     return T
 
 
-def sigma_c(omega, omega_out, wq, coeffs, pair_state, eps_np, nsig):
+def sigma_c(omega, omega_out, wq, coeffs, pair_state, eps_np, nsig, tables=None):
     """Sigma^c_s(i w_i) = -1/(2 pi) sum_q w_q sum_{p in s} sum_j T_ij(eps_p) c_{q,j,p}.
 
     coeffs[q]: [n_omega][n_pair_q]; pair_state[q], eps_np[q]: [n_pair_q].
+    tables: optional dict energy -> T from convolution_weights(omega, omega_out, energy)
+    (computed elsewhere, e.g. by worker processes); missing energies are computed here.
     Returns complex128 [nsig][n_out].
     """
     out = np.zeros((nsig, len(omega_out)), dtype=np.complex128)
-    cache = {}
+    cache = dict(tables) if tables else {}
     for iq in range(len(wq)):
         c = np.asarray(coeffs[iq])
         for p in range(c.shape[1]):

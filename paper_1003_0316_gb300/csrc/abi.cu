@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <map>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -51,6 +53,19 @@ int device_ctx(DeviceCtx* out) {
     g_ctx_ok[dev] = true;
   }
   *out = g_ctx[dev];
+  return GW_OK;
+}
+
+static std::mutex g_attr_mu;
+static std::map<std::pair<const void*, int>, size_t> g_attr_set;
+
+int set_max_dyn_smem(const void* kernel, size_t bytes, int device) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  auto key = std::make_pair(kernel, device);
+  auto it = g_attr_set.find(key);
+  if (it != g_attr_set.end() && it->second >= bytes) return GW_OK;
+  GW_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  g_attr_set[key] = bytes;
   return GW_OK;
 }
 

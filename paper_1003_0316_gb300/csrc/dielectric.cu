@@ -438,15 +438,11 @@ template <typename T>
 static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const DeviceCtx& ctx) {
   const size_t smem = 3 * DB * DLD * sizeof(T);
   const size_t smem_w = 2 * DB * DLD * sizeof(T);
-  static bool attr_set[64] = {};
-  if (!attr_set[ctx.device]) {
-    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(smem)));
-    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric_w<T>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_w)));
-    GW_CUDA_TRY(cudaFuncSetAttribute(k_dielectric_zcol<T>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_w)));
-    attr_set[ctx.device] = true;
+  {
+    int rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_dielectric<T>), smem, ctx.device);
+    if (!rc) rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_dielectric_w<T>), smem_w, ctx.device);
+    if (!rc) rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_dielectric_zcol<T>), smem_w, ctx.device);
+    if (rc) return rc;
   }
   const bool by_columns = !sys.empty() && sys[0].D != nullptr;
   for (size_t b0 = 0; b0 < sys.size(); b0 += DMAXSYS) {

@@ -440,23 +440,15 @@ int completeness_add(int nq, const ComplQ* qs, int dtype, double pref, int nw, c
     if (dtype == GW_C128) {
       k_completeness_fp64<<<unsigned(item), 256, 0, s>>>(L, pref, om, ctx.status);
     } else if (dtype == GW_C64) {
-      static bool attr64[64] = {};
-      if (!attr64[ctx.device]) {
-        GW_CUDA_TRY(cudaFuncSetAttribute(k_completeness_async<GW_C64>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(async_smem(GW_C64))));
-        attr64[ctx.device] = true;
-      }
+      int rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_completeness_async<GW_C64>),
+                                async_smem(GW_C64), ctx.device);
+      if (rc) return rc;
       k_completeness_async<GW_C64><<<unsigned(item), 256, async_smem(GW_C64), s>>>(L, pref, om,
                                                                                 ctx.status);
     } else {
-      static bool attr32[64] = {};
-      if (!attr32[ctx.device]) {
-        GW_CUDA_TRY(cudaFuncSetAttribute(k_completeness_async<GW_R32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(async_smem(GW_R32))));
-        attr32[ctx.device] = true;
-      }
+      int rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_completeness_async<GW_R32>),
+                                async_smem(GW_R32), ctx.device);
+      if (rc) return rc;
       k_completeness_async<GW_R32><<<unsigned(item), 256, async_smem(GW_R32), s>>>(L, pref, om,
                                                                                 ctx.status);
     }

@@ -41,6 +41,10 @@ struct DeviceCtx {
 };
 int device_ctx(DeviceCtx* out);
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device), thread safe
+// (a mutex guards the record of what was set; a larger size is set again).
+int set_max_dyn_smem(const void* kernel, size_t bytes, int device);
+
 __device__ __forceinline__ void raise_status(unsigned* status, unsigned bit) {
   atomicOr(status, bit);
 }

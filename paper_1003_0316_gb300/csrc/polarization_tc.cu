@@ -14,29 +14,34 @@
 // biases a long chain of additions toward zero (about 2e-8 of the running value per
 // MMA). A round is two 64-byte K chunks (2 x 16 TF32 or 2 x 32 BF16 transitions, 12 MMAs);
 // every drain period of PL rounds on one accumulator (PL = 1: one round) therefore starts a
-// fresh accumulator; the epilogue adds each period's result into FP32 running sums kept in
-// TMEM (round to nearest) and folds them into FP64 every 256 periods (FP64 reductions
-// performed at L2 into per-CTA sums), so no truncating chain is longer than 12 PL MMAs; the
-// round-to-nearest FP32 sums add only unbiased errors that average out over the folds.
+// fresh accumulator; the epilogue adds each period's result into FP32 running sums held in
+// its registers (round to nearest) and folds them into FP64 every 256 periods (FP64
+// reductions performed at L2 into per-CTA sums), so no truncating chain is longer than 12 PL
+// MMAs; the round-to-nearest FP32 sums add only unbiased errors that average out over the
+// folds.
 //
-// Layout and roles (480 threads, one persistent CTA per SM; 512 TMEM columns):
+// Layout and roles (512 threads in four warpgroups, one persistent CTA per SM; 512 TMEM
+// columns):
 //   TMEM  cols [0,256): two accumulators (round g uses g mod 2, PL rounds per drain);
-//         cols [256,384): FP32 running sums;
-//         cols [384,512): two A slots of one round each (per chunk 16 columns hi + 16 lo).
+//         cols [256,512): four A slots of one round each (per chunk 16 columns hi + 16 lo);
+//         round g uses slot g mod 4, so each A set owns two slots and can fill one while
+//         the MMAs still read the other.
 //   warps 0-7    A transform: scale x by s_tj, split, tcgen05.st into the A slot of their
-//                lane quadrant; set g mod 2 (warps 4 (g mod 2) .. + 3) takes round g and
-//                owns slot g mod 2 (AH = 2 would give each quadrant two warps per set, each
-//                with half of every chunk: measured slower at the lower register cap);
-//   warp 8       one thread issues the bulk copies of a round's pre-split B tiles and
-//                weights into a 4-stage shared-memory ring;
+//                lane quadrant; set g mod 2 (warps 4 (g mod 2) .. + 3) takes round g;
+//   warp 8       one thread issues the bulk copies of a round's pre-split B tiles into a
+//                4-stage shared-memory ring;
 //   warps 9-10   one thread each issues the MMAs (A from TMEM, B from shared memory) of the
 //                rounds of one accumulator, and tcgen05.commit;
-//   warps 11-14  epilogue, one per lane quadrant: tcgen05.ld of the finished accumulator
-//                and of the running sums, their sum back into TMEM, FP64 folding, the final
-//                complex combination and the Hermitian store.
+//   warp 11      one thread issues the bulk copies of the rounds' weights into an 8-slot ring
+//                of their own, so the A sets can run ahead of the B stages;
+//   warps 12-15  epilogue, one per lane quadrant: tcgen05.ld of the finished accumulator
+//                into FP32 running sums in registers (the warpgroup raises its register
+//                budget with setmaxnreg, the producer/MMA warpgroup lowers its own), FP64
+//                folding, the final complex combination and the Hermitian store.
 // Every barrier is waited on only by threads that see each of its phases in order (a
-// parity wait cannot tell phase p from phase p + 2): stage and slot counts are even, so the
-// A set and the MMA issuer of round g also handled rounds g - NSB and g - NSA.
+// parity wait cannot tell phase p from phase p + 2): the stage, slot and weight-slot counts
+// are even, so the A set and the MMA issuer of round g also handled rounds g - NSB, g - NSA
+// and g - NWS.
 // The same kernel forms the Sigma pair coefficients as a quadratic form (MODE 1: A = the pair
 // projections, B = the real form of W^c, c_p = row sums of (X R) o X) and the real polarization
 // of inversion-symmetric systems (MODE 2, real operand of width N_b).
@@ -60,26 +65,29 @@ constexpr int TN = 128;          // real Gram columns per tile (B operand, in sh
 constexpr int SWB = 64;          // bytes of K per B row per chunk (64-byte swizzle)
 constexpr int SUB = 2;           // 64-byte K chunks per barrier round
 constexpr int NSB = 4;           // B stages (rounds) in shared memory
-constexpr int NSA = 2;           // A slots (rounds) in TMEM: one per A set
+constexpr int NSA = 4;           // A slots (rounds) in TMEM: two per A set
+constexpr int NWS = 8;           // weight slots (rounds) in shared memory
 constexpr int B_TILE = TN * SWB;                 // 8 KB: one chunk's hi (or lo) tile
 constexpr int CHUNK_BYTES = 2 * B_TILE;          // hi + lo of one chunk (pre-split layout)
 constexpr int STAGE_BYTES = SUB * CHUNK_BYTES;   // one round
-constexpr int STAGE_STRIDE = STAGE_BYTES + 1024; // + the round's weights slice, 1024-aligned
+constexpr int WSLOT_BYTES = 256;                 // one round's weights (SUB x 32 floats at most)
 constexpr uint32_t ACC_COL = 0;                  // two accumulators: cols [0,128), [128,256)
-constexpr uint32_t SUM_COL = 2 * TN;             // FP32 running sums: cols [256,384)
-constexpr uint32_t A_COL = 3 * TN;               // A slots: [384,512), 64 columns each
-constexpr int AH = 1;            // A-transform warps per lane quadrant and set (2: chunk halves)
-constexpr int A_WARPS = 8 * AH;  // warps 0-15: A transform, two sets of AH warps per quadrant
-constexpr int PROD_WARP = A_WARPS;       // one thread: bulk copies of B tiles and weights
+constexpr uint32_t A_COL = 2 * TN;               // A slots: [256,512), 64 columns each
+constexpr int A_WARPS = 8;       // warps 0-7: A transform, two sets of one warp per quadrant
+constexpr int PROD_WARP = A_WARPS;       // one thread: bulk copies of B tiles
 constexpr int MMA_WARP = A_WARPS + 1;    // two warps issue the MMAs of even and odd rounds
-constexpr int EPI_WARP0 = A_WARPS + 3;   // four warps: epilogue, one per lane quadrant
+constexpr int WPROD_WARP = A_WARPS + 3;  // one thread: bulk copies of the weights
+constexpr int EPI_WARP0 = A_WARPS + 4;   // four warps: epilogue, one per lane quadrant
 constexpr int NEPI = 4;
 constexpr int NWARPS = EPI_WARP0 + NEPI;
 constexpr int NTHREADS = NWARPS * 32;
+constexpr int REG_LOW = 40;      // registers per thread of the producer/MMA warpgroup
+constexpr int REG_EPI = 216;     // ... of the epilogue warpgroup (128 + 128 - 40 at launch)
 constexpr int PL = 1;                            // own rounds per drain period and accumulator
 constexpr int FLUSH = 256;                       // periods per FP64 fold of the running sums
 constexpr int TQ = 64;
 constexpr uint64_t WAIT_LIMIT = 2000000000ull;   // ns: 2 s per bounded wait
+static_assert(NTHREADS == 512 && REG_EPI + REG_LOW == 2 * 128, "register split");
 
 struct TcLaunch {
   const float* xT[TQ];      // A side, chunk-major: float4 [row block][kpad / CH][CH / 4][128 rows]
@@ -181,8 +189,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   extern __shared__ __align__(1024) char dsmem[];
   char* ring = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t fullB[NSB], emptyB[NSB], fullA[NSA], emptyA[NSA], accf_bar[2],
-      acce_bar[2], done_bar[2];
+  char* wring = ring + NSB * STAGE_BYTES;     // weight slots
+  __shared__ __align__(8) uint64_t fullB[NSB], emptyB[NSB], fullA[NSA], emptyA[NSA], fullW[NWS],
+      emptyW[NWS], accf_bar[2], acce_bar[2], done_bar[2];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
 
@@ -193,8 +202,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mbar_init(&emptyB[i], 1);
     }
     for (int i = 0; i < NSA; ++i) {
-      tc::mbar_init(&fullA[i], 4 * AH);    // the set's warps (AH per lane quadrant)
+      tc::mbar_init(&fullA[i], 4);         // the set's four warps
       tc::mbar_init(&emptyA[i], 1);
+    }
+    for (int i = 0; i < NWS; ++i) {
+      tc::mbar_init(&fullW[i], 1);
+      tc::mbar_init(&emptyW[i], 4);        // the set's four warps have read the weights
     }
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&accf_bar[i], 1);
@@ -217,15 +230,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp < A_WARPS) {
     // ------------------------------------------------ A transform -> TMEM
-    // A set par (warps 4 AH par .. 4 AH par + 4 AH - 1: AH per lane quadrant, each taking
-    // 1/AH of every chunk's K values) takes the rounds g with g mod 2 == par (g counted over
-    // all items of this CTA) and owns A slot par. Each lane reads its column's values from the
-    // chunk-major copy (each float4 read of a warp is 512 contiguous bytes; a ring of register
-    // buffers keeps the reads of the next chunks in flight while the current one is split) and
-    // the round's weights from the stage.
-    constexpr int CHW = CH4 / AH;               // float4 per lane and chunk for this warp
+    // A set par (warps 4 par .. 4 par + 3, one per lane quadrant) takes the rounds g with
+    // g mod 2 == par (g counted over all items of this CTA); round g goes to A slot g mod 4.
+    // Each lane reads its column's values from the chunk-major copy (each float4 read of a
+    // warp is 512 contiguous bytes; a ring of register buffers keeps the reads of the next
+    // chunks in flight while the current one is split) and the round's weights from the
+    // weight ring.
     constexpr int RA = BF16 ? 2 : 4;            // chunks of column reads in flight
-    const int qd = warp & 3, hh = (warp >> 2) % AH, par = warp / (4 * AH);
+    const int qd = warp & 3, par = warp >> 2;
     const int m = qd * 32 + lane;
     uint64_t g0 = 0;                  // rounds of the previous items
     bool stop = false;
@@ -238,48 +250,48 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t r_first = int64_t((par + 2 - int(g0 & 1)) & 1);
       const int64_t nown = nr > r_first ? (nr - r_first + 1) / 2 : 0;
       // own chunk k (k = 0 .. SUB nown - 1) is chunk SUB (r_first + 2 (k / SUB)) + k % SUB
-      auto load = [&](int64_t k, float4 (&rg)[CHW]) {
+      auto load = [&](int64_t k, float4 (&rg)[CH4]) {
         const int64_t c = SUB * (r_first + 2 * (k / SUB)) + k % SUB;
 #pragma unroll
-        for (int e = 0; e < CHW; ++e) rg[e] = __ldg(xc + size_t(c * CH4 + hh * CHW + e) * TM);
+        for (int e = 0; e < CH4; ++e) rg[e] = __ldg(xc + size_t(c * CH4 + e) * TM);
       };
-      // chunk k of the own rounds: the first one of a round waits for the stage and the slot,
-      // the last one signals the slot full
-      auto process = [&](int64_t k, const float4 (&xr)[CHW]) -> bool {
+      // chunk k of the own rounds: the first one of a round waits for the round's weights;
+      // the chunk is scaled and split before the wait for the A slot, so that work overlaps
+      // the MMAs still reading the slot; the last chunk releases the weights and signals the
+      // slot full
+      auto process = [&](int64_t k, const float4 (&xr)[CH4]) -> bool {
         const int u = int(k % SUB);
         const uint64_t gg = g0 + uint64_t(r_first + 2 * (k / SUB));
-        const int slot = int(gg % NSA), st = int(gg % NSB);
-        // the weights arrive with the round's B stage; the chunk is scaled and split before the
-        // wait for the A slot, so that work overlaps the MMAs still reading the slot
-        if (u == 0 && !warp_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, status))
+        const int slot = int(gg % NSA), ws = int(gg % NWS);
+        if (!QF && u == 0 && !warp_wait(&fullW[ws], uint32_t(gg / NWS) & 1, &s_abort, status))
           return false;
-        const float4* sw =
-            reinterpret_cast<const float4*>(ring + st * STAGE_STRIDE + STAGE_BYTES) + u * CH4;
-        constexpr int NH = 2 / AH;                  // chunk halves of this warp
-        uint32_t hw[NH][8], lw[NH][8];
+        const float4* sw = reinterpret_cast<const float4*>(wring + ws * WSLOT_BYTES) + u * CH4;
+        uint32_t hw[2][8], lw[2][8];
 #pragma unroll
-        for (int hl = 0; hl < NH; ++hl) {           // halves of the chunk: 8 TMEM words each
-          const int h = hh * NH + hl;
+        for (int h = 0; h < 2; ++h) {               // halves of the chunk: 8 TMEM words each
           float y[CH / 2];
 #pragma unroll
           for (int e = 0; e < CH4 / 2; ++e) {
-            const float4 xv = xr[hl * (CH4 / 2) + e];
+            const float4 xv = xr[h * (CH4 / 2) + e];
             const float4 wv = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : sw[h * (CH4 / 2) + e];
             y[4 * e + 0] = wv.x * xv.x;
             y[4 * e + 1] = wv.y * xv.y;
             y[4 * e + 2] = wv.z * xv.z;
             y[4 * e + 3] = wv.w * xv.w;
           }
-          split_words<BF16>(y, hw[hl], lw[hl], 8);
+          split_words<BF16>(y, hw[h], lw[h], 8);
+        }
+        if (!QF && u == SUB - 1) {                  // this warp is done with the weights
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&emptyW[ws]);
         }
         if (u == 0 && !warp_wait(&emptyA[slot], (uint32_t(gg / NSA) & 1) ^ 1, &s_abort, status))
           return false;
         const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * (SUB * 32) + u * 32;
 #pragma unroll
-        for (int hl = 0; hl < NH; ++hl) {
-          const int h = hh * NH + hl;
-          tc::tmem_st8(base + h * 8, hw[hl]);
-          tc::tmem_st8(base + 16 + h * 8, lw[hl]);
+        for (int h = 0; h < 2; ++h) {
+          tc::tmem_st8(base + h * 8, hw[h]);
+          tc::tmem_st8(base + 16 + h * 8, lw[h]);
         }
         if (u == SUB - 1) {
           tc::tmem_wait_st();
@@ -291,7 +303,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       };
       const int64_t nk = SUB * nown;
       // ring of RA register buffers: the reads of the next RA - 1 own chunks are in flight
-      float4 X[RA][CHW];
+      float4 X[RA][CH4];
 #pragma unroll
       for (int v = 0; v < RA - 1; ++v)
         if (v < nk) load(v, X[v]);
@@ -309,123 +321,164 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       g0 += uint64_t(nr);
     }
-  } else if (warp == PROD_WARP) {
-    // ------------------------------------------------ B tiles and weights: bulk copies
-    // One round per stage: the SUB consecutive pre-split chunk tiles (contiguous) and the
-    // round's SUB CH weights.
-    if (lane == 0) {
-      uint64_t g = 0;
-      bool ok = true;
-      for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-        int q, j, bi, bj;
-        decode_item<QF>(L, item, q, j, bi, bj);
-        const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
-        const char* src =
-            L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * size_t(nr * SUB) * CHUNK_BYTES;
-        const float* ws = QF ? nullptr : L.s[q] + size_t(j) * L.kpad[q];
-        for (int64_t r = 0; r < nr; ++r, ++g) {
-          const int st = int(g % NSB);
-          if (!tc::mbar_wait(&emptyB[st], (uint32_t(g / NSB) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
-            ok = false;
-            break;
+  } else if (warp < EPI_WARP0) {
+    tc::setmaxnreg_dec<REG_LOW>();
+    if (warp == PROD_WARP) {
+      // ---------------------------------------------- B tiles: bulk copies
+      // One round per stage: the SUB consecutive pre-split chunk tiles (contiguous).
+      if (lane == 0) {
+        uint64_t g = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+          int q, j, bi, bj;
+          decode_item<QF>(L, item, q, j, bi, bj);
+          const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+          const char* src =
+              L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * size_t(nr * SUB) * CHUNK_BYTES;
+          for (int64_t r = 0; r < nr; ++r, ++g) {
+            const int st = int(g % NSB);
+            if (!tc::mbar_wait(&emptyB[st], (uint32_t(g / NSB) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
+              ok = false;
+              break;
+            }
+            char* dst = ring + st * STAGE_BYTES;
+            tc::mbar_arrive_expect_tx(&fullB[st], STAGE_BYTES);
+            tc::bulk_g2s(dst, src + size_t(r) * STAGE_BYTES, STAGE_BYTES, &fullB[st]);
           }
-          char* dst = ring + st * STAGE_STRIDE;
-          tc::mbar_arrive_expect_tx(&fullB[st], STAGE_BYTES + (QF ? 0 : SUB * CH * 4));
-          tc::bulk_g2s(dst, src + size_t(r) * STAGE_BYTES, STAGE_BYTES, &fullB[st]);
-          if (!QF) tc::bulk_g2s(dst + STAGE_BYTES, ws + r * SUB * CH, SUB * CH * 4, &fullB[st]);
+        }
+        if (!ok && !s_abort) {
+          s_abort = 1;
+          raise_status(status, ST_ETIMEOUT);
         }
       }
-      if (!ok && !s_abort) {
-        s_abort = 1;
-        raise_status(status, ST_ETIMEOUT);
-      }
-    }
-    __syncwarp();
-  } else if (warp == MMA_WARP || warp == MMA_WARP + 1) {
-    // ------------------------------------------------ MMA issue (two threads, alternate rounds)
-    // Round g goes to accumulator g mod 2 and is issued by MMA warp g mod 2 (g counted over
-    // all items), so the barrier waits of one issuing thread overlap the tensor-core work of
-    // the other. Each round is one drain period: SUB chunks x 2 K steps x 3 MMAs into a fresh
-    // accumulator.
-    const uint32_t mpar = uint32_t(warp - MMA_WARP);
-    if (lane == 0) {
-      uint64_t g = 0;
-      uint32_t kb = 0;              // periods issued on this warp's accumulator
-      const uint64_t desc0 = tc::smem_desc(tc::smem_u32(ring), 512, 4);
-      const uint32_t d = tmem + ACC_COL + mpar * TN;
-      bool ok = true;
-      for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-        int q, j, bi, bj;
-        decode_item<QF>(L, item, q, j, bi, bj);
-        const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
-        const int64_t first = int64_t((mpar + 2 - uint32_t(g & 1)) & 1);
-        const int64_t nown = nr > first ? (nr - first + 1) / 2 : 0;   // own rounds of the item
-        for (int64_t i = 0; i < nown; ++i) {
-          const int64_t r = first + 2 * i;
-          // a drain period is PL own rounds (fewer at the end of the item)
-          const bool pstart = i % PL == 0, pend = i % PL == PL - 1 || i == nown - 1;
-          const uint64_t gg = g + uint64_t(r);
-          const int st = int(gg % NSB), slot = int(gg % NSA);
-          if (!tc::mbar_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, WAIT_LIMIT) ||
-              !tc::mbar_wait(&fullA[slot], uint32_t(gg / NSA) & 1, &s_abort, WAIT_LIMIT) ||
-              (pstart && !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT))) {
-            ok = false;
-            break;
+      __syncwarp();
+    } else if (warp == WPROD_WARP) {
+      // ---------------------------------------------- weights: bulk copies
+      // One round per weight slot: the round's SUB CH weights (SUB CH 4 bytes, 16-byte
+      // aligned). The quadratic form has no weights.
+      if (!QF && lane == 0) {
+        uint64_t g = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+          int q, j, bi, bj;
+          decode_item<QF>(L, item, q, j, bi, bj);
+          const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+          const float* wsrc = L.s[q] + size_t(j) * L.kpad[q];
+          for (int64_t r = 0; r < nr; ++r, ++g) {
+            const int ws = int(g % NWS);
+            if (!tc::mbar_wait(&emptyW[ws], (uint32_t(g / NWS) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
+              ok = false;
+              break;
+            }
+            tc::mbar_arrive_expect_tx(&fullW[ws], SUB * CH * 4);
+            tc::bulk_g2s(wring + ws * WSLOT_BYTES, wsrc + r * SUB * CH, SUB * CH * 4, &fullW[ws]);
           }
-          tc::tc_fence_after();
-          const uint32_t a0 = tmem + A_COL + slot * (SUB * 32);
-          // descriptor address field is (addr >> 4): advancing the address adds to the low bits
-          const uint64_t dst = desc0 + uint64_t((st * STAGE_STRIDE) >> 4);
+        }
+        if (!ok && !s_abort) {
+          s_abort = 1;
+          raise_status(status, ST_ETIMEOUT);
+        }
+      }
+      __syncwarp();
+    } else {
+      // ---------------------------------------------- MMA issue (two threads, alternate rounds)
+      // Round g goes to accumulator g mod 2 and is issued by MMA warp g mod 2 (g counted over
+      // all items), so the barrier waits of one issuing thread overlap the tensor-core work of
+      // the other. Each round is one drain period: SUB chunks x 2 K steps x 3 MMAs into a
+      // fresh accumulator.
+      const uint32_t mpar = uint32_t(warp - MMA_WARP);
+      if (lane == 0) {
+        uint64_t g = 0;
+        uint32_t kb = 0;              // periods issued on this warp's accumulator
+        const uint64_t desc0 = tc::smem_desc(tc::smem_u32(ring), 512, 4);
+        const uint32_t d = tmem + ACC_COL + mpar * TN;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+          int q, j, bi, bj;
+          decode_item<QF>(L, item, q, j, bi, bj);
+          const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+          const int64_t first = int64_t((mpar + 2 - uint32_t(g & 1)) & 1);
+          const int64_t nown = nr > first ? (nr - first + 1) / 2 : 0;   // own rounds of the item
+          for (int64_t i = 0; i < nown; ++i) {
+            const int64_t r = first + 2 * i;
+            // a drain period is PL own rounds (fewer at the end of the item)
+            const bool pstart = i % PL == 0, pend = i % PL == PL - 1 || i == nown - 1;
+            const uint64_t gg = g + uint64_t(r);
+            const int st = int(gg % NSB), slot = int(gg % NSA);
+            if (!tc::mbar_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, WAIT_LIMIT) ||
+                !tc::mbar_wait(&fullA[slot], uint32_t(gg / NSA) & 1, &s_abort, WAIT_LIMIT) ||
+                (pstart && !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT))) {
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+            const uint32_t a0 = tmem + A_COL + slot * (SUB * 32);
+            // descriptor address field is (addr >> 4): advancing the address adds to the low bits
+            const uint64_t dst = desc0 + uint64_t((st * STAGE_BYTES) >> 4);
 #pragma unroll
-          for (int u = 0; u < SUB; ++u) {
+            for (int u = 0; u < SUB; ++u) {
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              const uint64_t dBh = dst + uint64_t((u * CHUNK_BYTES + ks * 32) >> 4);
-              const uint64_t dBl = dst + uint64_t((u * CHUNK_BYTES + B_TILE + ks * 32) >> 4);
-              const uint32_t ah = a0 + u * 32 + ks * 8, al = a0 + u * 32 + 16 + ks * 8;
-              const uint32_t acc0 = (pstart && u == 0 && ks == 0) ? 0u : 1u;
-              if (BF16) {
-                tc::mma_f16_ta(d, al, dBh, IDESC, acc0);
-                tc::mma_f16_ta(d, ah, dBl, IDESC, 1u);
-                tc::mma_f16_ta(d, ah, dBh, IDESC, 1u);
-              } else {
-                tc::mma_tf32_ta(d, al, dBh, IDESC, acc0);
-                tc::mma_tf32_ta(d, ah, dBl, IDESC, 1u);
-                tc::mma_tf32_ta(d, ah, dBh, IDESC, 1u);
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t dBh = dst + uint64_t((u * CHUNK_BYTES + ks * 32) >> 4);
+                const uint64_t dBl = dst + uint64_t((u * CHUNK_BYTES + B_TILE + ks * 32) >> 4);
+                const uint32_t ah = a0 + u * 32 + ks * 8, al = a0 + u * 32 + 16 + ks * 8;
+                const uint32_t acc0 = (pstart && u == 0 && ks == 0) ? 0u : 1u;
+                if (BF16) {
+                  tc::mma_f16_ta(d, al, dBh, IDESC, acc0);
+                  tc::mma_f16_ta(d, ah, dBl, IDESC, 1u);
+                  tc::mma_f16_ta(d, ah, dBh, IDESC, 1u);
+                } else {
+                  tc::mma_tf32_ta(d, al, dBh, IDESC, acc0);
+                  tc::mma_tf32_ta(d, ah, dBl, IDESC, 1u);
+                  tc::mma_tf32_ta(d, ah, dBh, IDESC, 1u);
+                }
               }
             }
+            tc::mma_commit(&emptyB[st]);
+            tc::mma_commit(&emptyA[slot]);
+            if (pend) {
+              tc::mma_commit(&accf_bar[mpar]);
+              ++kb;
+            }
           }
-          tc::mma_commit(&emptyB[st]);
-          tc::mma_commit(&emptyA[slot]);
-          if (pend) {
-            tc::mma_commit(&accf_bar[mpar]);
-            ++kb;
-          }
+          g += uint64_t(nr);
         }
-        g += uint64_t(nr);
+        if (!ok && !s_abort) {
+          s_abort = 1;
+          raise_status(status, ST_ETIMEOUT);
+        }
+        tc::mma_commit(&done_bar[mpar]);
+        int never = 0;
+        tc::mbar_wait(&done_bar[mpar], 0, reinterpret_cast<volatile int*>(&never), WAIT_LIMIT);
       }
-      if (!ok && !s_abort) {
-        s_abort = 1;
-        raise_status(status, ST_ETIMEOUT);
-      }
-      tc::mma_commit(&done_bar[mpar]);
-      int never = 0;
-      tc::mbar_wait(&done_bar[mpar], 0, reinterpret_cast<volatile int*>(&never), WAIT_LIMIT);
+      __syncwarp();
     }
-    __syncwarp();
-  } else if (warp >= EPI_WARP0) {
+  } else {
+    tc::setmaxnreg_inc<REG_EPI>();
     // ------------------------------------------------ drain / epilogue
-    // Each round's accumulator is added into FP32 running sums kept in TMEM (round to
-    // nearest); every FLUSH rounds (staggered over the warps) the sums are folded into FP64
-    // with L2 reductions.
+    // Each period's accumulator is added into FP32 running sums in registers (round to
+    // nearest): one read of the accumulator per period, no TMEM write. Every FLUSH periods
+    // (staggered over the warps) the sums are folded into FP64 with L2 reductions.
     const int qd = warp & 3;
     const int r = qd * 32 + lane;               // tile row
     const uint32_t lane_base = tmem + (uint32_t(qd * 32) << 16);
     double* acc = acc64 + size_t(blockIdx.x) * TN * TM + r;   // [col][row]
-    uint32_t kb[2] = {0, 0};        // periods drained per accumulator
+    uint32_t kb0 = 0, kb1 = 0;      // periods drained per accumulator
     uint32_t gp = 0;                // periods drained in total (flush schedule)
     uint64_t g0 = 0;                // rounds of the previous items
     bool stop = false;
+    float rs[TN];
+    // the conversions go through volatile asm so that they stay next to their reductions
+    // (converted all at once, 128 doubles would not fit beside the running sums)
+    auto fold = [&]() {
+#pragma unroll
+      for (int i = 0; i < TN; ++i) {
+        double d;
+        asm volatile("cvt.f64.f32 %0, %1;" : "=d"(d) : "f"(rs[i]));
+        atomicAdd(acc + size_t(i) * TM, d);
+        rs[i] = 0.0f;
+      }
+    };
     for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       int q, j, bi, bj;
       decode_item<QF>(L, item, q, j, bi, bj);
@@ -433,6 +486,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int nb = L.nb[q];
 #pragma unroll 8
       for (int i = 0; i < TN; ++i) acc[size_t(i) * TM] = 0.0;
+#pragma unroll
+      for (int i = 0; i < TN; ++i) rs[i] = 0.0f;
       bool sum_empty = true;
       // drain periods in completion order: the accumulators alternate, starting with the one
       // of the item's first round (its own-round count, and so its period count, is the larger)
@@ -440,51 +495,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t np0 = ((nr + 1) / 2 + PL - 1) / PL, np1 = (nr / 2 + PL - 1) / PL;
       for (int64_t k = 0; k < np0 + np1; ++k, ++gp) {
         const int buf = (k & 1) ? buf0 ^ 1 : buf0;
-        if (!warp_wait(&accf_bar[buf], kb[buf] & 1, &s_abort, status)) {
+        const uint32_t kbb = buf ? kb1 : kb0;
+        if (!warp_wait(&accf_bar[buf], kbb & 1, &s_abort, status)) {
           stop = true;
           break;
         }
-        ++kb[buf];
+        if (buf) ++kb1; else ++kb0;
         tc::tc_fence_after();
-#pragma unroll 1
-        for (int cb = 0; cb < TN / 32; ++cb) {
-          uint32_t va[32], vs[32];
-          tc::tmem_ld32_nowait(lane_base + ACC_COL + buf * TN + cb * 32, va);
-          if (!sum_empty) tc::tmem_ld32_nowait(lane_base + SUM_COL + cb * 32, vs);
-          tc::tmem_wait_ld();
-          float v[32];
+        const uint32_t src = lane_base + ACC_COL + buf * TN;
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            v[i] = sum_empty ? __uint_as_float(va[i]) : __uint_as_float(va[i]) + __uint_as_float(vs[i]);
-          tc::tmem_st32(lane_base + SUM_COL + cb * 32, v);
+        for (int hb = 0; hb < TN / 64; ++hb) {      // two loads in flight, then the sums
+          uint32_t va[32], vb[32];
+          tc::tmem_ld32_nowait(src + hb * 64, va);
+          tc::tmem_ld32_nowait(src + hb * 64 + 32, vb);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            rs[hb * 64 + i] += __uint_as_float(va[i]);
+            rs[hb * 64 + 32 + i] += __uint_as_float(vb[i]);
+          }
         }
-        tc::tmem_wait_st();
         sum_empty = false;
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
         if (int((gp + qd * (FLUSH / 4)) % FLUSH) == FLUSH - 1) {
-#pragma unroll 1
-          for (int cb = 0; cb < TN / 32; ++cb) {
-            float sv[32];
-            tc::tmem_ld32(lane_base + SUM_COL + cb * 32, sv);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) atomicAdd(acc + size_t(cb * 32 + i) * TM, double(sv[i]));
-          }
+          fold();
           sum_empty = true;
         }
       }
       if (stop) break;
       g0 += uint64_t(nr);
-      if (!sum_empty) {
-#pragma unroll 1
-        for (int cb = 0; cb < TN / 32; ++cb) {
-          float sv[32];
-          tc::tmem_ld32(lane_base + SUM_COL + cb * 32, sv);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) atomicAdd(acc + size_t(cb * 32 + i) * TM, double(sv[i]));
-        }
-      }
+      if (!sum_empty) fold();
       __threadfence();
       if (QF) {
         // c_p += sum_c X[p][c] Y[p][c] over this tile's columns (X = the A rows themselves)
@@ -782,12 +824,7 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
 
 template <bool BF16, int MODE>
 static int prepare_kernel(const DeviceCtx& ctx, size_t smem) {
-  static bool done[64] = {};
-  if (done[ctx.device]) return GW_OK;
-  GW_CUDA_TRY(cudaFuncSetAttribute(k_herk_tc<BF16, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(smem)));
-  done[ctx.device] = true;
-  return GW_OK;
+  return set_max_dyn_smem(reinterpret_cast<const void*>(k_herk_tc<BF16, MODE>), smem, ctx.device);
 }
 
 template <int MODE>
@@ -819,7 +856,7 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
   }
   std::vector<int> start;
   tc_groups(nq, Ks.data(), nbs.data(), nw, ctx.sm_count, start);
-  const size_t smem = NSB * STAGE_STRIDE + 1024;
+  const size_t smem = NSB * STAGE_BYTES + NWS * WSLOT_BYTES + 1024;
   for (size_t g = 0; g + 1 < start.size(); ++g) {
     const int q0 = start[g], n = start[g + 1] - start[g];
     cur.used = group_base;               // the previous group's launch is ordered before this one
@@ -947,7 +984,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
       k_prep_quad<false, false><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
     GW_LAUNCH_CHECK("k_prep_quad");
   }
-  const size_t smem = NSB * STAGE_STRIDE + 1024;
+  const size_t smem = NSB * STAGE_BYTES + NWS * WSLOT_BYTES + 1024;
   for (int q0 = 0; q0 < nq; q0 += TQ) {
     int n = std::min(TQ, nq - q0);
     TcLaunch L{};

@@ -580,12 +580,9 @@ int convolve_acc(int nq, const double* wq, const int64_t* npair, int nw, const O
     GW_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * 2 * size_t(nsig) * nw_out, s));
   const size_t smem = conv_smem(nw);
   {
-    static bool attr[64] = {};
-    if (!attr[ctx.device]) {
-      GW_CUDA_TRY(cudaFuncSetAttribute(k_conv_slot, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(conv_smem(GW_MAX_NW))));
-      attr[ctx.device] = true;
-    }
+    int rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_conv_slot), conv_smem(GW_MAX_NW),
+                              ctx.device);
+    if (rc) return rc;
   }
   WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
   for (int q0 = 0; q0 < nq; q0 += SMAXQ) {

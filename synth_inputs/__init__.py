@@ -8,7 +8,9 @@ generator and stands in for them:
 * occupied energies U[-0.5, 0] Ha and unoccupied energies U[0.05, 2] Ha, drawn per
   mesh point and band (energies measured from the Fermi level, Sec. II);
 * projections M_{t,I} = (N(0,1) + i N(0,1)) / (1 + I/16), I = 0 .. N_b-1 (Eq. proj_MB
-  shape: decaying weight for higher Coulomb eigenfunctions);
+  shape: decaying weight for higher Coulomb eigenfunctions); the self-energy projections
+  follow the same law times a workload factor (2^-5 for the mesh workloads, so that
+  |Sigma^c| is of physical size);
 * Coulomb eigenvalues v_I = 4 pi / (0.1 + I^(2/3)) (Eq. dielec_MB input);
 * imaginary-frequency mesh omega_j = tan(theta_j), theta_j the Gauss-Legendre nodes on
   [0, arctan 50] (dense near 0, Sec. III.C);
@@ -88,6 +90,7 @@ class Workload:
     nw: int
     states: tuple = None   # band indices at k0 = Gamma that get Sigma (None: all)
     nw_out: int = None     # output mesh size of Sigma (None: nw)
+    msig_scale: float = 1.0  # extra factor of the Sigma projections (a power of two)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -215,10 +218,32 @@ class Workload:
         cols = np.arange(nb, dtype=np.uint64) if cols is None else np.asarray(cols, dtype=np.uint64)
         idx = rows[:, None] * np.uint64(nb) + cols[None, :]
         z = complex_normals(self.seed, TID_MSIG, idx, self.qs[iq])
-        return z / (1.0 + cols.astype(np.float64)[None, :] / 16.0)
+        return z * (self.msig_scale / (1.0 + cols.astype(np.float64)[None, :] / 16.0))
 
     def state_energies(self):
         return self.eps_bands(0)[self.sigma_states()]
+
+
+def _m_block(args):
+    wl, iq, r0, r1, dtype = args
+    return wl.m_rows(iq, rows=np.arange(r0, r1, dtype=np.uint64)).astype(dtype)
+
+
+def m_rows_parallel(wl, iq, pool, dtype=np.complex128, block=16384):
+    """All projections M_{t,I} of q index iq (the draws of Workload.m_rows), row blocks drawn
+    by the worker processes of `pool` (a multiprocessing pool made with the "spawn" start
+    method, so that it is safe next to a CUDA context). Returns [K][N_b] in `dtype`."""
+    K = wl.K(iq)
+    jobs = [(wl, iq, r0, min(K, r0 + block), dtype) for r0 in range(0, K, block)]
+    parts = pool.map(_m_block, jobs)
+    return np.concatenate(parts) if parts else np.zeros((0, wl.nb[iq]), dtype=dtype)
+
+
+# Sigma projections of the mesh workloads carry a factor 2^-5, so that the correlation
+# self-energy of the synthetic states is of the size of a physical one (max |Sigma^c| about
+# 11 Ha on the 4x4x4-mesh workload instead of about 10^4 Ha); a power of two changes no
+# relative rounding anywhere on the path.
+MSIG_SCALE_PHYSICAL = 2.0 ** -5
 
 
 def _mesh_index(mesh, a, b, c):
@@ -246,7 +271,7 @@ def medium_mixed():
     qs = tuple(_mesh_index(mesh, a, b, c) for a in (0, 1) for b in (0, 1) for c in (0, 1))
     wl = Workload(name="nk64_8q_nb600_nocc16_nunocc400_nw16", seed=SEED_BASE + 1,
                   mesh=mesh, qs=qs, wq=tuple([8.0 / 64.0] * 8), nb=tuple([600] * 8),
-                  nocc=16, nunocc=tuple([400] * 8), nw=16)
+                  nocc=16, nunocc=tuple([400] * 8), nw=16, msig_scale=MSIG_SCALE_PHYSICAL)
     wl.states = _top_states(wl, 8, 8)
     return wl
 
@@ -266,7 +291,7 @@ def medium_mixed_sharded(world):
     qs = tuple(base.qs) + tuple(rest[:nq - 8])
     wl = Workload(name=f"nk64_{nq}q_nb600_nocc16_nunocc400_nw16", seed=base.seed, mesh=mesh,
                   qs=qs, wq=tuple([1.0 / nq] * nq), nb=tuple([600] * nq), nocc=16,
-                  nunocc=tuple([400] * nq), nw=16)
+                  nunocc=tuple([400] * nq), nw=16, msig_scale=MSIG_SCALE_PHYSICAL)
     wl.states = base.states
     return wl
 
@@ -275,7 +300,7 @@ def supercell():
     """Single q = Gamma, N_k = 8, N_MPB = 4096, 256 occ / 3000 unocc, 20 frequencies."""
     wl = Workload(name="nk8_1q_nb4096_nocc256_nunocc3000_nw20", seed=SEED_BASE + 2,
                   mesh=(2, 2, 2), qs=(0,), wq=(1.0,), nb=(4096,), nocc=256,
-                  nunocc=(3000,), nw=20)
+                  nunocc=(3000,), nw=20, msig_scale=MSIG_SCALE_PHYSICAL)
     wl.states = _top_states(wl, 8, 8)
     return wl
 
@@ -291,7 +316,7 @@ def batched_uneven():
     nu = tuple(int(200 + np.floor(x * 601)) for x in u[nq:])
     wl = Workload(name="nk64_64q_nbU300-1500_nocc32_nunoccU200-800_nw16", seed=seed,
                   mesh=mesh, qs=tuple(range(nq)), wq=tuple([1.0 / nq] * nq), nb=nb,
-                  nocc=32, nunocc=nu, nw=16)
+                  nocc=32, nunocc=nu, nw=16, msig_scale=MSIG_SCALE_PHYSICAL)
     wl.states = _top_states(wl, 8, 8)
     return wl
 

@@ -201,6 +201,9 @@ def test_convolution_shared_energies(gw, nw, nwo):
 
 
 def test_fit_recovers_poles(gw):
+    """Exact two-pole curves: the GPU fit and the oracle's run of the same algorithm on the
+    same data agree per curve, and both recover the poles and residues (1e-8). The oracle
+    recovers every one of these 64 curves (checked here too), so no curve is exempt."""
     om = S.omega_mesh(24)
     rng = np.random.default_rng(3)
     n = 64
@@ -209,17 +212,20 @@ def test_fit_recovers_poles(gw):
     y = np.stack([OC.model(a[i], wp[i], 1j * om) for i in range(n)])
     params, cost, iters, status = gw.continue_fit(T(y), om, npole=2)
     params = params.cpu().numpy()
-    ok = 0
+    status = status.cpu().numpy()
     for i in range(n):
-        th = params[i].reshape(-1)
-        a2, w2 = OC.unpack(th)
+        a2, w2 = OC.unpack(params[i].reshape(-1))
         o = np.argsort(w2.real)
         th_o, C_o, it_o, st_o = OC.plain_fit(om, y[i], 2, +1)
-        if np.allclose(w2[o], wp[i], rtol=1e-8, atol=1e-9) and np.allclose(a2[o], a[i], rtol=1e-8, atol=1e-9):
-            ok += 1
-        # same algorithm, same data: the costs agree with the oracle's run
-        assert float(cost[i]) <= max(10 * C_o, 1e-24)
-    assert ok >= int(0.9 * n)
+        a_o, w_o = OC.unpack(th_o)
+        oo = np.argsort(w_o.real)
+        # the oracle recovers the exact parameters ...
+        assert np.allclose(w_o[oo], wp[i], rtol=1e-8, atol=1e-9), i
+        assert np.allclose(a_o[oo], a[i], rtol=1e-8, atol=1e-9), i
+        # ... and so does the GPU, agreeing with the oracle's result
+        assert np.allclose(w2[o], w_o[oo], rtol=1e-8, atol=1e-10), i
+        assert np.allclose(a2[o], a_o[oo], rtol=1e-8, atol=1e-10), i
+        assert status[i] == 0 and st_o == 0, (i, status[i], st_o)
 
 
 def test_end_to_end_small_fp64(gw):
@@ -270,3 +276,58 @@ def test_screened_w_real_rejects_non_positive_definite(gw):
     with pytest.raises(gw.GWError) as e:
         gw.check()
     assert e.value.code == gw.GW_ENOTHPD
+
+
+def test_screened_w_uneven_batch_against_oracle(gw):
+    """One call over q points of unequal N_b (odd, not multiples of the 32-row blocks): the
+    per-system offsets, the grid over (system, block column) and the early exits of the
+    smaller systems, each system against the oracle."""
+    nbs = [150, 33, 97]
+    wls = [S.tiny(nb=nb, nocc=3, nunocc=24, mesh=(2, 2, 1), nw=3, seed=200 + nb) for nb in nbs]
+    om = wls[0].omega()
+    Ps = [OP.polarization(w.m_full(0), w.delta(0), om, w.prefactor) for w in wls]
+    vs = [w.v(0) for w in wls]
+    W = gw.screened_w([T(p) for p in Ps], [T(v) for v in vs])
+    gw.check()
+    for Pq, v, Wg in zip(Ps, vs, W):
+        ref = OS.screened_wc_all(Pq, v)
+        Wg = Wg.cpu().numpy()
+        assert rel_fro(Wg, ref) <= 1e-12
+        assert max_rel(Wg, ref) <= 1e-12
+
+
+@pytest.mark.slow
+def test_screened_w_bench_size_against_oracle(gw):
+    """N_b = 600 (the mesh workload's basis) at two frequencies, stagewise against the oracle."""
+    wl = S.tiny(nb=600, nocc=4, nunocc=40, mesh=(2, 2, 2), nw=2, seed=600)
+    om = wl.omega()
+    Po = OP.polarization(wl.m_full(0), wl.delta(0), om, wl.prefactor)
+    v = wl.v(0)
+    Wg = gw.screened_w([T(Po)], [T(v)])[0]
+    gw.check()
+    Wg = Wg.cpu().numpy()
+    ref = OS.screened_wc_all(Po, v)
+    assert rel_fro(Wg, ref) <= 1e-12
+    assert max_rel(Wg, ref) <= 1e-12
+
+
+@pytest.mark.slow
+def test_polarization_fp64_full_size_sampled(gw):
+    """The FP64 path at the mesh workload's size (one q: K = 409,600, N_b = 600; projections
+    generated on the device, split-K over whole waves of CTAs) at 2 frequencies: the full cross
+    block of 24 sampled basis indices against the oracle, which draws those columns itself."""
+    wl = S.medium_mixed()
+    iq = 1
+    K, nb = wl.K(iq), wl.nb[iq]
+    om = wl.omega()[[0, 9]]
+    M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[iq], 0, K, nb, dtype=torch.complex128)
+    d = wl.delta(iq)
+    P = gw.polarization([M], [T(d)], om, wl.prefactor, "fp64")[0]
+    gw.check()
+    del M
+    rng = np.random.default_rng(24)
+    cols = np.sort(rng.choice(nb, size=24, replace=False))
+    got = P[:, cols][:, :, cols].cpu().numpy()
+    ref = OP.polarization(wl.m_rows(iq, cols=cols), d, om, wl.prefactor)
+    assert rel_fro(got, ref) <= 1e-12
+    assert max_rel(got, ref) <= 1e-12

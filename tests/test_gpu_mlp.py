@@ -90,10 +90,32 @@ def test_adam_step_against_oracle(gw):
         p = OM.adam_step(p, gr, st, lr, t)
     got = w.cpu().numpy().astype(np.float64)
     ref = OM.pack(p)
-    # a step moves each weight by at most ~lr; components whose gradient is near zero
-    # relative to eps may differ in step size, never by more than 2 lr
-    assert np.abs(got - ref).max() <= 2.0 * lr
-    assert np.median(np.abs(got - ref)) <= 1e-3 * lr
+    w0n = OM.pack(OM.unpack(w0.cpu().numpy().astype(np.float64)))
+    # Each Adam step moves a weight by about lr g / (|g| + eps) (bias-corrected). The update
+    # vector as a whole agrees with the oracle's to 1e-3 (relative Frobenius: a sign-flipped
+    # or rescaled step gives 1 or more), and so does every weight whose gradient is well
+    # above its FP32 error (|g| >= 0.1 of the RMS gradient at both steps: 1e-3 lr). Where a
+    # gradient is within its FP32 error of zero, the second step's direction is not fixed by
+    # the data; those weights are only held to Adam's largest step.
+    p1 = OM.unpack(w0.cpu().numpy().astype(np.float64))
+    _, ga = OM.loss_and_grads(p1, OM24, y)
+    ga = OM.pack(ga)
+    p2 = OM.adam_step(OM.unpack(OM.pack(p1)), OM.unpack(ga), {}, lr, 1)
+    _, gb = OM.loss_and_grads(p2, OM24, y)
+    gb = OM.pack(gb)
+    rms = lambda g: float(np.sqrt(np.mean(g ** 2)))
+    firm = (np.abs(ga) >= 0.1 * rms(ga)) & (np.abs(gb) >= 0.1 * rms(gb))
+    w0n = OM.pack(p1)
+    d = np.abs(got - ref)
+    upd = ref - w0n
+    rel = float(np.linalg.norm((got - w0n) - upd) / np.linalg.norm(upd))
+    print(f"\nAdam: update rel Frobenius {rel:.2e}; max |dw| {d[firm].max() / lr:.2e} lr over "
+          f"{int(firm.sum())} weights with firm gradients, {d.max() / lr:.2e} lr over all "
+          f"{d.size}; median {np.median(d) / lr:.2e} lr")
+    assert rel <= 1e-3
+    assert d[firm].max() <= 1e-3 * lr
+    assert d.max() <= 2.0 * lr
+    assert np.median(d) <= 1e-3 * lr
 
 
 def test_trained_start_gain_over_plain_fit(gw):

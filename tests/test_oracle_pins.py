@@ -336,3 +336,63 @@ def test_qp_newton_single_real_pole_closed_form():
     # no self-energy: E = eps + Sigma_x - v_xc, Z = 1
     E, Z, _ = OQ.qp_solve(np.zeros((1, 2, 4)) + np.array([0, 0, 3.0, -1.0]), [0.3], [-0.5], [-0.4])
     assert abs(E[0] - 0.2) <= 1e-15 and abs(Z[0] - 1.0) <= 1e-15
+
+
+def test_adam_two_steps_by_hand():
+    """Adam (Kingma & Ba 2015, Algorithm 1) worked by hand on two parameters. With
+    m_0 = v_0 = 0 the bias corrections give, after step 1, m^ = g_1 and v^ = g_1^2, so the
+    update is lr g_1 / (|g_1| + eps); after step 2,
+    m^ = (b1 (1 - b1) g_1 + (1 - b1) g_2) / (1 - b1^2) = (b1 g_1 + g_2) / (1 + b1) and
+    v^ = (b2 g_1^2 + g_2^2) / (1 + b2). With g_1 = (0.5, -2), g_2 = (1, 4), lr = 0.1,
+    b1 = 0.9, b2 = 0.999, eps = 1e-8 the second update of the first parameter is
+    0.1 * (1.45 / 1.9) / (sqrt(1.249750 / 1.999) + 1e-8)."""
+    lr, eps = 0.1, 1e-8
+    p = {"w": np.array([1.0, -3.0])}
+    st = {}
+    g1 = {"w": np.array([0.5, -2.0])}
+    g2 = {"w": np.array([1.0, 4.0])}
+    p = OM.adam_step(p, g1, st, lr, 1)
+    step1 = lr * g1["w"] / (np.abs(g1["w"]) + eps)
+    assert np.allclose(p["w"], np.array([1.0, -3.0]) - step1, rtol=0, atol=1e-15)
+    p = OM.adam_step(p, g2, st, lr, 2)
+    mh = (0.9 * g1["w"] + g2["w"]) / 1.9
+    vh = (0.999 * g1["w"] ** 2 + g2["w"] ** 2) / 1.999
+    step2 = lr * mh / (np.sqrt(vh) + eps)
+    assert np.allclose(p["w"], np.array([1.0, -3.0]) - step1 - step2, rtol=0, atol=1e-15)
+    # the first parameter by hand: 1 - 0.0999999980 - 0.0965184...
+    assert abs(p["w"][0] - (1.0 - 0.1 * 0.5 / (0.5 + 1e-8)
+                            - 0.1 * (1.45 / 1.9) / (np.sqrt(1.24975 / 1.999) + 1e-8))) <= 1e-15
+    # a constant gradient: every bias-corrected step is exactly lr g / (|g| + eps)
+    q, st2 = {"w": np.array([0.0])}, {}
+    for t in range(1, 6):
+        q = OM.adam_step(q, {"w": np.array([0.25])}, st2, lr, t)
+    assert abs(q["w"][0] + 5 * lr * 0.25 / (0.25 + eps)) <= 1e-14
+
+
+def test_mlp_loss_reading_by_construction():
+    """The loss of the learned start against curves built from known parameters: a network
+    whose last layer is zero outputs its bias o, read as a_p = s (o_4p + i o_4p+1),
+    w_p = o_4p+2 + i o_4p+3 with s = max_j |y_j|. A curve that is exactly that two-pole
+    function has loss 0; the same curve shifted by a constant c has loss |c|^2 / s^2 (the
+    residual is -c at each of the 24 nodes, averaged over the nodes)."""
+    om = S.omega_mesh(24)
+    a = np.array([0.3 - 0.05j, 0.12 + 0.02j])
+    wp = np.array([0.8 - 0.1j, 3.1 - 0.4j])
+    y = OC.model(a, wp, 1j * om)
+    s = np.abs(y).max()
+    o = np.array([a[0].real / s, a[0].imag / s, wp[0].real, wp[0].imag,
+                  a[1].real / s, a[1].imag / s, wp[1].real, wp[1].imag])
+    p = OM.init_params(1)
+    p["W3"][:] = 0.0
+    p["b3"][:] = o
+    L0, _ = OM.loss_and_grads(p, om, y[None, :])
+    assert L0 <= 1e-30
+    c = 0.02 + 0.01j
+    yc = y + c
+    sc = np.abs(yc).max()
+    p["b3"][:] = o * np.array([s / sc, s / sc, 1, 1, s / sc, s / sc, 1, 1])
+    L1, _ = OM.loss_and_grads(p, om, yc[None, :])
+    assert abs(L1 - abs(c) ** 2 / sc ** 2) <= 1e-15
+    # the features are the curve over s, interleaved (Re y_0, Im y_0, Re y_1, ...)
+    x, s2 = OM.features(yc[None, :])
+    assert s2[0] == sc and x[0, 0] == yc[0].real / sc and x[0, 3] == yc[1].imag / sc

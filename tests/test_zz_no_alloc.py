@@ -13,6 +13,8 @@ import numpy as np
 import pytest
 
 import synth_inputs as S
+from oracle import polarization as OP
+from oracle import screening as OS
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -49,6 +51,23 @@ def test_noalloc_matches_workspace_entry_point(gw, nb, nw):
         got = out.cpu().numpy()
         assert rel_fro(got, ref) <= 1e-12
         assert max_rel(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("nb", [97, 600])
+def test_noalloc_against_oracle(gw, nb):
+    """The no-allocation entry point (whose inverse runs inside one CTA per system) directly
+    against the FP64 oracle, on a polarization the oracle computed itself."""
+    wl = S.tiny(nb=nb, nocc=4, nunocc=30, mesh=(2, 2, 2), nw=3, seed=nb + 17)
+    om = wl.omega()
+    Po = OP.polarization(wl.m_full(0), wl.delta(0), om, wl.prefactor)
+    v = wl.v(0)
+    dev = torch.device("cuda:0")
+    out = gw.screened_w_noalloc(torch.as_tensor(Po, device=dev), torch.as_tensor(v, device=dev))
+    gw.check()
+    got = out.cpu().numpy()
+    ref = OS.screened_wc_all(Po, v)
+    assert rel_fro(got, ref) <= 1e-12
+    assert max_rel(got, ref) <= 1e-12
 
 
 def test_noalloc_rejects_basis_beyond_static_scratch(gw):
