@@ -355,7 +355,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == WPROD_WARP) {
       // ---------------------------------------------- weights: bulk copies
       // One round per weight slot: the round's SUB CH weights (SUB CH 4 bytes, 16-byte
-      // aligned). The quadratic form has no weights.
+      // aligned). This thread runs up to NWS rounds ahead of the A sets, so it also asks L2
+      // to prefetch the round's A columns and B tiles (both contiguous, 16-byte aligned): the
+      // A sets' loads and the B copies then find them in L2 instead of waiting for DRAM.
+      // The quadratic form has no weights (its operands are small and stay in L2).
       if (!QF && lane == 0) {
         uint64_t g = 0;
         bool ok = true;
@@ -364,6 +367,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           decode_item<QF>(L, item, q, j, bi, bj);
           const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
           const float* wsrc = L.s[q] + size_t(j) * L.kpad[q];
+          const char* xsrc = reinterpret_cast<const char*>(L.xT[q]) +
+                             size_t(bi) * size_t(L.kpad[q] / CH) * CH4 * TM * 16;
+          const char* bsrc =
+              L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * size_t(nr * SUB) * CHUNK_BYTES;
           for (int64_t r = 0; r < nr; ++r, ++g) {
             const int ws = int(g % NWS);
             if (!tc::mbar_wait(&emptyW[ws], (uint32_t(g / NWS) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
@@ -372,6 +379,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc::mbar_arrive_expect_tx(&fullW[ws], SUB * CH * 4);
             tc::bulk_g2s(wring + ws * WSLOT_BYTES, wsrc + r * SUB * CH, SUB * CH * 4, &fullW[ws]);
+            tc::bulk_prefetch_l2(xsrc + size_t(r) * SUB * CH4 * TM * 16, SUB * CH4 * TM * 16);
+            tc::bulk_prefetch_l2(bsrc + size_t(r) * STAGE_BYTES, STAGE_BYTES);
           }
         }
         if (!ok && !s_abort) {
