@@ -434,6 +434,178 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_zcol(const DieBatchT<T>
   }
 }
 
+// ---- the factorisation over many CTAs (the caller-workspace entry points) -----------------
+// A right-looking blocked Cholesky with one launch per step and panel kt: the diagonal block
+// (one CTA per system), the panel below it (one CTA per system and 256 rows, one row per
+// thread), the trailing update of the lower tiles (one CTA per system and 32 x 32 tile). Every
+// SM takes part however few systems there are (20 systems of N_b = 4096 would leave 132 of
+// 152 SMs idle with one CTA per system).
+
+// eps = 1 - v^1/2 P v^1/2 over the full matrix: grid (element blocks, system)
+template <typename T>
+__global__ void __launch_bounds__(DTHREADS) k_eps_fill(const DieBatchT<T> batch, unsigned* status) {
+  const DieSysT<T>& sys = batch.s[blockIdx.y];
+  const size_t n = size_t(sys.n), nn = n * n;
+  bool bad = false;
+  for (size_t e = blockIdx.x * size_t(DTHREADS) + threadIdx.x; e < nn; e += size_t(gridDim.x) * DTHREADS) {
+    const size_t r = e / n, c = e % n;
+    T x = scal(from_c<T>(sys.P[e]), -sqrt(sys.v[r] * sys.v[c]));
+    if (r == c) x = add_re(x, 1.0);
+    if (!fin(x)) bad = true;
+    sys.E[e] = x;
+  }
+  if (bad) raise_status(status, ST_ENONFINITE);
+}
+
+// in-place Cholesky of the kb x kb lower block held in shared memory (SD, ld DLD); returns
+// false (through *fail) on a non-positive or non-finite pivot, which is replaced by 1
+template <typename T>
+__device__ void chol_block_smem(T* SD, int kb, int* fail) {
+  const int tid = threadIdx.x;
+  for (int c = 0; c < kb; ++c) {
+    if (tid == 0) {
+      double d = re_(SD[c * DLD + c]);
+      if (!(d > 0.0) || !isfinite(d)) {
+        *fail = 1;
+        d = 1.0;
+      }
+      SD[c * DLD + c] = real_of<T>(sqrt(d));
+    }
+    __syncthreads();
+    const double dinv = 1.0 / re_(SD[c * DLD + c]);
+    for (int r = c + 1 + tid; r < kb; r += DTHREADS) SD[r * DLD + c] = scal(SD[r * DLD + c], dinv);
+    __syncthreads();
+    for (int e = tid; e < DB * DB; e += DTHREADS) {
+      const int r = e / DB, s = e % DB;
+      if (r < kb && s > c && s <= r) {
+        T x = SD[r * DLD + s];
+        csubmul(x, SD[r * DLD + c], cconj(SD[s * DLD + c]));
+        SD[r * DLD + s] = x;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// step 1 of panel kt: the diagonal block, one CTA per system
+template <typename T>
+__global__ void __launch_bounds__(DTHREADS) k_chol_diag(const DieBatchT<T> batch, int kt,
+                                                        unsigned* status) {
+  __shared__ T SD[DB * DLD];
+  __shared__ int s_fail;
+  const DieSysT<T>& sys = batch.s[blockIdx.x];
+  const int n = sys.n, nt = (n + DB - 1) / DB;
+  if (kt >= nt) return;                      // whole CTA, before any barrier
+  const int k0 = kt * DB, kb = min(DB, n - k0);
+  if (threadIdx.x == 0) s_fail = 0;
+  load_tile(SD, sys.E, n, n, n, k0, k0, 1);
+  __syncthreads();
+  chol_block_smem(SD, kb, &s_fail);
+  for (int e = threadIdx.x; e < DB * DB; e += DTHREADS) {
+    const int r = e / DB, c = e % DB;
+    if (r < kb && c <= r) sys.E[size_t(k0 + r) * n + k0 + c] = SD[r * DLD + c];
+  }
+  if (threadIdx.x == 0 && s_fail) raise_status(status, ST_ENOTHPD);
+}
+
+// step 2: the panel X L_kk^H = A_ik below the diagonal block, one row per thread;
+// grid (256-row blocks of the trailing rows, system)
+template <typename T>
+__global__ void __launch_bounds__(DTHREADS) k_chol_panel(const DieBatchT<T> batch, int kt) {
+  __shared__ T SD[DB * DLD];
+  const DieSysT<T>& sys = batch.s[blockIdx.y];
+  const int n = sys.n, nt = (n + DB - 1) / DB;
+  if (kt >= nt - 1) return;                  // no rows below the last block
+  const int k0 = kt * DB;                    // a full block: kt < nt - 1
+  const int r0 = k0 + DB + blockIdx.x * DTHREADS;
+  if (r0 >= n) return;                       // whole CTA, before any barrier
+  load_tile(SD, sys.E, n, n, n, k0, k0, 1);
+  __syncthreads();
+  const int r = r0 + threadIdx.x;
+  if (r < n) {
+    T x[DB];
+    T* row = sys.E + size_t(r) * n + k0;
+#pragma unroll
+    for (int c = 0; c < DB; ++c) x[c] = row[c];
+#pragma unroll
+    for (int c = 0; c < DB; ++c) {
+      T acc = x[c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) csubmul(acc, x[k], cconj(SD[c * DLD + k]));
+      x[c] = scal(acc, 1.0 / re_(SD[c * DLD + c]));
+    }
+#pragma unroll
+    for (int c = 0; c < DB; ++c) row[c] = x[c];
+  }
+}
+
+// step 3: the trailing update A_ij -= L_ik L_jk^H for kt < j <= i (lower tiles; the diagonal
+// tiles keep their lower triangle); grid (tiles of the largest system, system)
+template <typename T>
+__global__ void __launch_bounds__(DTHREADS) k_chol_update(const DieBatchT<T> batch, int kt) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  T* SA = reinterpret_cast<T*>(dsm_raw);
+  T* SB = SA + DB * DLD;
+  const DieSysT<T>& sys = batch.s[blockIdx.y];
+  const int n = sys.n, nt = (n + DB - 1) / DB;
+  const int m = nt - kt - 1;                 // trailing block rows
+  const int64_t t = blockIdx.x;
+  if (m <= 0 || t >= int64_t(m) * (m + 1) / 2) return;   // whole CTA, before any barrier
+  // t -> (ii, jj), 0 <= jj <= ii < m, row by row
+  int ii = int((sqrt(8.0 * double(t) + 1.0) - 1.0) * 0.5);
+  while (int64_t(ii + 1) * (ii + 2) / 2 <= t) ++ii;
+  while (int64_t(ii) * (ii + 1) / 2 > t) --ii;
+  const int jj = int(t - int64_t(ii) * (ii + 1) / 2);
+  const int it = kt + 1 + ii, jt = kt + 1 + jj;
+  const int k0 = kt * DB;
+  const int tid = threadIdx.x, tr = tid >> 3, tc = tid & 7;
+  const T* E = sys.E;
+  load_tile(SA, E, n, n, n, it * DB, k0, 0);                  // L_ik
+  for (int e = tid; e < DB * DB; e += DTHREADS) {             // SB[k][c] = conj(L_jk[c][k])
+    const int k = e / DB, c = e % DB;
+    const int R = jt * DB + c;
+    SB[k * DLD + c] = R < n ? cconj(E[size_t(R) * n + k0 + k]) : T{};
+  }
+  __syncthreads();
+  T acc[4] = {T{}, T{}, T{}, T{}};
+  tile_mac<false>(acc, SA, SB, tr, tc);
+  const int R = it * DB + tr;
+  if (R < n) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int C = jt * DB + tc + 8 * b;
+      if (C < n && C <= R) sys.E[size_t(R) * n + C] = csub(E[size_t(R) * n + C], acc[b]);
+    }
+  }
+}
+
+template <typename T>
+static int launch_cholesky_grid(const DieBatchT<T>& batch, int nsys, int ntmax, cudaStream_t s,
+                                const DeviceCtx& ctx) {
+  const size_t smem_u = 2 * DB * DLD * sizeof(T);
+  int rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_chol_update<T>), smem_u, ctx.device);
+  if (rc) return rc;
+  int nmax = 0;
+  for (int i = 0; i < nsys; ++i) nmax = std::max(nmax, batch.s[i].n);
+  const int64_t nn = int64_t(nmax) * nmax;
+  const unsigned fb = unsigned(std::min<int64_t>((nn + DTHREADS - 1) / DTHREADS, 4096));
+  k_eps_fill<T><<<dim3(fb, unsigned(nsys)), DTHREADS, 0, s>>>(batch, ctx.status);
+  GW_LAUNCH_CHECK("k_eps_fill");
+  for (int kt = 0; kt < ntmax; ++kt) {
+    k_chol_diag<T><<<unsigned(nsys), DTHREADS, 0, s>>>(batch, kt, ctx.status);
+    GW_LAUNCH_CHECK("k_chol_diag");
+    const int rows = nmax - (kt + 1) * DB;
+    if (rows <= 0) continue;
+    const unsigned pb = unsigned((rows + DTHREADS - 1) / DTHREADS);
+    k_chol_panel<T><<<dim3(pb, unsigned(nsys)), DTHREADS, 0, s>>>(batch, kt);
+    GW_LAUNCH_CHECK("k_chol_panel");
+    const int64_t m = ntmax - kt - 1;
+    k_chol_update<T><<<dim3(unsigned(m * (m + 1) / 2), unsigned(nsys)), DTHREADS, smem_u, s>>>(batch, kt);
+    GW_LAUNCH_CHECK("k_chol_update");
+  }
+  return GW_OK;
+}
+
 template <typename T>
 static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const DeviceCtx& ctx) {
   const size_t smem = 3 * DB * DLD * sizeof(T);
@@ -453,8 +625,15 @@ static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const
       batch.s[i] = sys[b0 + i];
       ntmax = std::max(ntmax, (batch.s[i].n + DB - 1) / DB);
     }
-    k_dielectric<T><<<unsigned(nb_), DTHREADS, smem, s>>>(batch, ctx.status, !by_columns);
-    GW_LAUNCH_CHECK("k_dielectric");
+    if (by_columns) {
+      // caller workspace: the factorisation over many CTAs, then the inverse by block columns
+      int rc = launch_cholesky_grid<T>(batch, int(nb_), ntmax, s, ctx);
+      if (rc) return rc;
+    } else {
+      // no-allocation entry: factorisation and inverse inside one CTA per system
+      k_dielectric<T><<<unsigned(nb_), DTHREADS, smem, s>>>(batch, ctx.status, true);
+      GW_LAUNCH_CHECK("k_dielectric");
+    }
     if (by_columns) {
       const dim3 g2(static_cast<unsigned>(nb_), static_cast<unsigned>(ntmax));
       k_dielectric_dinv<T><<<g2, DTHREADS, DB * DLD * sizeof(T), s>>>(batch);

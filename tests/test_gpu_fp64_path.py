@@ -331,3 +331,20 @@ def test_polarization_fp64_full_size_sampled(gw):
     ref = OP.polarization(wl.m_rows(iq, cols=cols), d, om, wl.prefactor)
     assert rel_fro(got, ref) <= 1e-12
     assert max_rel(got, ref) <= 1e-12
+
+
+@pytest.mark.slow
+def test_screened_w_large_basis_against_oracle(gw):
+    """N_b = 2048 (the supercell's order of magnitude) at one frequency: the factorisation over
+    many CTAs (one launch per panel step), the inverse by block columns and W^c, against the
+    oracle on a polarization it computed itself from 4,096 transitions."""
+    wl = S.tiny(nb=2048, nocc=8, nunocc=256, mesh=(1, 1, 2), nw=1, seed=2048)
+    om = wl.omega()
+    Po = OP.polarization(wl.m_full(0), wl.delta(0), om, wl.prefactor)
+    v = wl.v(0)
+    Wg = gw.screened_w([T(Po)], [T(v)])[0]
+    gw.check()
+    Wg = Wg.cpu().numpy()
+    ref = OS.screened_wc_all(Po, v)
+    assert rel_fro(Wg, ref) <= 1e-12
+    assert max_rel(Wg, ref) <= 1e-12
