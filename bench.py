@@ -39,10 +39,11 @@ import synth_inputs as S  # noqa: E402
 
 METRIC = "P(iω)+Σ^c GFLOP/s and % of roofline, mixed vs FP64 on GB300 at ≤1e-6 rel err"
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one bench launch of the
-# split-precision HERK, from the ncu capture summarised in profiles/ (one q cut to
-# K = 102,400, scaled by K x q to the 8 q of K = 409,600). Valid for the kernel as profiled.
-HERK_TRAFFIC_BYTES = {"tf32x3": 14.86e9 * 32, "bf16x3": 8.06e9 * 32}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one HERK launch of the bench
+# (one q of K = 409,600), from the ncu capture summarised in profiles/ (one q cut to
+# K = 102,400, scaled by K: the tile grid is the same and the traffic grows in proportion with
+# K). Valid for the kernel as profiled; None where no capture of the current kernel exists.
+HERK_TRAFFIC_BYTES = {"bf16x3": (7.054e9 + 0.847e9) * 4, "tf32x3": None}
 
 
 def workload_flops(wl):
@@ -115,7 +116,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(wl, budget_s=20.0):
+def cpu_oracle_sample(wl, kpoints=12):
     """Time the CPU oracle on a bounded sample: P for one q over the transitions of
     the first k-points (all 16 frequencies), plus the Sigma^c pair coefficients of 256
     pairs at one frequency; returns algorithmic GFLOP/s and the sample description."""
@@ -125,7 +126,7 @@ def cpu_oracle_sample(wl, budget_s=20.0):
     om = wl.omega()
     nb = wl.nb[0]
     per_k = wl.nocc * wl.nunocc[0]
-    rows = per_k * 12                                # transitions of 12 of the 64 k-points
+    rows = per_k * kpoints                           # transitions of the first k-points
     M = wl.m_rows(0, rows=np.arange(rows))
     d = wl.delta(0)[:rows]
     t0 = time.perf_counter()
@@ -142,7 +143,7 @@ def cpu_oracle_sample(wl, budget_s=20.0):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": (fl_p + fl_s) / secs / 1e9, "unit": "GFLOP/s", "cores": cores,
             "kind": "oracle", "seconds": round(secs, 3),
-            "sample": f"P of q=0 over {rows} of {wl.K(0)} transitions (12 of 64 k-points), "
+            "sample": f"P of q=0 over {rows} of {wl.K(0)} transitions ({kpoints} of {wl.nk} k-points), "
                       f"all {len(om)} frequencies, N_b={nb}; Sigma pair coefficients of 256 "
                       f"pairs at one frequency (numpy FP64, BLAS threads)"}
 
@@ -152,11 +153,11 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     res = []
-    for _ in range(max(1, args.warmup)):
-        cpu_oracle_sample(wl)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, args.oracle_kpoints)
     t = time.perf_counter()
     for _ in range(args.steps):
-        res.append(cpu_oracle_sample(wl))
+        res.append(cpu_oracle_sample(wl, args.oracle_kpoints))
     el = time.perf_counter() - t
     v = statistics.median([r["value"] for r in res])
     cb = dict(res[0])
@@ -215,18 +216,25 @@ class Pipeline:
         self.ev_p0 = torch.cuda.Event(enable_timing=True)
         self.ev_p1 = torch.cuda.Event(enable_timing=True)
         self.p_ms = []
+        self.herk_events = []
 
     def _sigma_mixed_ok(self):
         return getattr(self.gw, "SIGMA_MIXED", False)
 
     def step(self, time_p=False):
         gw = self.gw
+        opts = None
         if time_p:
             self.ev_p0.record()
+            # a (start, end) event pair around each HERK launch: the dominant kernel's own time
+            opts = {"herk_events": [(self.torch.cuda.Event(enable_timing=True),
+                                     self.torch.cuda.Event(enable_timing=True))
+                                    for _ in range(self.wl.nq)]}
         gw.polarization(self.M, self.delta, self.om, self.wl.prefactor, self.prec, out=self.P,
-                        ws=self.ws_p)
+                        ws=self.ws_p, options=opts)
         if time_p:
             self.ev_p1.record()
+            self.herk_events.append(opts["herk_events"][:opts["herk_launches"]])
         gw.screened_w(self.P, self.v, out=self.P, ws=self.ws_w)
         gw.sigma_c(list(self.wl.wq), self.Msig, self.pair_state, self.eps, self.P, self.om,
                    self.om_out, self.nsig, precision=self.sprec, out=self.sigma, ws=self.ws_s)
@@ -271,8 +279,11 @@ class Pipeline:
                     groups, items = groups + 1, 0
                 items += t * (t + 1) // 2 * nw
             p = 2 * nq + groups
-        w = 4 * ((nq * nw + 255) // 256)            # dielectric: factor, diagonal inverses,
-                                                    # inverse by block columns, W^c
+        # dielectric, per batch of <= 256 systems: eps, per 32-wide panel the diagonal block
+        # (+ panel and trailing update but the last), diagonal inverses, inverse by block
+        # columns, W^c
+        nt = (max(self.wl.nb) + 31) // 32
+        w = (3 * nt + 2) * ((nq * nw + 255) // 256)
         if self.sprec == "fp64":
             s = 1 + nq                              # pair coefficients + per-q reductions
         else:
@@ -302,6 +313,9 @@ def run_gpu(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
+    if world > 1:
+        assert dist.get_world_size() == args.gpus, (dist.get_world_size(), args.gpus)
+
     for _ in range(args.warmup):
         pipe.step()
     gw.check()
@@ -321,6 +335,7 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     p_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in p_ms)
+    herk_ms = [a.elapsed_time(b) for step in pipe.herk_events[-args.steps:] for a, b in step]
     barrier()
     ck = clocks.stop()
     gw.check()
@@ -343,8 +358,13 @@ def run_gpu(args, rank, world):
         return
     pk, src = peaks()
     ratio = 0.5 if args.precision == "tf32x3" else 1.0
-    peak_tf = pk["bf16_tflops"] * ratio if args.precision != "fp64" else 1.25
-    achieved = fp / wl.nq * wl.nq / (p_launch_ms * 1e-3) / 1e12
+    # the HERK runs inside a step of about half a second: the sustained peak applies
+    peak_tf = (pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * ratio
+               if args.precision != "fp64" else 1.25)
+    # one HERK launch per q here (a q of this size fills a group): algorithmic flop of one q
+    # over the launch's average duration (CUDA events around each launch, on its stream)
+    herk_launch_ms = statistics.mean(herk_ms) if herk_ms else p_launch_ms / wl.nq
+    achieved = fp / wl.nq / (herk_launch_ms * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": step_flops * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -358,15 +378,19 @@ def run_gpu(args, rank, world):
                    "sigma_precision": pipe.sprec, "l2": "inputs larger than L2 (M = "
                    f"{sum(m.numel() * m.element_size() for m in pipe.M) / 1e9:.1f} GB)"},
         "roofline": {"bound": "tensor" if args.precision != "fp64" else "alu",
-                     "kernel": "gw_polarization (split-precision HERK + per-q prep)",
+                     "kernel": ("k_herk_tc (split-precision HERK, one launch per q; events around "
+                                "each launch)" if args.precision != "fp64" else "k_herk_fp64"),
                      "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf,
-                     "peak_source": (f"{src} bf16 x 0.5 (nominal tf32/bf16)" if args.precision == "tf32x3"
-                                     else f"{src} bf16" if args.precision == "bf16x3"
+                     "peak_source": (f"{src} bf16 sustained x 0.5 (nominal tf32/bf16)"
+                                     if args.precision == "tf32x3"
+                                     else f"{src} bf16 sustained" if args.precision == "bf16x3"
                                      else "nominal FP64 1.25 TFLOP/s"),
                      "traffic": HERK_TRAFFIC_BYTES.get(args.precision),
-                     "traffic_source": "ncu capture of one q at K = 102,400 scaled by K x q",
-                     "launch_ms": p_launch_ms},
+                     "traffic_source": "ncu capture of one q at K = 102,400 scaled by K to one launch",
+                     "algorithmic_bytes": wl.K(0) * wl.nb[0] * 8 + wl.nw * wl.nb[0] ** 2 * 16,
+                     "launch_ms": herk_launch_ms, "launches_per_step": len(herk_ms) // max(1, args.steps),
+                     "polarization_call_ms": p_launch_ms},
         "clocks": ck,
         "e2e": e2e,
         "gpu_launches": pipe.launches_per_step() * args.steps,
@@ -376,7 +400,7 @@ def run_gpu(args, rank, world):
         "sampled_err_Sigma": sig_err,
     }
     if world == 1:
-        line["cpu_baseline"] = cpu_oracle_sample(wl)
+        line["cpu_baseline"] = cpu_oracle_sample(wl, args.oracle_kpoints)
     print(json.dumps(line), flush=True)
 
 
@@ -549,6 +573,113 @@ def run_case_herk(args):
     print(json.dumps({"case": "herk", "K": K, "N_b": nb, "n_omega": wl.nw,
                       "precision": args.precision, "real_projections": bool(args.real), "ms": ms,
                       "tflops": fl / (ms * 1e-3) / 1e12}), flush=True)
+
+
+def run_case_supercell(args):
+    """The supercell-shaped workload at full size: one q, N_k = 8, N_MPB = 4096, 256 occupied /
+    3000 unoccupied bands (K = 6,144,000 transitions), 20 frequencies, 16 Sigma states x 3256
+    partner bands. The polarization runs in eight K slices of one k point each (768,000
+    transitions, 25 GB of complex64 projections generated on the device per slice) accumulated
+    into one P (P is additive over transitions; gw_polarization_ex with accumulate); then the 20
+    FP64 dielectric solves of order 4096 and the Sigma^c of the 16 states. Prints one JSON line
+    with the time and algorithmic rate of every stage and, unless --no-sigma-check, the error of
+    P on 48 sampled basis indices (their full cross block, diagonal included) at full K against
+    the oracle (host draws of those columns by spawned workers)."""
+    import multiprocessing as mp
+    import torch
+    import paper_1003_0316_gb300 as gw
+    wl = S.supercell()
+    prec, sprec = args.precision, args.sigma_precision
+    nb, nw = wl.nb[0], wl.nw
+    om = wl.omega()
+    K = wl.K(0)
+    kslice = wl.nocc * wl.nunocc[0]
+    nslice = K // kslice
+    dev = torch.device("cuda:0")
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    d_all = torch.as_tensor(wl.delta(0), device=dev)
+    P = torch.zeros((nw, nb, nb), dtype=torch.complex128, device=dev)
+    M = torch.empty((kslice, nb), dtype=torch.complex64, device=dev)
+    opts = {"accumulate": True}
+    ws = torch.empty(gw.polarization_workspace_ex([kslice], [nb], nw, prec, opts), dtype=torch.uint8,
+                     device=dev)
+    # a small warm-up (kernel attributes) outside the timed stages
+    tiny = S.tiny(nb=64)
+    gw.polarization([torch.as_tensor(tiny.m_full(0), dtype=torch.complex64, device=dev)],
+                    [torch.as_tensor(tiny.delta(0), device=dev)], tiny.omega(), 1.0, prec)
+    torch.cuda.synchronize()
+    gen_ms = pol_ms = herk_ms = 0.0
+    for k in range(nslice):
+        g0, g1, p0, p1 = E(), E(), E(), E()
+        g0.record()
+        gw.synth_projections(wl.seed, S.TID_M, wl.qs[0], k * kslice, kslice, nb, out=M)
+        g1.record()
+        ev = [(E(), E())]
+        p0.record()
+        gw.polarization([M], [d_all[k * kslice:(k + 1) * kslice]], om, wl.prefactor, prec, out=[P],
+                        ws=ws, options=dict(opts, herk_events=ev))
+        p1.record()
+        torch.cuda.synchronize()
+        gw.check()
+        gen_ms += g0.elapsed_time(g1)
+        pol_ms += p0.elapsed_time(p1)
+        herk_ms += ev[0][0].elapsed_time(ev[0][1])
+    del M, ws
+    torch.cuda.empty_cache()
+    fl_p = 4.0 * K * nb * (nb + 1) * nw
+    err_p = None
+    if not args.no_sigma_check:
+        cols = np.sort(np.random.default_rng(4096).choice(nb, size=48, replace=False))
+        got = P[:, cols][:, :, cols].cpu().numpy()
+        from oracle import polarization as OP
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        with mp.get_context("spawn").Pool(max(1, min(16, cores))) as pool:
+            Mc = S.m_rows_parallel(wl, 0, pool, dtype=np.complex64, cols=cols)
+        ref = OP.polarization(Mc.astype(np.complex128), wl.delta(0), om, wl.prefactor)
+        err_p = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    # the FP64 dielectric solves (in place)
+    v = torch.as_tensor(wl.v(0), device=dev)
+    wsw = torch.empty(gw.screened_w_workspace([nb], nw), dtype=torch.uint8, device=dev)
+    w0, w1 = E(), E()
+    w0.record()
+    gw.screened_w([P], [v], out=[P], ws=wsw)
+    w1.record()
+    torch.cuda.synchronize()
+    gw.check()
+    del wsw
+    torch.cuda.empty_cache()
+    # Sigma^c of the 16 states
+    ps, eps = wl.sigma_pairs(0)
+    Ms = gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[0], 0, len(ps), nb,
+                              dtype=torch.complex64).mul_(wl.msig_scale)
+    pst = torch.as_tensor(ps, dtype=torch.int32, device=dev)
+    epst = torch.as_tensor(eps, device=dev)
+    nsig = len(wl.sigma_states())
+    sig = torch.empty((nsig, nw), dtype=torch.complex128, device=dev)
+    wss = torch.empty(gw.sigma_workspace([len(ps)], [nb], nw, sprec), dtype=torch.uint8, device=dev)
+    s0, s1 = E(), E()
+    s0.record()
+    gw.sigma_c(list(wl.wq), [Ms], [pst], [epst], [P], om, om, nsig, precision=sprec, out=sig, ws=wss)
+    s1.record()
+    torch.cuda.synchronize()
+    gw.check()
+    fl_s = 8.0 * nb * nb * len(ps) * nw
+    w_ms, s_ms = w0.elapsed_time(w1), s0.elapsed_time(s1)
+    print(json.dumps({
+        "case": "supercell", "workload": wl.name, "K": K, "k_slices": nslice, "N_b": nb,
+        "n_omega": nw, "precision": prec, "sigma_precision": sprec, "pairs": len(ps),
+        "generation_ms": gen_ms,
+        "polarization": {"ms": pol_ms, "tflops": fl_p / (pol_ms * 1e-3) / 1e12,
+                         "herk_ms": herk_ms, "herk_tflops": fl_p / (herk_ms * 1e-3) / 1e12,
+                         "algorithmic_flop": fl_p},
+        "dielectric_fp64": {"ms": w_ms, "tflops": 4.0 * nb ** 3 * nw / (w_ms * 1e-3) / 1e12,
+                            "systems": nw},
+        "sigma": {"ms": s_ms, "tflops": fl_s / (s_ms * 1e-3) / 1e12},
+        "total_ms": gen_ms + pol_ms + w_ms + s_ms,
+        "path_tflops": (fl_p + fl_s) / ((pol_ms + w_ms + s_ms) * 1e-3) / 1e12,
+        "sampled_rel_err_P": err_p,
+        "check": "48 sampled basis indices (full cross block) at full K against the oracle",
+        "max_abs_sigma_Ha": float(sig.abs().max())}), flush=True)
 
 
 def run_case_fit(args):
@@ -804,6 +935,19 @@ def run_case_aux(args):
                       "qp_solve_ms": ms_qp, "qp_states": n}), flush=True)
 
 
+def relaunch(args):
+    """--gpus N > 1 without a torchrun environment: start N ranks on this node through
+    torch.distributed.run (127.0.0.1, a free port) and return its exit code."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={args.gpus}", "--master-addr=127.0.0.1", f"--master-port={port}",
+           os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -814,12 +958,14 @@ def main():
     ap.add_argument("--sigma-precision", default="tf32x3", choices=["bf16x3", "tf32x3", "fp64"],
                     help="precision of the Sigma pair coefficients (TF32x3 by default: its Sigma^c "
                          "error at the workload's sizes is 1e-6 Ha against 2e-5 Ha for BF16x3)")
+    ap.add_argument("--oracle-kpoints", type=int, default=12,
+                    help="k points of the oracle's timed sample (CPU baseline and reference arm)")
     ap.add_argument("--no-sigma-check", action="store_true",
                     help="skip the oracle comparison of one q's Sigma^c after the timed region")
     ap.add_argument("--real", action="store_true",
                     help="--case herk with real projections (inversion-symmetric systems)")
     ap.add_argument("--case", default=None,
-                    choices=["herk", "fit", "batched", "extrapolar", "aux"],
+                    choices=["herk", "fit", "batched", "extrapolar", "aux", "supercell"],
                     help="run one profiling case instead of the bench step")
     args = ap.parse_args()
     if args.case == "herk":
@@ -837,6 +983,11 @@ def main():
     if args.case == "aux":
         run_case_aux(args)
         return
+    if args.case == "supercell":
+        run_case_supercell(args)
+        return
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch(args))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:

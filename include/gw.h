@@ -111,6 +111,47 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host,
                     double* const* P_dev, int precision,
                     void* ws_dev, size_t ws_bytes, gw_stream_t stream);
 
+/* Execution options of gw_polarization_ex (no counterpart in the paper: they control how the
+ * GPU computes Eq. polar_MB, not what is computed; every choice gives the same P up to the
+ * rounding of its precision). NULL, or a zero-initialised struct, gives the behaviour of
+ * gw_polarization.
+ *   accumulate          nonzero: P_dev[q] += this call's sum over its transitions (P is
+ *                       additive over transitions, so disjoint slices of a K too large for
+ *                       one call are processed one after another into one P); 0: overwrite.
+ *   group_items_per_sm  split-precision paths: q points are prepared and launched in groups,
+ *                       a group closing at this many work items (128 x 128 tile x frequency)
+ *                       per SM; 0 means 4. Larger groups share one launch, smaller ones need
+ *                       less workspace.
+ *   b_stages            split-precision paths: shared-memory stages of the B operand, 4 or 6
+ *                       (two rounds more in flight, less L1 for the A loads); 0 means 4.
+ *   fp64_waves          GW_FP64: the K splits fill at least this many waves of CTAs; 0 means 4.
+ *   herk_events         NULL, or n_herk_events pairs of cudaEvent_t (created by the caller,
+ *                       layout [start, end] per pair): the call records the pair around each
+ *                       of its first n_herk_events HERK launches on `stream` (the dominant
+ *                       kernel alone, without the per-q preparation);
+ *   n_herk_events       the number of pairs in herk_events;
+ *   herk_launches_out   NULL, or (host) the number of HERK launches of the call.
+ * gw_polarization_workspace_ex gives the workspace for the same options (group_items_per_sm
+ * and fp64_waves change it). Errors: GW_EINVAL for b_stages other than 0, 4 or 6, negative
+ * counts. */
+typedef struct gw_pol_options {
+  int accumulate;
+  int group_items_per_sm;
+  int b_stages;
+  int fp64_waves;
+  void* const* herk_events;
+  int n_herk_events;
+  int* herk_launches_out;
+} gw_pol_options;
+size_t gw_polarization_workspace_ex(int nq, const int64_t* K_host, const int* nb_host, int nw,
+                                    int precision, const gw_pol_options* options);
+int gw_polarization_ex(int nq, const int64_t* K_host, const int* nb_host,
+                       const void* const* M_dev, int m_dtype,
+                       const double* const* delta_dev, const double* const* f_dev,
+                       double prefactor, int nw, const double* omega_host,
+                       double* const* P_dev, int precision, const gw_pol_options* options,
+                       void* ws_dev, size_t ws_bytes, gw_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Extrapolar correction of the polarization (Sec. V, the paragraph on the convergence with
  * the number of bands; the scheme of Bruneval and Gonze). The unoccupied sum of Eq. polar_MB

@@ -52,6 +52,16 @@ _sig("gw_transition_weights", _i32, _i64, _vp, _vp, _f64, _i32, _P(_f64), _vp, _
 _sig("gw_polarization_workspace", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32)
 _sig("gw_polarization", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp), _f64,
      _i32, _P(_f64), _P(_vp), _i32, _vp, _sz, _vp)
+class PolOptions(ctypes.Structure):
+    """gw_pol_options (include/gw.h)."""
+    _fields_ = [("accumulate", _i32), ("group_items_per_sm", _i32), ("b_stages", _i32),
+                ("fp64_waves", _i32), ("herk_events", _P(_vp)), ("n_herk_events", _i32),
+                ("herk_launches_out", _P(_i32))]
+
+
+_sig("gw_polarization_workspace_ex", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32, _P(PolOptions))
+_sig("gw_polarization_ex", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp), _f64,
+     _i32, _P(_f64), _P(_vp), _i32, _P(PolOptions), _vp, _sz, _vp)
 _sig("gw_polarization_extrapolar", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp),
      _P(_vp), _P(_i64), _P(_vp), _P(_vp), _P(_vp), _f64, _i32, _P(_f64), _P(_vp), _i32, _vp, _sz,
      _vp)
@@ -172,8 +182,48 @@ def polarization_workspace(Ks, nbs, nw, precision):
                                           PRECISIONS.get(precision, precision))
 
 
-def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=None, ws=None):
-    """P[q] = sum_t w_tj M_tI conj(M_tJ) for each q (complex128 [nw][N_b][N_b])."""
+def _pol_options(options):
+    """A PolOptions from a dict (keys as in gw_pol_options; "herk_events": a list of
+    (start, end) torch.cuda.Event pairs). Returns (struct or None, keep-alive objects)."""
+    if not options:
+        return None, ()
+    o = PolOptions()
+    o.accumulate = int(bool(options.get("accumulate", False)))
+    o.group_items_per_sm = int(options.get("group_items_per_sm", 0))
+    o.b_stages = int(options.get("b_stages", 0))
+    o.fp64_waves = int(options.get("fp64_waves", 0))
+    keep = []
+    evs = options.get("herk_events")
+    if evs:
+        handles = []
+        for a, b in evs:
+            for e in (a, b):
+                if not e.cuda_event:             # torch creates the event on its first record
+                    e.record()
+                handles.append(e.cuda_event)
+        arr = (_vp * len(handles))(*handles)
+        keep.append(arr)
+        o.herk_events = ctypes.cast(arr, _P(_vp))
+        o.n_herk_events = len(evs)
+    cnt = _i32(0)
+    keep.append(cnt)
+    o.herk_launches_out = ctypes.pointer(cnt)
+    return o, keep
+
+
+def polarization_workspace_ex(Ks, nbs, nw, precision, options=None):
+    o, _keep = _pol_options(options)
+    return _lib.gw_polarization_workspace_ex(len(Ks), _arr(_i64, Ks), _arr(_i32, nbs), nw,
+                                             PRECISIONS.get(precision, precision),
+                                             ctypes.byref(o) if o is not None else None)
+
+
+def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=None, ws=None,
+                 options=None):
+    """P[q] = sum_t w_tj M_tI conj(M_tJ) for each q (complex128 [nw][N_b][N_b]).
+    options: None or a dict of gw_pol_options fields (accumulate, group_items_per_sm,
+    b_stages, fp64_waves, herk_events = [(start, end), ...] torch.cuda.Event pairs); after the
+    call options["herk_launches"] holds the number of HERK launches."""
     prec = PRECISIONS.get(precision, precision)
     om, nw = _om(omega)
     nq = len(Ms)
@@ -182,15 +232,23 @@ def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=No
     dev = Ms[0].device
     if out is None:
         out = [torch.empty((nw, nb, nb), dtype=torch.complex128, device=dev) for nb in nbs]
-    need = polarization_workspace(Ks, nbs, nw, prec)
+    o, keep = _pol_options(options)
+    need = polarization_workspace_ex(Ks, nbs, nw, prec, options)
     if ws is None:
         wsb, wsp, wsn = _ws(need, dev)
     else:
         wsb, wsp, wsn = ws, _vp(ws.data_ptr()), ws.numel()
     fptr = _ptrs(fs) if fs is not None else None
-    _raise(_lib.gw_polarization(nq, _arr(_i64, Ks), _arr(_i32, nbs), _ptrs(Ms), _dtype_code(Ms[0]),
-                                _ptrs(deltas), fptr, float(prefactor), nw, om, _ptrs(out), prec,
-                                wsp, wsn, _stream()))
+    if o is None:
+        _raise(_lib.gw_polarization(nq, _arr(_i64, Ks), _arr(_i32, nbs), _ptrs(Ms),
+                                    _dtype_code(Ms[0]), _ptrs(deltas), fptr, float(prefactor), nw,
+                                    om, _ptrs(out), prec, wsp, wsn, _stream()))
+    else:
+        _raise(_lib.gw_polarization_ex(nq, _arr(_i64, Ks), _arr(_i32, nbs), _ptrs(Ms),
+                                       _dtype_code(Ms[0]), _ptrs(deltas), fptr, float(prefactor),
+                                       nw, om, _ptrs(out), prec, ctypes.byref(o), wsp, wsn,
+                                       _stream()))
+        options["herk_launches"] = keep[-1].value
     return out
 
 

@@ -96,6 +96,32 @@ static int check_ws(void* ws, size_t ws_bytes, size_t need) {
   return GW_OK;
 }
 
+int resolve_pol_options(const gw_pol_options* o, PolOpts* out) {
+  *out = PolOpts{};
+  if (o == nullptr) return GW_OK;
+  if (o->group_items_per_sm < 0 || o->fp64_waves < 0 || o->n_herk_events < 0)
+    return set_error(GW_EINVAL, "negative count in gw_pol_options");
+  if (o->b_stages != 0 && o->b_stages != 4 && o->b_stages != 6)
+    return set_error(GW_EINVAL, "b_stages=%d: 0, 4 or 6", o->b_stages);
+  if (o->n_herk_events > 0 && o->herk_events == nullptr)
+    return set_error(GW_EINVAL, "n_herk_events > 0 with NULL herk_events");
+  out->accumulate = o->accumulate != 0;
+  if (o->group_items_per_sm) out->group_items_per_sm = o->group_items_per_sm;
+  if (o->b_stages) out->b_stages = o->b_stages;
+  if (o->fp64_waves) out->fp64_waves = o->fp64_waves;
+  out->events = o->herk_events;
+  out->n_events = o->n_herk_events;
+  return GW_OK;
+}
+
+int record_herk_event(PolOpts& o, int idx, bool end, cudaStream_t s) {
+  if (o.events == nullptr || idx >= o.n_events) return GW_OK;
+  cudaEvent_t ev = static_cast<cudaEvent_t>(o.events[2 * idx + (end ? 1 : 0)]);
+  if (ev == nullptr) return GW_OK;
+  GW_CUDA_TRY(cudaEventRecord(ev, s));
+  return GW_OK;
+}
+
 }  // namespace gw
 
 using namespace gw;
@@ -151,11 +177,23 @@ static int validate_pol(int nq, const int64_t* K, const int* nb, int precision) 
   return GW_OK;
 }
 
+static size_t polarization_workspace_impl(int nq, const int64_t* K_host, const int* nb_host,
+                                          int nw, int precision, const PolOpts& o) {
+  if (validate_pol(nq, K_host, nb_host, precision) || nw < 1 || nw > GW_MAX_NW) return 0;
+  if (precision == GW_FP64) return pol_fp64_workspace(nq, K_host, nb_host, nw, o);
+  return pol_tc_workspace(nq, K_host, nb_host, nw, precision, o);
+}
+
 size_t gw_polarization_workspace(int nq, const int64_t* K_host, const int* nb_host, int nw,
                                  int precision) {
-  if (validate_pol(nq, K_host, nb_host, precision) || nw < 1 || nw > GW_MAX_NW) return 0;
-  if (precision == GW_FP64) return pol_fp64_workspace(nq, K_host, nb_host, nw);
-  return pol_tc_workspace(nq, K_host, nb_host, nw, precision);
+  return polarization_workspace_impl(nq, K_host, nb_host, nw, precision, PolOpts{});
+}
+
+size_t gw_polarization_workspace_ex(int nq, const int64_t* K_host, const int* nb_host, int nw,
+                                    int precision, const gw_pol_options* options) {
+  PolOpts o;
+  if (resolve_pol_options(options, &o)) return 0;
+  return polarization_workspace_impl(nq, K_host, nb_host, nw, precision, o);
 }
 
 static int polarization_impl(int nq, const int64_t* K_host, const int* nb_host,
@@ -163,8 +201,11 @@ static int polarization_impl(int nq, const int64_t* K_host, const int* nb_host,
                              const double* const* dbar_dev, const double* const* f_dev,
                              double prefactor, int nw, const double* omega_host,
                              double* const* P_dev, int precision, void* ws_dev, size_t ws_bytes,
-                             gw_stream_t stream) {
-  int rc = validate_pol(nq, K_host, nb_host, precision);
+                             gw_stream_t stream, const gw_pol_options* options = nullptr) {
+  PolOpts po;
+  int rc = resolve_pol_options(options, &po);
+  if (rc) return rc;
+  rc = validate_pol(nq, K_host, nb_host, precision);
   if (rc) return rc;
   OmegaArr om;
   if ((rc = fill_omega(nw, omega_host, &om, false, false))) return rc;
@@ -192,14 +233,18 @@ static int polarization_impl(int nq, const int64_t* K_host, const int* nb_host,
     if (precision != GW_FP64 && (reinterpret_cast<uintptr_t>(qs[q].M) & 15u))
       return set_error(GW_EINVAL, "M_dev[%d] not 16-byte aligned", q);
   }
-  size_t need = gw_polarization_workspace(nq, K_host, nb_host, nw, precision);
+  size_t need = polarization_workspace_impl(nq, K_host, nb_host, nw, precision, po);
   if ((rc = check_ws(ws_dev, ws_bytes, need))) return rc;
   DeviceCtx ctx;
   if ((rc = device_ctx(&ctx))) return rc;
   if (precision == GW_FP64)
-    return pol_fp64(nq, qs.data(), prefactor, nw, om, ws_dev, ws_bytes, stream, ctx);
-  return pol_tc(nq, qs.data(), prefactor, nw, om, precision, m_dtype == GW_R32, ws_dev, ws_bytes,
-                stream, ctx);
+    rc = pol_fp64(nq, qs.data(), prefactor, nw, om, ws_dev, ws_bytes, stream, ctx, po);
+  else
+    rc = pol_tc(nq, qs.data(), prefactor, nw, om, precision, m_dtype == GW_R32, ws_dev, ws_bytes,
+                stream, ctx, po);
+  if (options != nullptr && options->herk_launches_out != nullptr)
+    *options->herk_launches_out = po.launches;
+  return rc;
 }
 
 int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const void* const* M_dev,
@@ -208,6 +253,16 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host, const voi
                     int precision, void* ws_dev, size_t ws_bytes, gw_stream_t stream) {
   return polarization_impl(nq, K_host, nb_host, M_dev, m_dtype, delta_dev, nullptr, f_dev,
                            prefactor, nw, omega_host, P_dev, precision, ws_dev, ws_bytes, stream);
+}
+
+int gw_polarization_ex(int nq, const int64_t* K_host, const int* nb_host, const void* const* M_dev,
+                       int m_dtype, const double* const* delta_dev, const double* const* f_dev,
+                       double prefactor, int nw, const double* omega_host, double* const* P_dev,
+                       int precision, const gw_pol_options* options, void* ws_dev,
+                       size_t ws_bytes, gw_stream_t stream) {
+  return polarization_impl(nq, K_host, nb_host, M_dev, m_dtype, delta_dev, nullptr, f_dev,
+                           prefactor, nw, omega_host, P_dev, precision, ws_dev, ws_bytes, stream,
+                           options);
 }
 
 int gw_polarization_extrapolar(int nq, const int64_t* K_host, const int* nb_host,

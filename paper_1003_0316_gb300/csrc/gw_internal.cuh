@@ -84,12 +84,27 @@ struct PolQ {
   int64_t K;
   int nb;
 };
-size_t pol_fp64_workspace(int nq, const int64_t* K, const int* nb, int nw);
+// resolved execution options (defaults filled in)
+struct PolOpts {
+  bool accumulate = false;
+  int group_items_per_sm = 4;
+  int b_stages = 4;
+  int fp64_waves = 4;
+  void* const* events = nullptr;   // cudaEvent_t pairs around the HERK launches
+  int n_events = 0;
+  int launches = 0;                // out: HERK launches of the call
+};
+int resolve_pol_options(const gw_pol_options* o, PolOpts* out);
+// records the pair's start (end = false) or end event of HERK launch `idx`, if one was given
+int record_herk_event(PolOpts& o, int idx, bool end, cudaStream_t s);
+size_t pol_fp64_workspace(int nq, const int64_t* K, const int* nb, int nw, const PolOpts& o);
 int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, void* ws,
-             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
-size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision);
+             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx, PolOpts& o);
+size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision,
+                        const PolOpts& o);
 int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
-           bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx);
+           bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx,
+           PolOpts& o);
 
 // extrapolar correction (completeness term of P, extra pair coefficients of Sigma^c)
 struct ComplQ {

@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(256) k_herk_fp64(PolLaunch L, double pref, Ome
 }
 
 // Sum the K-splits of one (q, j, tile) and write the tile and its mirror.
-__global__ void __launch_bounds__(256) k_herk_reduce(PolLaunch L, const double2* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_herk_reduce(PolLaunch L, const double2* __restrict__ part,
+                                                     bool accumulate) {
   int64_t blk = blockIdx.x;  // one block per (q, tile, j)
   int q = 0;
   // item0 counts (tile, j, split); blocks count (tile, j)
@@ -203,12 +204,17 @@ __global__ void __launch_bounds__(256) k_herk_reduce(PolLaunch L, const double2*
       s.y += v.y;
     }
     if (I == J) s.y = 0.0;
+    if (accumulate) {                          // each entry is written by this thread only
+      const double2 o = P[size_t(I) * nb + J];
+      s = make_double2(o.x + s.x, o.y + s.y);
+      if (I == J) s.y = 0.0;
+    }
     P[size_t(I) * nb + J] = s;
     if (I != J) P[size_t(J) * nb + I] = make_double2(s.x, -s.y);
   }
 }
 
-static void plan_fp64(int nq, const int64_t* K, const int* nb, int nw, int sm_count,
+static void plan_fp64(int nq, const int64_t* K, const int* nb, int nw, int sm_count, int waves,
                       std::vector<int>& splits, std::vector<int64_t>& tiles) {
   splits.resize(nq);
   tiles.resize(nq);
@@ -218,14 +224,14 @@ static void plan_fp64(int nq, const int64_t* K, const int* nb, int nw, int sm_co
     tiles[q] = int64_t(T) * (T + 1) / 2;
     base += tiles[q] * nw;
   }
-  // K splits: at least four waves of CTAs (one CTA per SM: 136 registers x 256 threads) and
+  // K splits: at least `waves` (default four) waves of CTAs (one CTA per SM: 136 registers x 256 threads) and
   // whole waves as far as possible, since every CTA of a launch takes about the same time and a
   // partly filled last wave idles the rest of the GPU; at least 512 rows per split. Among the
   // split counts from the four-wave minimum to twice it, the smallest whose fill of the last
   // wave is within 1 % of the best is taken.
   const int64_t slots = std::max(1, sm_count);
   const int64_t b = std::max<int64_t>(base, 1);
-  const int64_t s_lo = std::max<int64_t>(1, (4 * slots + b - 1) / b), s_hi = 2 * s_lo;
+  const int64_t s_lo = std::max<int64_t>(1, (int64_t(waves) * slots + b - 1) / b), s_hi = 2 * s_lo;
   auto items_at = [&](int64_t sp) {
     int64_t it = 0;
     for (int q = 0; q < nq; ++q)
@@ -248,7 +254,7 @@ static void plan_fp64(int nq, const int64_t* K, const int* nb, int nw, int sm_co
     splits[q] = int(std::max<int64_t>(1, std::min<int64_t>(pick, std::max<int64_t>(1, K[q] / 512))));
 }
 
-size_t pol_fp64_workspace(int nq, const int64_t* K, const int* nb, int nw) {
+size_t pol_fp64_workspace(int nq, const int64_t* K, const int* nb, int nw, const PolOpts& o) {
   std::vector<int> splits;
   std::vector<int64_t> tiles;
   int sm = 152;
@@ -256,14 +262,14 @@ size_t pol_fp64_workspace(int nq, const int64_t* K, const int* nb, int nw) {
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
-  plan_fp64(nq, K, nb, nw, sm, splits, tiles);
+  plan_fp64(nq, K, nb, nw, sm, o.fp64_waves, splits, tiles);
   size_t ntile = 0;
   for (int q = 0; q < nq; ++q) ntile += size_t(tiles[q]) * nw * splits[q];
   return ws_round(ntile * HT * HT * sizeof(double2));
 }
 
 int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, void* ws,
-             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
+             size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx, PolOpts& o) {
   std::vector<int64_t> K(nq);
   std::vector<int> nb(nq);
   for (int q = 0; q < nq; ++q) {
@@ -272,7 +278,7 @@ int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, vo
   }
   std::vector<int> splits;
   std::vector<int64_t> tiles;
-  plan_fp64(nq, K.data(), nb.data(), nw, ctx.sm_count, splits, tiles);
+  plan_fp64(nq, K.data(), nb.data(), nw, ctx.sm_count, o.fp64_waves, splits, tiles);
   for (int q0 = 0; q0 < nq; q0 += MAXQ) {
     int n = std::min(MAXQ, nq - q0);
     PolLaunch L{};
@@ -302,11 +308,15 @@ int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, vo
     if (part * HT * HT * sizeof(double2) > ws_bytes)
       return set_error(GW_EWORKSPACE, "internal: FP64 partial buffer exceeds workspace");
     double2* pbuf = static_cast<double2*>(ws);
+    int rc = record_herk_event(o, o.launches, false, s);
+    if (rc) return rc;
     k_herk_fp64<<<unsigned(item), 256, 0, s>>>(L, pref, om, pbuf, ctx.status);
     GW_LAUNCH_CHECK("k_herk_fp64");
+    if ((rc = record_herk_event(o, o.launches, true, s))) return rc;
+    ++o.launches;
     int64_t nblk = 0;
     for (int q = 0; q < n; ++q) nblk += tiles[q0 + q] * nw;
-    k_herk_reduce<<<unsigned(nblk), 256, 0, s>>>(L, pbuf);
+    k_herk_reduce<<<unsigned(nblk), 256, 0, s>>>(L, pbuf, o.accumulate);
     GW_LAUNCH_CHECK("k_herk_reduce");
   }
   return GW_OK;

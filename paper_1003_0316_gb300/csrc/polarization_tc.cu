@@ -64,7 +64,7 @@ constexpr int TM = 128;          // real Gram rows per tile (A operand, in TMEM)
 constexpr int TN = 128;          // real Gram columns per tile (B operand, in shared memory)
 constexpr int SWB = 64;          // bytes of K per B row per chunk (64-byte swizzle)
 constexpr int SUB = 2;           // 64-byte K chunks per barrier round
-constexpr int NSB = 4;           // B stages (rounds) in shared memory
+constexpr int NSB_MAX = 6;       // B stages (rounds) in shared memory: 4 (default) or 6
 constexpr int NSA = 4;           // A slots (rounds) in TMEM: two per A set
 constexpr int NWS = 8;           // weight slots (rounds) in shared memory
 constexpr int B_TILE = TN * SWB;                 // 8 KB: one chunk's hi (or lo) tile
@@ -90,6 +90,7 @@ constexpr uint64_t WAIT_LIMIT = 2000000000ull;   // ns: 2 s per bounded wait
 static_assert(NTHREADS == 512 && REG_EPI + REG_LOW == 2 * 128, "register split");
 
 struct TcLaunch {
+  int accumulate;           // P += the tile's sum instead of P = (slices of K into one P)
   const float* xT[TQ];      // A side, chunk-major: float4 [row block][kpad / CH][CH / 4][128 rows]
   const char* bsp[TQ];      // [nbi][nch] pre-split B tiles: 8 KB hi + 8 KB lo, swizzled
   const float* s[TQ];       // [nw][kpad] |w_tj| in FP32 (zero padded)
@@ -179,7 +180,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
 
 // MODE: 0 complex polarization, 1 quadratic form (Sigma pair coefficients), 2 real
 // polarization (real projections, inversion-symmetric systems: P = -G directly).
-template <bool BF16, int MODE>
+template <bool BF16, int MODE, int NSB>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_herk_tc(const __grid_constant__ TcLaunch L, double* __restrict__ acc64, unsigned* status) {
   constexpr bool QF = MODE == 1;
@@ -558,7 +559,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int i = 0; i < TN; ++i) {
           const int J = bj * TN + i;
           if (I < nb && J < nb && I <= J) {
-            const double g = -acc[size_t(i) * TM];
+            double g = -acc[size_t(i) * TM];
+            if (L.accumulate) g += P[size_t(I) * nb + J].x;     // written by this thread only
             P[size_t(I) * nb + J] = make_double2(g, 0.0);
             if (I != J) P[size_t(J) * nb + I] = make_double2(g, 0.0);
           }
@@ -580,6 +582,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (I < nb && J < nb && I <= J) {
               double re = -(e0 + o1);
               double im = (I == J) ? 0.0 : -(o0 - e1);
+              if (L.accumulate) {               // written by this thread only
+                const double2 old = P[size_t(I) * nb + J];
+                re += old.x;
+                if (I != J) im += old.y;
+              }
               P[size_t(I) * nb + J] = make_double2(re, im);
               if (I != J) P[size_t(J) * nb + I] = make_double2(re, -im);
             }
@@ -787,7 +794,6 @@ static void q_sizes(int64_t K, int ncol, int precision, int64_t* nch, int64_t* k
 // large q run one at a time (measured faster than one launch over many large q) and small q
 // share a launch; the workspace holds one group at a time. The grouping uses the complex tile
 // count for real and complex projections alike, so the workspace query and the call agree.
-constexpr int64_t GROUP_ITEMS_PER_SM = 4;
 
 static size_t q_bytes(int64_t K, int ncol, int nw, int precision) {
   int64_t nch, kpad;
@@ -800,12 +806,12 @@ static size_t q_bytes(int64_t K, int ncol, int nw, int precision) {
 
 // first q of every group, and the end (nq)
 static void tc_groups(int nq, const int64_t* K, const int* nb, int nw, int sm,
-                      std::vector<int>& start) {
+                      int64_t items_per_sm, std::vector<int>& start) {
   start.clear();
   int64_t items = 0;
   int n = 0;
   for (int q = 0; q < nq; ++q) {
-    if (n == 0 || items >= GROUP_ITEMS_PER_SM * sm || n == TQ) {
+    if (n == 0 || items >= items_per_sm * sm || n == TQ) {
       start.push_back(q);
       items = 0;
       n = 0;
@@ -816,12 +822,13 @@ static void tc_groups(int nq, const int64_t* K, const int* nb, int nw, int sm,
   start.push_back(nq);
 }
 
-size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision) {
+size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision,
+                        const PolOpts& o) {
   int sm = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
   std::vector<int> start;
-  tc_groups(nq, K, nb, nw, sm, start);
+  tc_groups(nq, K, nb, nw, sm, o.group_items_per_sm, start);
   size_t group_max = 0;
   for (size_t g = 0; g + 1 < start.size(); ++g) {
     size_t b = 0;
@@ -831,26 +838,34 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
   return ws_round(size_t(sm) * TN * TM * sizeof(double)) + group_max;
 }
 
-template <bool BF16, int MODE>
-static int prepare_kernel(const DeviceCtx& ctx, size_t smem) {
-  return set_max_dyn_smem(reinterpret_cast<const void*>(k_herk_tc<BF16, MODE>), smem, ctx.device);
-}
+static size_t herk_smem(int nsb) { return size_t(nsb) * STAGE_BYTES + NWS * WSLOT_BYTES + 1024; }
 
-template <int MODE>
-static int launch_tc(const TcLaunch& L, bool bf, unsigned grid, size_t smem, double* acc64,
-                     cudaStream_t s, const DeviceCtx& ctx) {
-  int rc = bf ? prepare_kernel<true, MODE>(ctx, smem) : prepare_kernel<false, MODE>(ctx, smem);
+template <bool BF16, int MODE, int NSB>
+static int launch_tc_k(const TcLaunch& L, unsigned grid, double* acc64, cudaStream_t s,
+                       const DeviceCtx& ctx) {
+  const size_t smem = herk_smem(NSB);
+  int rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_herk_tc<BF16, MODE, NSB>), smem,
+                            ctx.device);
   if (rc) return rc;
-  if (bf)
-    k_herk_tc<true, MODE><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
-  else
-    k_herk_tc<false, MODE><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
+  k_herk_tc<BF16, MODE, NSB><<<grid, NTHREADS, smem, s>>>(L, acc64, ctx.status);
   GW_LAUNCH_CHECK("k_herk_tc");
   return GW_OK;
 }
 
+// the quadratic form always runs with 4 stages; the polarization with o.b_stages
+template <int MODE>
+static int launch_tc(const TcLaunch& L, bool bf, int nsb, unsigned grid, double* acc64,
+                     cudaStream_t s, const DeviceCtx& ctx) {
+  if (MODE != 1 && nsb == 6)
+    return bf ? launch_tc_k<true, MODE, 6>(L, grid, acc64, s, ctx)
+              : launch_tc_k<false, MODE, 6>(L, grid, acc64, s, ctx);
+  return bf ? launch_tc_k<true, MODE, 4>(L, grid, acc64, s, ctx)
+            : launch_tc_k<false, MODE, 4>(L, grid, acc64, s, ctx);
+}
+
 int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
-           bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx) {
+           bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx,
+           PolOpts& o) {
   const bool bf = precision == GW_BF16X3;
   const int cpb = real ? 1 : 2;          // real operand columns per basis function
   WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
@@ -864,14 +879,14 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     nbs[q] = qs[q].nb;
   }
   std::vector<int> start;
-  tc_groups(nq, Ks.data(), nbs.data(), nw, ctx.sm_count, start);
-  const size_t smem = NSB * STAGE_BYTES + NWS * WSLOT_BYTES + 1024;
+  tc_groups(nq, Ks.data(), nbs.data(), nw, ctx.sm_count, o.group_items_per_sm, start);
   for (size_t g = 0; g + 1 < start.size(); ++g) {
     const int q0 = start[g], n = start[g + 1] - start[g];
     cur.used = group_base;               // the previous group's launch is ordered before this one
     TcLaunch L{};
     L.nq = n;
     L.nw = nw;
+    L.accumulate = o.accumulate ? 1 : 0;
     int64_t item = 0;
     for (int i = 0; i < n; ++i) {
       const PolQ& Q = qs[q0 + i];
@@ -912,9 +927,13 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     L.item0[n] = item;
     if (item == 0) continue;
     unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
-    int rc = real ? launch_tc<2>(L, bf, grid, smem, acc64, s, ctx)
-                  : launch_tc<0>(L, bf, grid, smem, acc64, s, ctx);
+    int rc = record_herk_event(o, o.launches, false, s);
     if (rc) return rc;
+    rc = real ? launch_tc<2>(L, bf, o.b_stages, grid, acc64, s, ctx)
+              : launch_tc<0>(L, bf, o.b_stages, grid, acc64, s, ctx);
+    if (rc) return rc;
+    if ((rc = record_herk_event(o, o.launches, true, s))) return rc;
+    ++o.launches;
   }
   return GW_OK;
 }
@@ -993,7 +1012,6 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
       k_prep_quad<false, false><<<pg, 128, 0, s>>>(W, nb[q], nch, bsp[q], jstride);
     GW_LAUNCH_CHECK("k_prep_quad");
   }
-  const size_t smem = NSB * STAGE_BYTES + NWS * WSLOT_BYTES + 1024;
   for (int q0 = 0; q0 < nq; q0 += TQ) {
     int n = std::min(TQ, nq - q0);
     TcLaunch L{};
@@ -1020,7 +1038,7 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
     L.item0[n] = item;
     if (item == 0) continue;
     unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
-    int rc = launch_tc<1>(L, bf, grid, smem, acc64, s, ctx);
+    int rc = launch_tc<1>(L, bf, 4, grid, acc64, s, ctx);
     if (rc) return rc;
   }
   return GW_OK;

@@ -12,8 +12,8 @@
 namespace gw {
 
 static size_t pol_ws(int nq, const int64_t* K, const int* nb, int nw, int precision) {
-  return precision == GW_FP64 ? pol_fp64_workspace(nq, K, nb, nw)
-                              : pol_tc_workspace(nq, K, nb, nw, precision);
+  return precision == GW_FP64 ? pol_fp64_workspace(nq, K, nb, nw, PolOpts{})
+                              : pol_tc_workspace(nq, K, nb, nw, precision, PolOpts{});
 }
 
 int plan_waves(int nq, const int64_t* K, const int* nb, int nw, int precision, size_t budget,

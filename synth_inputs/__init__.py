@@ -225,18 +225,22 @@ class Workload:
 
 
 def _m_block(args):
-    wl, iq, r0, r1, dtype = args
-    return wl.m_rows(iq, rows=np.arange(r0, r1, dtype=np.uint64)).astype(dtype)
+    wl, iq, r0, r1, cols, dtype = args
+    return wl.m_rows(iq, rows=np.arange(r0, r1, dtype=np.uint64), cols=cols).astype(dtype)
 
 
-def m_rows_parallel(wl, iq, pool, dtype=np.complex128, block=16384):
-    """All projections M_{t,I} of q index iq (the draws of Workload.m_rows), row blocks drawn
-    by the worker processes of `pool` (a multiprocessing pool made with the "spawn" start
-    method, so that it is safe next to a CUDA context). Returns [K][N_b] in `dtype`."""
-    K = wl.K(iq)
-    jobs = [(wl, iq, r0, min(K, r0 + block), dtype) for r0 in range(0, K, block)]
+def m_rows_parallel(wl, iq, pool, dtype=np.complex128, block=16384, cols=None, rows=None):
+    """Projections M_{t,I} of q index iq (the draws of Workload.m_rows) for the rows
+    range(*rows) (default: all K) and the given columns (default: all), row blocks drawn by the
+    worker processes of `pool` (a multiprocessing pool made with the "spawn" start method, so
+    that it is safe next to a CUDA context). Returns [rows][cols] in `dtype`."""
+    r_lo, r_hi = rows if rows is not None else (0, wl.K(iq))
+    if cols is not None:
+        block = max(block, 16384 * 256 // max(1, len(cols)))   # about 4M draws per job
+    jobs = [(wl, iq, r0, min(r_hi, r0 + block), cols, dtype) for r0 in range(r_lo, r_hi, block)]
     parts = pool.map(_m_block, jobs)
-    return np.concatenate(parts) if parts else np.zeros((0, wl.nb[iq]), dtype=dtype)
+    ncol = wl.nb[iq] if cols is None else len(cols)
+    return np.concatenate(parts) if parts else np.zeros((0, ncol), dtype=dtype)
 
 
 # Sigma projections of the mesh workloads carry a factor 2^-5, so that the correlation

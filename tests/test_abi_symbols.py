@@ -101,3 +101,30 @@ def test_polarization_workspace_holds_one_group_of_large_q():
     ws8 = lib.gw_polarization_workspace(8, Ks, nbs, 16, GW_BF16X3)
     ws1 = lib.gw_polarization_workspace(1, Ks1, nbs1, 16, GW_BF16X3)
     assert ws8 > ws1
+
+
+def test_polarization_options_rejected_without_gpu():
+    """gw_polarization_ex checks its options before any device call: b_stages must be 0, 4 or
+    6, counts must not be negative, event pairs need an array (GW_EINVAL = 1)."""
+    lib = _lib()
+    lib.gw_last_error.restype = ctypes.c_char_p
+
+    class Opt(ctypes.Structure):
+        _fields_ = [("accumulate", ctypes.c_int), ("group_items_per_sm", ctypes.c_int),
+                    ("b_stages", ctypes.c_int), ("fp64_waves", ctypes.c_int),
+                    ("herk_events", ctypes.c_void_p), ("n_herk_events", ctypes.c_int),
+                    ("herk_launches_out", ctypes.c_void_p)]
+
+    K = (ctypes.c_int64 * 1)(64)
+    nb = (ctypes.c_int * 1)(8)
+    om = (ctypes.c_double * 2)(0.5, 1.0)
+    for fields, word in (({"b_stages": 5}, b"b_stages"), ({"group_items_per_sm": -1}, b"negative"),
+                         ({"n_herk_events": 2}, b"herk_events")):
+        o = Opt(**fields)
+        lib.gw_polarization_ex.restype = ctypes.c_int
+        rc = lib.gw_polarization_ex(1, K, nb, None, 1, None, None, ctypes.c_double(1.0), 2, om,
+                                    None, 2, ctypes.byref(o), None, ctypes.c_size_t(0), None)
+        assert rc == 1 and word in lib.gw_last_error(), (fields, lib.gw_last_error())
+    lib.gw_polarization_workspace_ex.restype = ctypes.c_size_t
+    assert lib.gw_polarization_workspace_ex(1, K, nb, 2, 2, ctypes.byref(Opt(b_stages=5))) == 0
+    assert lib.gw_polarization_workspace_ex(1, K, nb, 2, 2, ctypes.byref(Opt(b_stages=6))) > 0

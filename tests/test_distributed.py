@@ -88,3 +88,24 @@ def test_two_rank_sigma_matches_single_process(tmp_path):
     for r in range(world):
         got = np.load(tmp_path / f"sigma_{r}.npy")
         assert np.allclose(got, full, rtol=1e-12, atol=1e-13 * np.abs(full).max())
+
+
+def test_bench_launches_its_own_ranks():
+    """`bench.py --gpus 2` without a torchrun environment starts two ranks itself (gloo for the
+    reference arm, on the CPU) and rank 0 alone prints one line with n_gpus = 2."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    env["OMP_NUM_THREADS"] = "1"
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "0", "--oracle-kpoints", "1"],
+                       capture_output=True, text=True, timeout=600, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
+    assert d["config"]["workload"].startswith("nk64_16q")
