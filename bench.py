@@ -412,10 +412,20 @@ def e2e_measure(pipe, args, world):
     host_d = [d.cpu().pin_memory() for d in pipe.delta]
     h2d = sum(t.numel() * t.element_size() for t in host_M + host_Ms + host_d)
     steps = max(1, min(args.steps, 2))
+    copy_stream = torch.cuda.Stream()
+    # the host-to-device bandwidth of this machine for these pinned inputs (varies between boxes):
+    # the copies hide behind the polarization when it exceeds about 60 GB/s
     torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(copy_stream)
+    with torch.cuda.stream(copy_stream):
+        for dst, src in zip(pipe.M, host_M):
+            dst.copy_(src, non_blocking=True)
+    c1.record(copy_stream)
+    torch.cuda.synchronize()
+    h2d_gbs = sum(t.numel() * t.element_size() for t in host_M) / (c0.elapsed_time(c1) * 1e-3) / 1e9
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    copy_stream = torch.cuda.Stream()
     e0.record()
     d2h = 0
     for _ in range(steps):
@@ -428,7 +438,11 @@ def e2e_measure(pipe, args, world):
     ms = e0.elapsed_time(e1) / steps
     fp, fs = workload_flops(wl)
     return {"value": (fp + fs) * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms,
+            "h2d_gbs_measured": h2d_gbs,
+            "how": "projections streamed q by q from pinned host memory on a copy stream while "
+                   "the polarization of the q before runs; Sigma projections and energies too; "
+                   "fitted parameters and Sigma^c read back"}
 
 
 def fp64_sample(pipe):
@@ -742,6 +756,7 @@ def run_case_batched(args):
     not a bench line."""
     import torch
     import paper_1003_0316_gb300 as gw
+    from paper_1003_0316_gb300 import autotune
     wl = S.batched_uneven()
     om = wl.omega()
     prec = args.precision
@@ -751,13 +766,31 @@ def run_case_batched(args):
     free, _ = torch.cuda.mem_get_info()
     budget = int(free * 0.85)
     waves = gw.plan_waves(Ks, nbs, wl.nw, prec, budget)
-    # kernel attributes are set by a first, tiny call outside any capture
+    # execution options per wave from the autotuner (tuned on the wave's largest q, cached per
+    # shape bucket; the tuning time is reported apart); the precision stays the one asked for
+    tuned, tune_s = [], 0.0
+    for w in waves:
+        qbig = max(w, key=lambda q: Ks[q] * nbs[q] ** 2)
+        if args.autotune and prec != "fp64":
+            t0 = time.perf_counter()
+            e = autotune.tune(nbs[qbig], Ks[qbig], wl.nw, precisions=(prec,), bound=1e-6,
+                              cache_path=os.path.join(ROOT, "gpurun_out", "autotune.json")
+                              if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+            tune_s += time.perf_counter() - t0
+            tuned.append(e)
+        else:
+            tuned.append(None)
+    # kernel attributes are set by a first, tiny call outside any capture (with every option
+    # set a wave will use)
     tiny = S.tiny(nb=64)
-    gw.polarization([torch.as_tensor(tiny.m_full(0), dtype=cdt, device="cuda")],
-                    [torch.as_tensor(tiny.delta(0), device="cuda")], tiny.omega(), 1.0, prec)
+    for e in [None] + [e for e in tuned if e is not None]:
+        gw.polarization([torch.as_tensor(tiny.m_full(0), dtype=cdt, device="cuda")],
+                        [torch.as_tensor(tiny.delta(0), device="cuda")], tiny.omega(), 1.0, prec,
+                        options=autotune.options_of(e) if e else None)
     torch.cuda.synchronize()
     gen_ms = p_ms = 0.0
     flops = 0.0
+    gen_list = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for w in waves:
         e0.record()
@@ -767,13 +800,16 @@ def run_case_batched(args):
         gen_ms += e0.elapsed_time(e1)
         d = [torch.as_tensor(wl.delta(q), device="cuda") for q in w]
         P = [torch.empty((wl.nw, nbs[q], nbs[q]), dtype=torch.complex128, device="cuda") for q in w]
-        ws = torch.empty(gw.polarization_workspace([Ks[q] for q in w], [nbs[q] for q in w], wl.nw, prec),
+        opts = autotune.options_of(tuned[len(gen_list)]) if tuned[len(gen_list)] else None
+        gen_list.append(1)
+        ws = torch.empty(gw.polarization_workspace_ex([Ks[q] for q in w], [nbs[q] for q in w], wl.nw,
+                                                      prec, opts),
                          dtype=torch.uint8, device="cuda")
         st = torch.cuda.Stream()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.stream(st):
             with torch.cuda.graph(g, stream=st):
-                gw.polarization(M, d, om, wl.prefactor, prec, out=P, ws=ws)
+                gw.polarization(M, d, om, wl.prefactor, prec, out=P, ws=ws, options=opts)
         torch.cuda.synchronize()
         e0.record()
         g.replay()
@@ -790,7 +826,11 @@ def run_case_batched(args):
                       "q_per_wave": [len(w) for w in waves],
                       "projection_bytes": m_bytes, "generation_ms": gen_ms,
                       "polarization_ms": p_ms, "polarization_tflops": flops / (p_ms * 1e-3) / 1e12,
-                      "algorithmic_flop": flops}), flush=True)
+                      "algorithmic_flop": flops, "autotune_s": round(tune_s, 2),
+                      "tuned": [None if e is None else
+                                {k: e[k] for k in ("precision", "b_stages", "group_items_per_sm",
+                                                   "err", "cached")} for e in tuned]}),
+          flush=True)
 
 
 def run_case_extrapolar(args):
@@ -958,6 +998,8 @@ def main():
     ap.add_argument("--sigma-precision", default="tf32x3", choices=["bf16x3", "tf32x3", "fp64"],
                     help="precision of the Sigma pair coefficients (TF32x3 by default: its Sigma^c "
                          "error at the workload's sizes is 1e-6 Ha against 2e-5 Ha for BF16x3)")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="--case batched: execution options from the autotuner")
     ap.add_argument("--oracle-kpoints", type=int, default=12,
                     help="k points of the oracle's timed sample (CPU baseline and reference arm)")
     ap.add_argument("--no-sigma-check", action="store_true",

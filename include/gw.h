@@ -75,6 +75,22 @@ const char* gw_last_error(void);
 int gw_check(gw_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Transition energies of one transfer momentum q (the energy differences in the bracket of
+ * Eq. polar_MB, Sec. III.C): for t = (k N_occ + n) N_unocc + n',
+ *   Delta_t = e_unocc[kq[k]][n'] - e_occ[k][n],
+ * k = 0 .. N_k-1 the mesh points, n < N_occ, n' < N_unocc, kq[k] the mesh index of k + q.
+ *   eps_occ_dev   [N_k][ld_occ] double (energies from the Fermi level, Sec. II), ld_occ >= N_occ;
+ *   eps_unocc_dev [N_k][ld_unocc] double, ld_unocc >= N_unocc;
+ *   kq_dev        [N_k] int, each in [0, N_k);
+ *   delta_dev     [N_k N_occ N_unocc] double output (the layout of the projections' rows).
+ * Errors: GW_EINVAL for negative sizes, a leading dimension below its count or NULL pointers
+ * (nothing is launched); a kq entry outside [0, N_k) is reported by gw_check as GW_EINVAL and
+ * its transitions are set to 0 (which gw_polarization then rejects as Delta <= 0). */
+int gw_make_delta(int nk, int nocc, int nunocc, const double* eps_occ_dev, int ld_occ,
+                  const double* eps_unocc_dev, int ld_unocc, const int* kq_dev,
+                  double* delta_dev, gw_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * a1. Transition weights (bracket of Eq. polar_MB at w = i omega, Sec. III.C):
  *   w[j][t] = prefactor * f_t * ( 1/(i omega_j - Delta_t) - 1/(i omega_j + Delta_t) )
  *           = -prefactor * f_t * 2 Delta_t / (Delta_t^2 + omega_j^2).

@@ -48,6 +48,7 @@ def _sig(name, res, *args):
 _sig("gw_version", _i32)
 _sig("gw_last_error", ctypes.c_char_p)
 _sig("gw_check", _i32, _vp)
+_sig("gw_make_delta", _i32, _i32, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _vp, _vp)
 _sig("gw_transition_weights", _i32, _i64, _vp, _vp, _f64, _i32, _P(_f64), _vp, _vp)
 _sig("gw_polarization_workspace", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32)
 _sig("gw_polarization", _i32, _i32, _P(_i64), _P(_i32), _P(_vp), _i32, _P(_vp), _P(_vp), _f64,
@@ -163,6 +164,22 @@ def _dtype_code(t):
     if t.dtype == torch.float32:
         return GW_R32
     raise TypeError(f"projections must be complex128, complex64 or float32, got {t.dtype}")
+
+
+# ------------------------------------------------------- transition energies ---
+def make_delta(eps_occ, eps_unocc, kq, nunocc=None, out=None):
+    """Delta[t] = eps_unocc[kq[k]][n'] - eps_occ[k][n], t = (k N_occ + n) N_unocc + n'
+    (float64 [N_k N_occ N_unocc]); eps_occ [N_k][N_occ], eps_unocc [N_k][>= N_unocc] float64,
+    kq [N_k] int32 (mesh index of k + q), all on the device; N_unocc defaults to the width of
+    eps_unocc."""
+    nk, nocc = eps_occ.shape
+    nu = eps_unocc.shape[1] if nunocc is None else int(nunocc)
+    if out is None:
+        out = torch.empty(nk * nocc * nu, dtype=torch.float64, device=eps_occ.device)
+    _raise(_lib.gw_make_delta(nk, nocc, nu, eps_occ.data_ptr(), eps_occ.stride(0),
+                              eps_unocc.data_ptr(), eps_unocc.stride(0), kq.data_ptr(),
+                              out.data_ptr(), _stream()))
+    return out
 
 
 # ---------------------------------------------------------------- a1 --------

@@ -150,6 +150,24 @@ int gw_check(gw_stream_t stream) {
   return GW_OK;
 }
 
+int gw_make_delta(int nk, int nocc, int nunocc, const double* eps_occ_dev, int ld_occ,
+                  const double* eps_unocc_dev, int ld_unocc, const int* kq_dev,
+                  double* delta_dev, gw_stream_t stream) {
+  if (nk < 0 || nocc < 0 || nunocc < 0)
+    return set_error(GW_EINVAL, "negative size (nk=%d, nocc=%d, nunocc=%d)", nk, nocc, nunocc);
+  if (ld_occ < nocc || ld_unocc < nunocc)
+    return set_error(GW_EINVAL, "leading dimension below its count (ld_occ=%d, ld_unocc=%d)",
+                     ld_occ, ld_unocc);
+  if (int64_t(nk) * nocc * nunocc == 0) return GW_OK;
+  if (!eps_occ_dev || !eps_unocc_dev || !kq_dev || !delta_dev)
+    return set_error(GW_EINVAL, "NULL eps_occ_dev, eps_unocc_dev, kq_dev or delta_dev");
+  DeviceCtx ctx;
+  int rc = device_ctx(&ctx);
+  if (rc) return rc;
+  return launch_make_delta(nk, nocc, nunocc, eps_occ_dev, ld_occ, eps_unocc_dev, ld_unocc, kq_dev,
+                           delta_dev, stream, ctx);
+}
+
 int gw_transition_weights(int64_t K, const double* delta_dev, const double* f_dev,
                           double prefactor, int nw, const double* omega_host, double* w_dev,
                           gw_stream_t stream) {

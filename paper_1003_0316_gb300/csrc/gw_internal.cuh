@@ -70,6 +70,9 @@ struct WsCursor {
 inline size_t ws_round(size_t b) { return (b + 255) & ~size_t(255); }
 
 // ---------------------------------------------------------- launchers -------
+// transition energies of one q
+int launch_make_delta(int nk, int nocc, int nunocc, const double* eo, int ldo, const double* eu,
+                      int ldu, const int* kq, double* delta, cudaStream_t s, const DeviceCtx& ctx);
 // a1
 int launch_weights(int64_t K, const double* delta, const double* f, double pref, int nw,
                    const OmegaArr& om, double* w, cudaStream_t s, const DeviceCtx& ctx);

@@ -43,6 +43,37 @@ int launch_weights(int64_t K, const double* delta, const double* f, double pref,
   return GW_OK;
 }
 
+// Delta_t = e_unocc[kq[k]][n'] - e_occ[k][n] for t = (k nocc + n) nunocc + n'
+__global__ void k_make_delta(int nk, int nocc, int nunocc, const double* __restrict__ eo, int ldo,
+                             const double* __restrict__ eu, int ldu, const int* __restrict__ kq,
+                             double* __restrict__ delta, unsigned* status) {
+  const int64_t K = int64_t(nk) * nocc * nunocc;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < K;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int np = int(t % nunocc);
+    const int64_t kn = t / nunocc;
+    const int n = int(kn % nocc), k = int(kn / nocc);
+    const int k2 = kq[k];
+    if (k2 < 0 || k2 >= nk) {
+      raise_status(status, ST_EINVAL);
+      delta[t] = 0.0;
+      continue;
+    }
+    delta[t] = eu[size_t(k2) * ldu + np] - eo[size_t(k) * ldo + n];
+  }
+}
+
+int launch_make_delta(int nk, int nocc, int nunocc, const double* eo, int ldo, const double* eu,
+                      int ldu, const int* kq, double* delta, cudaStream_t s, const DeviceCtx& ctx) {
+  const int64_t K = int64_t(nk) * nocc * nunocc;
+  if (K == 0) return GW_OK;
+  const int64_t blocks = std::min<int64_t>((K + 255) / 256, int64_t(ctx.sm_count) * 8);
+  k_make_delta<<<unsigned(blocks), 256, 0, s>>>(nk, nocc, nunocc, eo, ldo, eu, ldu, kq, delta,
+                                                ctx.status);
+  GW_LAUNCH_CHECK("k_make_delta");
+  return GW_OK;
+}
+
 // ------------------------------------------------------------------ a2 -------
 constexpr int HT = 64;   // output tile edge
 constexpr int HKC = 8;   // rows per shared-memory chunk

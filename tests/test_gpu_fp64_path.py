@@ -348,3 +348,28 @@ def test_screened_w_large_basis_against_oracle(gw):
     ref = OS.screened_wc_all(Po, v)
     assert rel_fro(Wg, ref) <= 1e-12
     assert max_rel(Wg, ref) <= 1e-12
+
+
+def test_make_delta_matches_the_transition_layout(gw):
+    """gw_make_delta builds Delta_t from the band energies and the k+q map in the row order of
+    the projections, the same numbers as the input module's layout (the 4x4x4 mesh, two q, one
+    with fewer unoccupied bands than the energy table holds); a bad k+q index is reported."""
+    wl = S.medium_mixed()
+    eo = T(wl.eps_occ())
+    eu = T(wl.eps_unocc())
+    for iq in (0, 5):
+        kq = T(wl.kplus(np.arange(wl.nk), wl.qs[iq]).astype(np.int32))
+        d = gw.make_delta(eo, eu, kq, nunocc=wl.nunocc[iq])
+        gw.check()
+        assert np.array_equal(d.cpu().numpy(), wl.delta(iq))
+    d = gw.make_delta(eo, eu[:, :300], T(wl.kplus(np.arange(wl.nk), wl.qs[1]).astype(np.int32)))
+    gw.check()
+    ref = (wl.eps_unocc()[wl.kplus(np.arange(wl.nk), wl.qs[1])][:, None, :300]
+           - wl.eps_occ()[:, :, None]).reshape(-1)
+    assert np.array_equal(d.cpu().numpy(), ref)
+    bad = np.zeros(wl.nk, dtype=np.int32)
+    bad[3] = wl.nk
+    gw.make_delta(eo, eu, T(bad))
+    with pytest.raises(gw.GWError) as e:
+        gw.check()
+    assert e.value.code == gw.GW_EINVAL
