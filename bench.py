@@ -195,7 +195,7 @@ class Pipeline:
         self.eps = [torch.as_tensor(e, device=device) for e in eps]
         npair = [len(p) for p in ps]
         sig_cdt = torch.complex128 if precision == "fp64" else torch.complex64
-        self.Msig = [gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[i], 0, npair[i], wl.nb[i],
+        self.Msig = [gw.synth_projections(wl.seed, S.TID_MSIG, wl.msig_counter(i), 0, npair[i], wl.nb[i],
                                           dtype=sig_cdt).mul_(wl.msig_scale) for i in range(wl.nq)]
         self.nsig = len(wl.sigma_states())
         self.sign = torch.as_tensor(np.sign(wl.state_energies()), device=device)
@@ -664,7 +664,7 @@ def run_case_supercell(args):
     torch.cuda.empty_cache()
     # Sigma^c of the 16 states
     ps, eps = wl.sigma_pairs(0)
-    Ms = gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[0], 0, len(ps), nb,
+    Ms = gw.synth_projections(wl.seed, S.TID_MSIG, wl.msig_counter(0), 0, len(ps), nb,
                               dtype=torch.complex64).mul_(wl.msig_scale)
     pst = torch.as_tensor(ps, dtype=torch.int32, device=dev)
     epst = torch.as_tensor(eps, device=dev)
@@ -887,7 +887,7 @@ def run_case_extrapolar(args):
     Wc = gw.screened_w(P, [dev(wl.v(0))])[0]
     ps, eps = wl.sigma_pairs(0)
     nsig, nbnd = len(wl.sigma_states()), wl.n_pair_bands(0)
-    Msf = gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[0], 0, nsig * nbnd, nb,
+    Msf = gw.synth_projections(wl.seed, S.TID_MSIG, wl.msig_counter(0), 0, nsig * nbnd, nb,
                                dtype=torch.complex128).view(nsig, nbnd, nb)
     Sm = torch.matmul(Msf.conj().transpose(1, 2), Msf)
     pk = np.arange(len(ps))[(np.arange(len(ps)) % nbnd) < wl.nocc + nkeep]
@@ -949,7 +949,7 @@ def run_case_aux(args):
     ms_div = timed(lambda: gw.sigma_div(om, head, cbz, (4 * 10.26) ** 3, est, om, sig))
     # exchange over the 8 q
     ps, es = zip(*[wl.sigma_pairs(i) for i in range(wl.nq)])
-    Ms = [gw.synth_projections(wl.seed, S.TID_MSIG, wl.qs[i], 0, len(ps[i]), wl.nb[i],
+    Ms = [gw.synth_projections(wl.seed, S.TID_MSIG, wl.msig_counter(i), 0, len(ps[i]), wl.nb[i],
                                dtype=torch.complex64).mul_(wl.msig_scale) for i in range(wl.nq)]
     pst = [dev(p, torch.int32) for p in ps]
     eps = [dev(e) for e in es]

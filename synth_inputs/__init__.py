@@ -91,6 +91,7 @@ class Workload:
     states: tuple = None   # band indices at k0 = Gamma that get Sigma (None: all)
     nw_out: int = None     # output mesh size of Sigma (None: nw)
     msig_scale: float = 1.0  # extra factor of the Sigma projections (a power of two)
+    k0: int = 0            # mesh index of the Sigma states' k point
     extra: dict = field(default_factory=dict)
 
     @property
@@ -191,7 +192,7 @@ class Workload:
     def m_full(self, iq):
         return self.m_rows(iq)
 
-    # ---- self-energy pairs p = (state s, band n' at k0+q), k0 = Gamma --------
+    # ---- self-energy pairs p = (state s at k0, band n' at k0+q) --------------
     def sigma_states(self):
         if self.states is not None:
             return np.asarray(self.states, dtype=np.int64)
@@ -205,7 +206,7 @@ class Workload:
         q = self.qs[iq]
         ns = len(self.sigma_states())
         nbnd = self.n_pair_bands(iq)
-        kq = int(self.kplus(0, q))
+        kq = int(self.kplus(self.k0, q))
         e = np.concatenate([self.eps_occ()[kq], self.eps_unocc()[kq][: self.nunocc[iq]]])
         pair_state = np.repeat(np.arange(ns, dtype=np.int32), nbnd)
         eps_np = np.tile(e, ns)
@@ -217,11 +218,16 @@ class Workload:
         rows = np.arange(npair, dtype=np.uint64) if rows is None else np.asarray(rows, dtype=np.uint64)
         cols = np.arange(nb, dtype=np.uint64) if cols is None else np.asarray(cols, dtype=np.uint64)
         idx = rows[:, None] * np.uint64(nb) + cols[None, :]
-        z = complex_normals(self.seed, TID_MSIG, idx, self.qs[iq])
+        z = complex_normals(self.seed, TID_MSIG, idx, self.msig_counter(iq))
         return z * (self.msig_scale / (1.0 + cols.astype(np.float64)[None, :] / 16.0))
 
+    def msig_counter(self, iq):
+        """Third Philox counter word of the Sigma projections: q's mesh index, plus N_k k0 for
+        states at k0 != Gamma (k0 = 0 keeps the draws of a Gamma-only workload)."""
+        return int(self.qs[iq]) + self.nk * int(self.k0)
+
     def state_energies(self):
-        return self.eps_bands(0)[self.sigma_states()]
+        return self.eps_bands(self.k0)[self.sigma_states()]
 
 
 def _m_block(args):
@@ -262,7 +268,7 @@ def small_fp64():
 
 
 def _top_states(wl, n_occ_states, n_unocc_states):
-    e = wl.eps_bands(0)
+    e = wl.eps_bands(wl.k0)
     occ = np.argsort(e[: wl.nocc])[::-1][:n_occ_states]
     unocc = wl.nocc + np.argsort(e[wl.nocc:])[:n_unocc_states]
     return tuple(int(x) for x in np.concatenate([np.sort(occ), np.sort(unocc)]))

@@ -150,3 +150,54 @@ def test_trained_start_gain_over_plain_fit(gw):
           f"training loss {float(losses[:50].mean()):.3e} -> {float(losses[-200:].mean()):.3e}")
     assert fail <= 0.10, fail
     assert it_mlp.mean() < it_plain.mean(), (it_mlp.mean(), it_plain.mean())
+
+
+@pytest.mark.slow
+def test_trained_start_gain_on_pipeline_curves(gw, tmp_path_factory):
+    """The learned start trained and judged on Sigma^c(i w) curves the method itself produces:
+    eight runs of the 4x4x4-mesh workload (seeds 0x10030316 + 100 ..), every band at the 8 k0
+    points on the 24-node mesh, through the library's polarization, screened interaction and
+    Sigma^c (paper_1003_0316_gb300.curves); seven runs train the network, 512 curves of the
+    eighth are held out. The generation resumes from its manifest (a second call runs nothing)."""
+    from paper_1003_0316_gb300 import curves as C
+    out = str(tmp_path_factory.mktemp("pipeline_curves"))
+    seeds = [S.SEED_BASE + 100 + r for r in range(8)]
+    man = C.generate(out, seeds[:2])
+    assert [s["seed"] for s in man["shards"]] == seeds[:2]
+    man = C.generate(out, seeds)                    # resumes: runs only the six missing seeds
+    assert [s["seed"] for s in man["shards"]] == seeds
+    assert all(s["curves"] == 8 * 416 for s in man["shards"])
+    ytr, _ = C.load(out, seeds[:7])
+    yte, sg = C.load(out, seeds[7:])
+    rng = np.random.default_rng(8)
+    pick = np.sort(rng.choice(len(yte), size=512, replace=False))
+    yte, sg = yte[pick], sg[pick]
+    assert np.all(np.isfinite(ytr)) and np.all(yte.imag[:, 0] * 0 == 0)
+    w = gw.mlp_init(11)
+    losses = gw.train_mlp(dev(ytr), OM24, w, steps=3000, batch=512, lr=2e-3, seed=1)
+    gw.check()
+    Y, sign = dev(yte), dev(sg)
+    res = {}
+    for meth in ("plain", "mlp_only", "mlp"):
+        prm, cost, it, st = gw.continue_fit(Y, OM24, npole=2, sign=sign, method=meth, mlp=w)
+        gw.check()
+        res[meth] = (cost.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy())
+    c_plain, it_plain, st_plain = res["plain"]
+    c_mlp, it_mlp, st_mlp = res["mlp_only"]
+    c_comb, it_comb, _ = res["mlp"]
+    fail = float(np.mean(c_mlp > 10.0 * c_plain))
+    better = float(np.mean(c_mlp < 0.9 * c_plain))
+    print(f"\npipeline curves: {len(ytr)} training, {len(yte)} held out; training loss "
+          f"{float(losses[:50].mean()):.3e} -> {float(losses[-200:].mean()):.3e}; mean LM "
+          f"iterations plain {it_plain.mean():.1f}, learned start {it_mlp.mean():.1f}, combined "
+          f"{it_comb.mean():.1f}; median final cost plain {np.median(c_plain):.3e}, learned "
+          f"{np.median(c_mlp):.3e}, combined {np.median(c_comb):.3e}; learned start ends above "
+          f"10x the plain fit's cost on {fail:.3f}, below 0.9x on {better:.3f}; status counts "
+          f"plain {np.bincount(st_plain, minlength=3).tolist()}, learned "
+          f"{np.bincount(st_mlp, minlength=3).tolist()}")
+    assert float(losses[-200:].mean()) < float(losses[:50].mean())
+    assert np.all(c_comb <= c_plain * (1 + 1e-12))
+    # the learned start alone: fewer LM iterations on average (107 -> 42 measured) and a failure
+    # rate (final cost above 10x the plain fit's) of at most 10 % (0 measured)
+    assert it_mlp.mean() < it_plain.mean(), (it_mlp.mean(), it_plain.mean())
+    assert fail <= 0.10, fail
