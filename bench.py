@@ -696,6 +696,67 @@ def run_case_supercell(args):
         "max_abs_sigma_Ha": float(sig.abs().max())}), flush=True)
 
 
+def run_case_dielectric(args):
+    """The FP64 dielectric step alone (Eqs. dielec_MB, screen_MB): the 8 q x 16 frequencies of
+    the 4x4x4-mesh workload at N_b = 600 (complex, and real for inversion-symmetric systems), on
+    polarizations of a K = 40,960 slice of each q; and two systems of order 4096 (the supercell's
+    basis). Prints one line of timings (FP64 algorithmic rate: 4 N_b^3 real flop per complex
+    system, N_b^3 per real one), not a bench line."""
+    import torch
+    import paper_1003_0316_gb300 as gw
+    wl = S.medium_mixed()
+    dev = torch.device("cuda:0")
+    nb, nw, ks = wl.nb[0], wl.nw, 40960
+    Ps = []
+    for i in range(wl.nq):
+        M = gw.synth_projections(wl.seed, S.TID_M, wl.qs[i], 0, ks, nb, dtype=torch.complex64)
+        Ps.append(gw.polarization([M], [torch.as_tensor(wl.delta(i)[:ks], device=dev)], wl.omega(),
+                                  wl.prefactor, "bf16x3")[0])
+    v = [torch.as_tensor(wl.v(i), device=dev) for i in range(wl.nq)]
+    out = {"case": "dielectric", "N_b": nb, "systems": wl.nq * nw}
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    for real in (False, True):
+        Pin = [p.real.to(torch.complex128).contiguous() for p in Ps] if real else Ps
+        res = [torch.empty_like(p) for p in Pin]
+        wsq = gw._lib.gw_screened_w_real_workspace if real else gw._lib.gw_screened_w_workspace
+        ws = torch.empty(wsq(wl.nq, gw._arr(gw._i32, list(wl.nb)), nw), dtype=torch.uint8,
+                         device=dev)
+        for _ in range(max(1, args.warmup)):
+            gw.screened_w(Pin, v, out=res, ws=ws, real=real)
+        gw.check()
+        e0, e1 = E(), E()
+        e0.record()
+        for _ in range(args.steps):
+            gw.screened_w(Pin, v, out=res, ws=ws, real=real)
+        e1.record()
+        torch.cuda.synchronize()
+        gw.check()
+        ms = e0.elapsed_time(e1) / args.steps
+        fl = (1.0 if real else 4.0) * nb ** 3 * wl.nq * nw
+        out["real" if real else "complex"] = {"ms": ms, "fp64_tflops": fl / (ms * 1e-3) / 1e12}
+    del Ps, res, ws
+    torch.cuda.empty_cache()
+    n2 = 4096
+    M = gw.synth_projections(wl.seed, S.TID_M, 0, 0, 65536, n2, dtype=torch.complex64)
+    d = torch.as_tensor(np.random.default_rng(1).uniform(0.05, 2.5, 65536), device=dev)
+    P2 = gw.polarization([M], [d], S.omega_mesh(20)[[0, 10]], 0.25, "bf16x3")
+    del M
+    torch.cuda.empty_cache()
+    v2 = [torch.as_tensor(S.coulomb_eigenvalues(n2), device=dev)]
+    ws2 = torch.empty(gw.screened_w_workspace([n2], 2), dtype=torch.uint8, device=dev)
+    gw.screened_w(P2, v2, ws=ws2)
+    gw.check()
+    e0, e1 = E(), E()
+    e0.record()
+    gw.screened_w(P2, v2, ws=ws2)
+    e1.record()
+    torch.cuda.synchronize()
+    gw.check()
+    ms = e0.elapsed_time(e1)
+    out["nb4096_2systems"] = {"ms": ms, "fp64_tflops": 4.0 * n2 ** 3 * 2 / (ms * 1e-3) / 1e12}
+    print(json.dumps(out), flush=True)
+
+
 def run_case_fit(args):
     """Analytic continuation at the scale of 2e5 self-energy curves on 24 frequencies: the
     plain FP64 Levenberg-Marquardt fit, BF16 inference of the learned start, the fit from
@@ -1007,7 +1068,8 @@ def main():
     ap.add_argument("--real", action="store_true",
                     help="--case herk with real projections (inversion-symmetric systems)")
     ap.add_argument("--case", default=None,
-                    choices=["herk", "fit", "batched", "extrapolar", "aux", "supercell"],
+                    choices=["herk", "fit", "batched", "extrapolar", "aux", "supercell",
+                             "dielectric"],
                     help="run one profiling case instead of the bench step")
     args = ap.parse_args()
     if args.case == "herk":
@@ -1027,6 +1089,9 @@ def main():
         return
     if args.case == "supercell":
         run_case_supercell(args)
+        return
+    if args.case == "dielectric":
+        run_case_dielectric(args)
         return
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(relaunch(args))

@@ -214,8 +214,13 @@ int gw_plan_waves(int nq, const int64_t* K_host, const int* nb_host, int nw, int
  *   v_dev[q]  [N_b] double > 0 Coulomb eigenvalues,
  *   P_dev[q]  [nw][N_b][N_b] complex128 (Hermitian NSD),
  *   Wc_dev[q] [nw][N_b][N_b] complex128 output (may alias P_dev[q]).
- * A failed factorisation is reported by gw_check as GW_ENOTHPD.
- * Workspace: gw_screened_w_workspace() bytes. */
+ * The factorisation runs over many CTAs (per 32-wide panel: the diagonal block, the panel
+ * below it, the trailing update), the inverse factor by block columns, W^c by block rows.
+ * A failed factorisation (eps not positive definite, or non-finite entries) is reported by
+ * gw_check as GW_ENOTHPD (GW_ENONFINITE); the later phases still run on the half-finished
+ * factor, so Wc_dev (and P_dev where it aliases Wc_dev) is undefined after such an error.
+ * Workspace: gw_screened_w_workspace() bytes, per (q, frequency) system
+ * 16 (2 N_b^2 + 1024 ceil(N_b / 32)) bytes rounded up to 256. */
 size_t gw_screened_w_workspace(int nq, const int* nb_host, int nw);
 int gw_screened_w(int nq, const int* nb_host, int nw, const double* const* v_dev,
                   const double* const* P_dev, double* const* Wc_dev,
@@ -225,7 +230,8 @@ int gw_screened_w(int nq, const int* nb_host, int nw, const double* const* v_dev
  * Sec. II: with inversion symmetry the basis and the wave functions can be chosen real): the
  * Cholesky factor and the inverse are real (a quarter of the FP64 work), the imaginary parts of
  * P_dev are not read (taken as zero), W^c is written with zero imaginary parts. Same layouts
- * and errors as gw_screened_w. Workspace: gw_screened_w_real_workspace() bytes. */
+ * and errors as gw_screened_w. Workspace: gw_screened_w_real_workspace() bytes, per system
+ * 8 (2 N_b^2 + 1024 ceil(N_b / 32)) bytes rounded up to 256. */
 size_t gw_screened_w_real_workspace(int nq, const int* nb_host, int nw);
 int gw_screened_w_real(int nq, const int* nb_host, int nw, const double* const* v_dev,
                        const double* const* P_dev, double* const* Wc_dev,

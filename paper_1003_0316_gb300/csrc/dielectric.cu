@@ -653,7 +653,7 @@ static size_t dielectric_ws_t(int nq, const int* nb, int nw) {
   for (int q = 0; q < nq; ++q) {
     size_t n = size_t(nb[q]);
     const size_t nt = (n + DB - 1) / DB;
-    b += size_t(nw) * ws_round((2 * n * n + n * DB + nt * DB * DB) * sizeof(T));
+    b += size_t(nw) * ws_round((2 * n * n + nt * DB * DB) * sizeof(T));   // E, Z, D
   }
   return b;
 }
@@ -672,12 +672,12 @@ static int dielectric_t(int nq, const int* nb, int nw, const double* const* v,
       d.Wc = reinterpret_cast<double2*>(Wc[q]) + size_t(j) * n * n;
       d.v = v[q];
       const size_t nt = (n + DB - 1) / DB;
-      char* blk = static_cast<char*>(cur.take((2 * n * n + n * DB + nt * DB * DB) * sizeof(T)));
+      char* blk = static_cast<char*>(cur.take((2 * n * n + nt * DB * DB) * sizeof(T)));
       if (!blk) return set_error(GW_EWORKSPACE, "internal: dielectric workspace too small");
-      d.E = reinterpret_cast<T*>(blk);
-      d.Tp = d.E + n * n;
-      d.Z = d.Tp + n * DB;                    // the inverse by block columns
-      d.D = d.Z + n * n;
+      d.E = reinterpret_cast<T*>(blk);       // eps, then its Cholesky factor
+      d.Tp = nullptr;                         // (the in-CTA inverse's panel: not used here)
+      d.Z = d.E + n * n;                      // the inverse factor, by block columns
+      d.D = d.Z + n * n;                      // the inverted diagonal blocks
       d.n = int(n);
       sys.push_back(d);
     }
