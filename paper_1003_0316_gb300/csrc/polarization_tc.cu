@@ -64,7 +64,7 @@ constexpr int TM = 128;          // real Gram rows per tile (A operand, in TMEM)
 constexpr int TN = 128;          // real Gram columns per tile (B operand, in shared memory)
 constexpr int SWB = 64;          // bytes of K per B row per chunk (64-byte swizzle)
 constexpr int SUB = 2;           // 64-byte K chunks per barrier round
-constexpr int NSB_MAX = 6;       // B stages (rounds) in shared memory: 4 (default) or 6
+// B stages (rounds) in shared memory: a template parameter of the kernel, 4 (default) or 6
 constexpr int NSA = 4;           // A slots (rounds) in TMEM: two per A set
 constexpr int NWS = 8;           // weight slots (rounds) in shared memory
 constexpr int B_TILE = TN * SWB;                 // 8 KB: one chunk's hi (or lo) tile
@@ -356,9 +356,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == WPROD_WARP) {
       // ---------------------------------------------- weights: bulk copies
       // One round per weight slot: the round's SUB CH weights (SUB CH 4 bytes, 16-byte
-      // aligned). This thread runs up to NWS rounds ahead of the A sets, so it also asks L2
-      // to prefetch the round's A columns and B tiles (both contiguous, 16-byte aligned): the
-      // A sets' loads and the B copies then find them in L2 instead of waiting for DRAM.
+      // aligned). With BF16 pieces this thread also asks L2 to prefetch the A columns
+      // (contiguous, 16-byte aligned) of the round PD rounds behind the one whose weights it
+      // copies, i.e. about three rounds ahead of the A sets (it runs at most NWS ahead of them),
+      // so that their loads find the columns in L2 (measured on one q of K = 102,400: BF16x3
+      // 9.65 -> 7.84 ms; the same for TF32 pieces, or a prefetch eight rounds ahead, or of the
+      // B tiles as well, raised the DRAM reads and slowed TF32x3 down: 14.8 -> 16.7 ms).
       // The quadratic form has no weights (its operands are small and stay in L2).
       if (!QF && lane == 0) {
         uint64_t g = 0;
@@ -370,8 +373,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const float* wsrc = L.s[q] + size_t(j) * L.kpad[q];
           const char* xsrc = reinterpret_cast<const char*>(L.xT[q]) +
                              size_t(bi) * size_t(L.kpad[q] / CH) * CH4 * TM * 16;
-          const char* bsrc =
-              L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * size_t(nr * SUB) * CHUNK_BYTES;
           for (int64_t r = 0; r < nr; ++r, ++g) {
             const int ws = int(g % NWS);
             if (!tc::mbar_wait(&emptyW[ws], (uint32_t(g / NWS) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
@@ -380,8 +381,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc::mbar_arrive_expect_tx(&fullW[ws], SUB * CH * 4);
             tc::bulk_g2s(wring + ws * WSLOT_BYTES, wsrc + r * SUB * CH, SUB * CH * 4, &fullW[ws]);
-            tc::bulk_prefetch_l2(xsrc + size_t(r) * SUB * CH4 * TM * 16, SUB * CH4 * TM * 16);
-            tc::bulk_prefetch_l2(bsrc + size_t(r) * STAGE_BYTES, STAGE_BYTES);
+            if (BF16) {
+              constexpr int64_t PD = NWS - 3;
+              const uint32_t xb = SUB * CH4 * TM * 16;           // one round of A columns
+              if (r == 0)                                         // the item's first rounds
+                for (int64_t r2 = 0; r2 < PD && r2 < nr; ++r2)
+                  tc::bulk_prefetch_l2(xsrc + size_t(r2) * xb, xb);
+              if (r >= PD) tc::bulk_prefetch_l2(xsrc + size_t(r - PD) * xb, xb);
+            }
           }
         }
         if (!ok && !s_abort) {
