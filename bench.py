@@ -43,7 +43,7 @@ METRIC = "P(iω)+Σ^c GFLOP/s and % of roofline, mixed vs FP64 on GB300 at ≤1e
 # (one q of K = 409,600), from the ncu capture summarised in profiles/ (one q cut to
 # K = 102,400, scaled by K: the tile grid is the same and the traffic grows in proportion with
 # K). Valid for the kernel as profiled; None where no capture of the current kernel exists.
-HERK_TRAFFIC_BYTES = {"bf16x3": (7.054e9 + 0.847e9) * 4, "tf32x3": None}
+HERK_TRAFFIC_BYTES = {"bf16x3": (7.060e9 + 0.849e9) * 4, "tf32x3": (22.615e9 + 1.646e9) * 4}
 
 
 def workload_flops(wl):
