@@ -556,8 +556,18 @@ def run_case_herk(args):
     """Profiling case: the polarization alone on one q of the 4x4x4-mesh workload, cut to
     K = 102,400 transitions (N_b = 600, 16 frequencies; M = 0.49 GB in complex64, so every
     input is larger than L2 while the device holds about 3 GB). Prints one line of timings,
-    not a bench line."""
+    not a bench line. With --wait-profile it builds and loads the profiling library
+    (libgw_prof.so, HERK wait counters) and adds the counters of the timed launches; its times
+    are then those of the counting build."""
     import torch
+    if args.wait_profile:
+        import importlib.util
+        spec = importlib.util.spec_from_file_location(
+            "gw_build", os.path.join(ROOT, "paper_1003_0316_gb300", "_build.py"))
+        builder = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(builder)
+        builder.build(variant="prof")
+        os.environ["GW_LIBRARY"] = "prof"
     import paper_1003_0316_gb300 as gw
     wl = S.medium_mixed()
     iq, K, nb = 1, 102400, wl.nb[1]
@@ -570,23 +580,28 @@ def run_case_herk(args):
     P = [torch.empty((wl.nw, nb, nb), dtype=torch.complex128, device="cuda")]
     ws = torch.empty(gw.polarization_workspace([K], [nb], wl.nw, args.precision),
                      dtype=torch.uint8, device="cuda")
+    opts = {"b_stages": args.b_stages} if args.b_stages else None
     for _ in range(args.warmup):
-        gw.polarization([M], [d], om, wl.prefactor, args.precision, out=P, ws=ws)
+        gw.polarization([M], [d], om, wl.prefactor, args.precision, out=P, ws=ws, options=opts)
     gw.check()
+    if args.wait_profile:
+        gw.herk_wait_profile(reset=True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        gw.polarization([M], [d], om, wl.prefactor, args.precision, out=P, ws=ws)
+        gw.polarization([M], [d], om, wl.prefactor, args.precision, out=P, ws=ws, options=opts)
     e1.record()
     torch.cuda.synchronize()
     gw.check()
+    prof = gw.herk_wait_profile(reset=True) if args.wait_profile else None
     ms = e0.elapsed_time(e1) / args.steps
     # algorithmic flop: complex Hermitian 4 K N_b (N_b + 1), real symmetric K N_b (N_b + 1)
     fl = (1.0 if args.real else 4.0) * K * nb * (nb + 1) * wl.nw
     print(json.dumps({"case": "herk", "K": K, "N_b": nb, "n_omega": wl.nw,
-                      "precision": args.precision, "real_projections": bool(args.real), "ms": ms,
-                      "tflops": fl / (ms * 1e-3) / 1e12}), flush=True)
+                      "precision": args.precision, "real_projections": bool(args.real),
+                      "b_stages": args.b_stages or 4, "ms": ms,
+                      "tflops": fl / (ms * 1e-3) / 1e12, "wait_profile": prof}), flush=True)
 
 
 def run_case_supercell(args):
@@ -1065,6 +1080,11 @@ def main():
                     help="k points of the oracle's timed sample (CPU baseline and reference arm)")
     ap.add_argument("--no-sigma-check", action="store_true",
                     help="skip the oracle comparison of one q's Sigma^c after the timed region")
+    ap.add_argument("--wait-profile", action="store_true",
+                    help="--case herk: build and load the profiling library and print the "
+                         "HERK's wait counters (times are then the counting build's)")
+    ap.add_argument("--b-stages", type=int, default=0, choices=[0, 4, 6],
+                    help="--case herk: shared-memory B stages of the tensor-core kernel")
     ap.add_argument("--real", action="store_true",
                     help="--case herk with real projections (inversion-symmetric systems)")
     ap.add_argument("--case", default=None,

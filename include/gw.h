@@ -168,6 +168,27 @@ int gw_polarization_ex(int nq, const int64_t* K_host, const int* nb_host,
                        double* const* P_dev, int precision, const gw_pol_options* options,
                        void* ws_dev, size_t ws_bytes, gw_stream_t stream);
 
+/* Wait profile of the split-precision HERK (no counterpart in the paper: an instrument of the
+ * kernel design). Only a library built with GW_HERK_WAIT_PROFILE defined (the package's build
+ * script with --prof, as libgw_prof.so) counts; every other build returns GW_EUNSUPPORTED. The
+ * counters are SM cycles (clock64) of the one issuing thread of each role (lane 0 of each
+ * A-transform and epilogue warp), summed over the CTAs of every HERK launch since the last
+ * reset, on the current device, in this order:
+ *    0 A transform: total   1 waits for the round's weights   2 waits for a free A slot
+ *    3 A transform: rounds (count)
+ *    4 MMA issue: total     5 waits for the B stage   6 waits for the A slot
+ *    7 waits for the drained accumulator   8 MMA issue: rounds (count)
+ *    9 epilogue: total     10 waits for a finished accumulator   11 drains (TMEM loads + sums)
+ *   12 FP64 folds          13 epilogue: periods (count)
+ *   14 B producer: total   15 its waits for a free stage
+ *   16 weight producer: total   17 its waits for a free slot
+ * gw_herk_wait_profile synchronises the device, copies the first min(n, 18) counters to the host
+ * array `counters` (n may be 0) and, if reset != 0, zeroes them. The counting build is slower
+ * (clock reads in every loop); its times are not the library's. Errors: GW_EUNSUPPORTED,
+ * GW_EINVAL (n < 0, or counters NULL with n > 0), GW_ECUDA. */
+#define GW_HERK_WAIT_COUNTERS 18
+int gw_herk_wait_profile(unsigned long long* counters, int n, int reset);
+
 /* ---------------------------------------------------------------------------
  * Extrapolar correction of the polarization (Sec. V, the paragraph on the convergence with
  * the number of bands; the scheme of Bruneval and Gonze). The unoccupied sum of Eq. polar_MB

@@ -12,9 +12,14 @@ import os
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_PKG, "libgw.so")
+# GW_LIBRARY=prof selects the profiling build (HERK wait counters, built with --prof)
+_VARIANT = os.environ.get("GW_LIBRARY", "")
+if _VARIANT not in ("", "prof"):
+    raise ImportError(f"GW_LIBRARY={_VARIANT!r}: only 'prof' (or unset) is known")
+_LIB_PATH = os.path.join(_PKG, "libgw_prof.so" if _VARIANT == "prof" else "libgw.so")
 if not os.path.exists(_LIB_PATH):
-    raise ImportError(f"{_LIB_PATH} is not built; run `python -m paper_1003_0316_gb300._build`")
+    raise ImportError(f"{_LIB_PATH} is not built; run `python paper_1003_0316_gb300/_build.py"
+                      f"{' --prof' if _VARIANT else ''}`")
 _lib = ctypes.CDLL(_LIB_PATH)
 
 GW_OK, GW_EINVAL, GW_EWORKSPACE, GW_ECUDA, GW_ENONFINITE, GW_ENOTHPD, GW_ETIMEOUT, \
@@ -100,6 +105,7 @@ _sig("gw_plan_waves", _i32, _i32, _P(_i64), _P(_i32), _i32, _i32, _sz, _P(_i32),
 _sig("gw_selftest_bounded_wait", _i32, _f64, _vp)
 _sig("gw_qp_solve", _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("gw_synth_projections", _i32, _u64, _u32, _u32, _i64, _i64, _i32, _i32, _vp, _vp)
+_sig("gw_herk_wait_profile", _i32, _P(ctypes.c_ulonglong), _i32, _i32)
 
 
 class GWError(RuntimeError):
@@ -164,6 +170,38 @@ def _dtype_code(t):
     if t.dtype == torch.float32:
         return GW_R32
     raise TypeError(f"projections must be complex128, complex64 or float32, got {t.dtype}")
+
+
+HERK_WAIT_COUNTERS = ("a_total", "a_wait_weights", "a_wait_slot", "a_rounds",
+                      "mma_total", "mma_wait_b", "mma_wait_a", "mma_wait_acc", "mma_rounds",
+                      "epi_total", "epi_wait_acc", "epi_drain", "epi_fold", "epi_periods",
+                      "bprod_total", "bprod_wait", "wprod_total", "wprod_wait")
+
+
+def herk_wait_profile(reset=True):
+    """The split-precision HERK's wait counters (include/gw.h, gw_herk_wait_profile) as a dict
+    of cycle sums and counts, plus the fraction of each role's time spent in each wait; only
+    the profiling build (GW_LIBRARY=prof) counts, any other raises GWError(GW_EUNSUPPORTED)."""
+    n = len(HERK_WAIT_COUNTERS)
+    c = (ctypes.c_ulonglong * n)()
+    _raise(_lib.gw_herk_wait_profile(c, n, 1 if reset else 0))
+    d = dict(zip(HERK_WAIT_COUNTERS, (int(v) for v in c)))
+    frac = lambda a, b: d[a] / d[b] if d[b] else None
+    d["fractions"] = {
+        "a_wait_weights": frac("a_wait_weights", "a_total"),
+        "a_wait_slot": frac("a_wait_slot", "a_total"),
+        "mma_wait_b": frac("mma_wait_b", "mma_total"),
+        "mma_wait_a": frac("mma_wait_a", "mma_total"),
+        "mma_wait_acc": frac("mma_wait_acc", "mma_total"),
+        "epi_wait_acc": frac("epi_wait_acc", "epi_total"),
+        "epi_drain": frac("epi_drain", "epi_total"),
+        "epi_fold": frac("epi_fold", "epi_total"),
+        "bprod_wait": frac("bprod_wait", "bprod_total"),
+        "wprod_wait": frac("wprod_wait", "wprod_total")}
+    d["cycles_per_drain"] = frac("epi_drain", "epi_periods")
+    # two MMA issuers each take every other round: a CTA's time per round is half of this ratio
+    d["cycles_per_round"] = (d["mma_total"] / (2 * d["mma_rounds"])) if d["mma_rounds"] else None
+    return d
 
 
 # ------------------------------------------------------- transition energies ---

@@ -1,7 +1,13 @@
 """Build libgw.so in-tree: every csrc/*.cu compiled for sm_103a, in parallel.
 
-    python -m paper_1003_0316_gb300._build            # build if sources changed
-    python -m paper_1003_0316_gb300._build --force    # rebuild everything
+    python paper_1003_0316_gb300/_build.py            # build if sources changed
+    python paper_1003_0316_gb300/_build.py --force    # rebuild everything
+    python paper_1003_0316_gb300/_build.py --prof     # libgw_prof.so: HERK wait counters
+
+(run by path: importing the package loads the library, which may not be built yet)
+
+The profiling library (GW_HERK_WAIT_PROFILE defined, own object folder) is what the binding
+loads when GW_LIBRARY=prof is set in the environment; gw_herk_wait_profile reads its counters.
 """
 import concurrent.futures as cf
 import os
@@ -15,6 +21,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgw.so")
+VARIANTS = {None: (BUILD, LIB, []),
+            "prof": (os.path.join(PKG, "_build_prof"), os.path.join(PKG, "libgw_prof.so"),
+                     ["-DGW_HERK_WAIT_PROFILE"])}
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -41,8 +50,8 @@ def _headers():
     return hs
 
 
-def _compile(src, force, extra):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src, force, extra, objdir=BUILD):
+    obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if not force and os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj, None
@@ -53,24 +62,27 @@ def _compile(src, force, extra):
     return obj, None
 
 
-def build(force=False, verbose=False, extra=()):
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra=(), variant=None):
+    objdir, lib, vflags = VARIANTS[variant]
+    os.makedirs(objdir, exist_ok=True)
     srcs = _sources()
+    flags = vflags + list(extra)
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        res = list(ex.map(lambda s: _compile(s, force, list(extra)), srcs))
+        res = list(ex.map(lambda s: _compile(s, force, flags, objdir), srcs))
     errs = [e for _, e in res if e]
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
     objs = [o for o, _ in res]
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcuda"]
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", lib] + objs + ["-lcuda"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
     if verbose:
-        print(LIB)
-    return LIB
+        print(lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True,
+          variant="prof" if "--prof" in sys.argv else None)

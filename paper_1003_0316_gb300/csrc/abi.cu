@@ -150,6 +150,10 @@ int gw_check(gw_stream_t stream) {
   return GW_OK;
 }
 
+int gw_herk_wait_profile(unsigned long long* counters, int n, int reset) {
+  return herk_wait_profile(counters, n, reset);
+}
+
 int gw_make_delta(int nk, int nocc, int nunocc, const double* eps_occ_dev, int ld_occ,
                   const double* eps_unocc_dev, int ld_unocc, const int* kq_dev,
                   double* delta_dev, gw_stream_t stream) {

@@ -105,6 +105,8 @@ int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, vo
              size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx, PolOpts& o);
 size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision,
                         const PolOpts& o);
+// the HERK wait counters of a profiling build (GW_EUNSUPPORTED otherwise)
+int herk_wait_profile(unsigned long long* counters, int n, int reset);
 int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
            bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx,
            PolOpts& o);

@@ -89,6 +89,32 @@ constexpr int TQ = 64;
 constexpr uint64_t WAIT_LIMIT = 2000000000ull;   // ns: 2 s per bounded wait
 static_assert(NTHREADS == 512 && REG_EPI + REG_LOW == 2 * 128, "register split");
 
+// Wait profile, compiled in only with GW_HERK_WAIT_PROFILE defined: the SM cycles (clock64)
+// that the issuing thread of each role spends in its barrier waits, in its drain and fold work
+// and in total, summed over the CTAs into g_herk_prof (the order of include/gw.h's
+// GW_HERK_WAIT_COUNTERS); in a normal build every counter is dead code.
+#ifdef GW_HERK_WAIT_PROFILE
+constexpr bool kWaitProfile = true;
+#else
+constexpr bool kWaitProfile = false;
+#endif
+enum HerkProf {
+  HP_A_TOTAL, HP_A_WAIT_W, HP_A_WAIT_SLOT, HP_A_ROUNDS,
+  HP_MMA_TOTAL, HP_MMA_WAIT_B, HP_MMA_WAIT_A, HP_MMA_WAIT_ACC, HP_MMA_ROUNDS,
+  HP_EPI_TOTAL, HP_EPI_WAIT_ACC, HP_EPI_DRAIN, HP_EPI_FOLD, HP_EPI_PERIODS,
+  HP_BP_TOTAL, HP_BP_WAIT, HP_WP_TOTAL, HP_WP_WAIT, HP_N
+};
+static_assert(HP_N == GW_HERK_WAIT_COUNTERS, "counter list of include/gw.h");
+__device__ unsigned long long g_herk_prof[HP_N];
+
+__device__ __forceinline__ uint64_t hp_now() {
+  if constexpr (kWaitProfile) return clock64();
+  return 0;
+}
+__device__ __forceinline__ void hp_flush(int i, uint64_t v) {
+  if constexpr (kWaitProfile) atomicAdd(&g_herk_prof[i], static_cast<unsigned long long>(v));
+}
+
 struct TcLaunch {
   int accumulate;           // P += the tile's sum instead of P = (slices of K into one P)
   const float* xT[TQ];      // A side, chunk-major: float4 [row block][kpad / CH][CH / 4][128 rows]
@@ -161,6 +187,25 @@ __device__ __forceinline__ void split_words(const float* y, uint32_t* hi, uint32
       hi[i] = h;
       lo[i] = tc::cvt_bf16x2(y[2 * i] - h0, y[2 * i + 1] - h1);
     }
+  }
+}
+
+// TF32 pieces of packed pairs of values (pair i = values 2i, 2i + 1, low word first), the
+// subtraction of the hi pieces by paired instructions: the same pieces as split_words<false>
+// with fewer instructions (measured: TF32x3 polarization 14.7 -> 13.9 ms on one q of
+// K = 102,400; the same for BF16 pieces brought nothing).
+__device__ __forceinline__ void split_pairs_tf32(const uint64_t* yp, uint32_t* hi, uint32_t* lo,
+                                                 int nwords) {
+  for (int i = 0; i < nwords / 2; ++i) {
+    float y0, y1;
+    tc::f2_unpack(yp[i], y0, y1);
+    const uint32_t h0 = tf32_rna(y0), h1 = tf32_rna(y1);
+    float r0, r1;
+    tc::f2_unpack(tc::f2_sub(yp[i], tc::f2_pack(h0, h1)), r0, r1);
+    hi[2 * i] = h0;
+    hi[2 * i + 1] = h1;
+    lo[2 * i] = tf32_rna(r0);
+    lo[2 * i + 1] = tf32_rna(r1);
   }
 }
 
@@ -242,6 +287,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int m = qd * 32 + lane;
     uint64_t g0 = 0;                  // rounds of the previous items
     bool stop = false;
+    const uint64_t hp0 = hp_now();
+    uint64_t hp_ww = 0, hp_ws = 0, hp_n = 0;
     for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       int q, j, bi, bj;
       decode_item<QF>(L, item, q, j, bi, bj);
@@ -264,30 +311,55 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int u = int(k % SUB);
         const uint64_t gg = g0 + uint64_t(r_first + 2 * (k / SUB));
         const int slot = int(gg % NSA), ws = int(gg % NWS);
+        uint64_t t = hp_now();
         if (!QF && u == 0 && !warp_wait(&fullW[ws], uint32_t(gg / NWS) & 1, &s_abort, status))
           return false;
+        hp_ww += hp_now() - t;
         const float4* sw = reinterpret_cast<const float4*>(wring + ws * WSLOT_BYTES) + u * CH4;
         uint32_t hw[2][8], lw[2][8];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {               // halves of the chunk: 8 TMEM words each
-          float y[CH / 2];
+          if constexpr (BF16) {
+            float y[CH / 2];
 #pragma unroll
-          for (int e = 0; e < CH4 / 2; ++e) {
-            const float4 xv = xr[h * (CH4 / 2) + e];
-            const float4 wv = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : sw[h * (CH4 / 2) + e];
-            y[4 * e + 0] = wv.x * xv.x;
-            y[4 * e + 1] = wv.y * xv.y;
-            y[4 * e + 2] = wv.z * xv.z;
-            y[4 * e + 3] = wv.w * xv.w;
+            for (int e = 0; e < CH4 / 2; ++e) {
+              const float4 xv = xr[h * (CH4 / 2) + e];
+              const float4 wv = QF ? make_float4(1.f, 1.f, 1.f, 1.f) : sw[h * (CH4 / 2) + e];
+              y[4 * e + 0] = wv.x * xv.x;
+              y[4 * e + 1] = wv.y * xv.y;
+              y[4 * e + 2] = wv.z * xv.z;
+              y[4 * e + 3] = wv.w * xv.w;
+            }
+            split_words<true>(y, hw[h], lw[h], 8);
+          } else {                                  // scaled values in packed pairs
+            uint64_t yp[CH / 4];
+#pragma unroll
+            for (int e = 0; e < CH4 / 2; ++e) {
+              const float4 xv = xr[h * (CH4 / 2) + e];
+              const uint64_t x01 = tc::f2_pack(__float_as_uint(xv.x), __float_as_uint(xv.y));
+              const uint64_t x23 = tc::f2_pack(__float_as_uint(xv.z), __float_as_uint(xv.w));
+              if (QF) {
+                yp[2 * e] = x01;
+                yp[2 * e + 1] = x23;
+              } else {
+                const float4 wv = sw[h * (CH4 / 2) + e];
+                yp[2 * e] = tc::f2_mul(tc::f2_pack(__float_as_uint(wv.x), __float_as_uint(wv.y)), x01);
+                yp[2 * e + 1] =
+                    tc::f2_mul(tc::f2_pack(__float_as_uint(wv.z), __float_as_uint(wv.w)), x23);
+              }
+            }
+            split_pairs_tf32(yp, hw[h], lw[h], 8);
           }
-          split_words<BF16>(y, hw[h], lw[h], 8);
         }
         if (!QF && u == SUB - 1) {                  // this warp is done with the weights
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&emptyW[ws]);
         }
+        t = hp_now();
         if (u == 0 && !warp_wait(&emptyA[slot], (uint32_t(gg / NSA) & 1) ^ 1, &s_abort, status))
           return false;
+        hp_ws += hp_now() - t;
+        hp_n += u == 0;
         const uint32_t base = tmem + (uint32_t(qd * 32) << 16) + A_COL + slot * (SUB * 32) + u * 32;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -322,6 +394,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       g0 += uint64_t(nr);
     }
+    if (kWaitProfile && lane == 0) {
+      hp_flush(HP_A_TOTAL, hp_now() - hp0);
+      hp_flush(HP_A_WAIT_W, hp_ww);
+      hp_flush(HP_A_WAIT_SLOT, hp_ws);
+      hp_flush(HP_A_ROUNDS, hp_n);
+    }
   } else if (warp < EPI_WARP0) {
     tc::setmaxnreg_dec<REG_LOW>();
     if (warp == PROD_WARP) {
@@ -330,6 +408,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0) {
         uint64_t g = 0;
         bool ok = true;
+        const uint64_t hp0 = hp_now();
+        uint64_t hp_w = 0;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
           int q, j, bi, bj;
           decode_item<QF>(L, item, q, j, bi, bj);
@@ -338,10 +418,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * size_t(nr * SUB) * CHUNK_BYTES;
           for (int64_t r = 0; r < nr; ++r, ++g) {
             const int st = int(g % NSB);
+            const uint64_t t = hp_now();
             if (!tc::mbar_wait(&emptyB[st], (uint32_t(g / NSB) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
               ok = false;
               break;
             }
+            hp_w += hp_now() - t;
             char* dst = ring + st * STAGE_BYTES;
             tc::mbar_arrive_expect_tx(&fullB[st], STAGE_BYTES);
             tc::bulk_g2s(dst, src + size_t(r) * STAGE_BYTES, STAGE_BYTES, &fullB[st]);
@@ -350,6 +432,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!ok && !s_abort) {
           s_abort = 1;
           raise_status(status, ST_ETIMEOUT);
+        }
+        if (kWaitProfile) {
+          hp_flush(HP_BP_TOTAL, hp_now() - hp0);
+          hp_flush(HP_BP_WAIT, hp_w);
         }
       }
       __syncwarp();
@@ -366,6 +452,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!QF && lane == 0) {
         uint64_t g = 0;
         bool ok = true;
+        const uint64_t hp0 = hp_now();
+        uint64_t hp_w = 0;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
           int q, j, bi, bj;
           decode_item<QF>(L, item, q, j, bi, bj);
@@ -375,10 +463,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                              size_t(bi) * size_t(L.kpad[q] / CH) * CH4 * TM * 16;
           for (int64_t r = 0; r < nr; ++r, ++g) {
             const int ws = int(g % NWS);
+            const uint64_t t = hp_now();
             if (!tc::mbar_wait(&emptyW[ws], (uint32_t(g / NWS) & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
               ok = false;
               break;
             }
+            hp_w += hp_now() - t;
             tc::mbar_arrive_expect_tx(&fullW[ws], SUB * CH * 4);
             tc::bulk_g2s(wring + ws * WSLOT_BYTES, wsrc + r * SUB * CH, SUB * CH * 4, &fullW[ws]);
             if (BF16) {
@@ -395,6 +485,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           s_abort = 1;
           raise_status(status, ST_ETIMEOUT);
         }
+        if (kWaitProfile) {
+          hp_flush(HP_WP_TOTAL, hp_now() - hp0);
+          hp_flush(HP_WP_WAIT, hp_w);
+        }
       }
       __syncwarp();
     } else {
@@ -410,6 +504,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint64_t desc0 = tc::smem_desc(tc::smem_u32(ring), 512, 4);
         const uint32_t d = tmem + ACC_COL + mpar * TN;
         bool ok = true;
+        const uint64_t hp0 = hp_now();
+        uint64_t hp_wb = 0, hp_wa = 0, hp_wc = 0, hp_n = 0;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
           int q, j, bi, bj;
           decode_item<QF>(L, item, q, j, bi, bj);
@@ -422,12 +518,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const bool pstart = i % PL == 0, pend = i % PL == PL - 1 || i == nown - 1;
             const uint64_t gg = g + uint64_t(r);
             const int st = int(gg % NSB), slot = int(gg % NSA);
-            if (!tc::mbar_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, WAIT_LIMIT) ||
-                !tc::mbar_wait(&fullA[slot], uint32_t(gg / NSA) & 1, &s_abort, WAIT_LIMIT) ||
-                (pstart && !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT))) {
+            const uint64_t t0 = hp_now();
+            if (!tc::mbar_wait(&fullB[st], uint32_t(gg / NSB) & 1, &s_abort, WAIT_LIMIT)) {
               ok = false;
               break;
             }
+            const uint64_t t1 = hp_now();
+            if (!tc::mbar_wait(&fullA[slot], uint32_t(gg / NSA) & 1, &s_abort, WAIT_LIMIT)) {
+              ok = false;
+              break;
+            }
+            const uint64_t t2 = hp_now();
+            if (pstart && !tc::mbar_wait(&acce_bar[mpar], (kb & 1) ^ 1, &s_abort, WAIT_LIMIT)) {
+              ok = false;
+              break;
+            }
+            hp_wb += t1 - t0;
+            hp_wa += t2 - t1;
+            hp_wc += hp_now() - t2;
+            ++hp_n;
             tc::tc_fence_after();
             const uint32_t a0 = tmem + A_COL + slot * (SUB * 32);
             // descriptor address field is (addr >> 4): advancing the address adds to the low bits
@@ -464,6 +573,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           s_abort = 1;
           raise_status(status, ST_ETIMEOUT);
         }
+        if (kWaitProfile) {
+          hp_flush(HP_MMA_TOTAL, hp_now() - hp0);
+          hp_flush(HP_MMA_WAIT_B, hp_wb);
+          hp_flush(HP_MMA_WAIT_A, hp_wa);
+          hp_flush(HP_MMA_WAIT_ACC, hp_wc);
+          hp_flush(HP_MMA_ROUNDS, hp_n);
+        }
         tc::mma_commit(&done_bar[mpar]);
         int never = 0;
         tc::mbar_wait(&done_bar[mpar], 0, reinterpret_cast<volatile int*>(&never), WAIT_LIMIT);
@@ -484,6 +600,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t gp = 0;                // periods drained in total (flush schedule)
     uint64_t g0 = 0;                // rounds of the previous items
     bool stop = false;
+    const uint64_t hp0 = hp_now();
+    uint64_t hp_wc = 0, hp_dr = 0, hp_fo = 0, hp_n = 0;
     float rs[TN];
     // the conversions go through volatile asm so that they stay next to their reductions
     // (converted all at once, 128 doubles would not fit beside the running sums)
@@ -513,10 +631,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int64_t k = 0; k < np0 + np1; ++k, ++gp) {
         const int buf = (k & 1) ? buf0 ^ 1 : buf0;
         const uint32_t kbb = buf ? kb1 : kb0;
+        const uint64_t t0 = hp_now();
         if (!warp_wait(&accf_bar[buf], kbb & 1, &s_abort, status)) {
           stop = true;
           break;
         }
+        const uint64_t t1 = hp_now();
+        hp_wc += t1 - t0;
         if (buf) ++kb1; else ++kb0;
         tc::tc_fence_after();
         const uint32_t src = lane_base + ACC_COL + buf * TN;
@@ -536,9 +657,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
+        const uint64_t t2 = hp_now();
+        hp_dr += t2 - t1;
+        ++hp_n;
         if (int((gp + qd * (FLUSH / 4)) % FLUSH) == FLUSH - 1) {
           fold();
           sum_empty = true;
+          hp_fo += hp_now() - t2;
         }
       }
       if (stop) break;
@@ -600,6 +725,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       }
+    }
+    if (kWaitProfile && lane == 0) {
+      hp_flush(HP_EPI_TOTAL, hp_now() - hp0);
+      hp_flush(HP_EPI_WAIT_ACC, hp_wc);
+      hp_flush(HP_EPI_DRAIN, hp_dr);
+      hp_flush(HP_EPI_FOLD, hp_fo);
+      hp_flush(HP_EPI_PERIODS, hp_n);
     }
   }
 
@@ -1047,6 +1179,22 @@ int quad_tc(int nq, const int64_t* npair, const int* nb, const void* const* Msig
     unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
     int rc = launch_tc<1>(L, bf, 4, grid, acc64, s, ctx);
     if (rc) return rc;
+  }
+  return GW_OK;
+}
+
+int herk_wait_profile(unsigned long long* counters, int n, int reset) {
+  if (!kWaitProfile)
+    return set_error(GW_EUNSUPPORTED, "the library was built without GW_HERK_WAIT_PROFILE");
+  if (n < 0 || (n > 0 && !counters))
+    return set_error(GW_EINVAL, "n=%d with counters=%p", n, static_cast<void*>(counters));
+  GW_CUDA_TRY(cudaDeviceSynchronize());
+  if (n > 0)
+    GW_CUDA_TRY(cudaMemcpyFromSymbol(counters, g_herk_prof,
+                                     sizeof(unsigned long long) * std::min(n, int(HP_N))));
+  if (reset) {
+    const unsigned long long zero[HP_N] = {};
+    GW_CUDA_TRY(cudaMemcpyToSymbol(g_herk_prof, zero, sizeof(zero)));
   }
   return GW_OK;
 }
