@@ -604,6 +604,19 @@ def run_case_herk(args):
                       "tflops": fl / (ms * 1e-3) / 1e12, "wait_profile": prof}), flush=True)
 
 
+def run_case_mma_issue(args):
+    """Profiling case: SM cycles per 128 x 128 x 16 MMA of the HERK's tcgen05.mma sequence
+    (gw_probe_mma_issue) alone and beside warps of independent FMA chains. Prints one line."""
+    import torch
+    import paper_1003_0316_gb300 as gw
+    torch.cuda.init()
+    gw.probe_mma_issue(0, 50)                    # kernel attributes, clocks up
+    out = {name: round(gw.probe_mma_issue(v, 500), 1) for v, name in enumerate(gw.MMA_ISSUE_VARIANTS)}
+    gw.check()
+    print(json.dumps({"case": "mma-issue", "unit": "SM cycles per 128x128x16 BF16 MMA (64 = pipe rate)",
+                      "rounds": 500, "cycles_per_mma": out}), flush=True)
+
+
 def run_case_supercell(args):
     """The supercell-shaped workload at full size: one q, N_k = 8, N_MPB = 4096, 256 occupied /
     3000 unoccupied bands (K = 6,144,000 transitions), 20 frequencies, 16 Sigma states x 3256
@@ -1089,7 +1102,7 @@ def main():
                     help="--case herk with real projections (inversion-symmetric systems)")
     ap.add_argument("--case", default=None,
                     choices=["herk", "fit", "batched", "extrapolar", "aux", "supercell",
-                             "dielectric"],
+                             "dielectric", "mma-issue"],
                     help="run one profiling case instead of the bench step")
     args = ap.parse_args()
     if args.case == "herk":
@@ -1112,6 +1125,9 @@ def main():
         return
     if args.case == "dielectric":
         run_case_dielectric(args)
+        return
+    if args.case == "mma-issue":
+        run_case_mma_issue(args)
         return
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(relaunch(args))

@@ -460,6 +460,19 @@ int gw_mlp_train_step(int n, const double* omega_host, const double* sigma_dev,
  * usable. For testing the timeout path without hanging the GPU. */
 int gw_selftest_bounded_wait(double limit_ms, gw_stream_t stream);
 
+/* Diagnostic (no counterpart in the paper): the issue rate of the split-precision HERK's
+ * tcgen05.mma sequence (rounds of 12 MMAs of 128 x 128 x 16 BF16, A from TMEM, B from a
+ * 64-byte-swizzled shared-memory ring, 3 commits per round) in one CTA per SM, on random
+ * operands, alone or beside warps of independent FMA chains (warp w runs on SM sub-partition
+ * w mod 4). variant: 0 issuer alone; 1 a branch on a shared-memory value before each round;
+ * 2 three FMA warps on the issuer's sub-partition; 3 three FMA warps on the other three;
+ * 4 as 2 with MMAs of 128 x 256 x 16; 5 two issuers on two sub-partitions, concurrent, three
+ * FMA warps beside each. rounds: 2 .. 100000. Writes (host) the average SM cycles per
+ * 128 x 128 x 16 MMA (64 = the tensor pipe's rate) and synchronises the stream. Allocates
+ * and frees 16 bytes of device memory. Errors: GW_EINVAL, GW_ECUDA; a bounded wait that
+ * expired is reported by gw_check as GW_ETIMEOUT. */
+int gw_probe_mma_issue(int variant, int rounds, double* cycles_per_mma_host, gw_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Synthetic-input generator (not part of the method): fills projections with
  * complex normals (Philox4x32-10 keyed by seed, counter (element index, q, tid),

@@ -106,6 +106,7 @@ _sig("gw_selftest_bounded_wait", _i32, _f64, _vp)
 _sig("gw_qp_solve", _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("gw_synth_projections", _i32, _u64, _u32, _u32, _i64, _i64, _i32, _i32, _vp, _vp)
 _sig("gw_herk_wait_profile", _i32, _P(ctypes.c_ulonglong), _i32, _i32)
+_sig("gw_probe_mma_issue", _i32, _i32, _i32, _P(_f64), _vp)
 
 
 class GWError(RuntimeError):
@@ -170,6 +171,21 @@ def _dtype_code(t):
     if t.dtype == torch.float32:
         return GW_R32
     raise TypeError(f"projections must be complex128, complex64 or float32, got {t.dtype}")
+
+
+MMA_ISSUE_VARIANTS = ("issuer alone", "branch on a shared value before each round",
+                      "3 FMA warps on the issuer's sub-partition",
+                      "3 FMA warps on the other sub-partitions",
+                      "3 FMA warps on the issuer's sub-partition, 128 x 256 x 16 MMAs",
+                      "2 concurrent issuers, 3 FMA warps beside each")
+
+
+def probe_mma_issue(variant, rounds=500):
+    """SM cycles per 128 x 128 x 16 MMA of the HERK's MMA sequence under load (include/gw.h,
+    gw_probe_mma_issue); variant indexes MMA_ISSUE_VARIANTS."""
+    out = _f64(0.0)
+    _raise(_lib.gw_probe_mma_issue(int(variant), int(rounds), ctypes.byref(out), _stream()))
+    return out.value
 
 
 HERK_WAIT_COUNTERS = ("a_total", "a_wait_weights", "a_wait_slot", "a_rounds",

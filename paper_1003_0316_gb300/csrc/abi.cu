@@ -735,6 +735,16 @@ int gw_selftest_bounded_wait(double limit_ms, gw_stream_t stream) {
   return selftest_bounded_wait(limit_ms, stream, ctx);
 }
 
+int gw_probe_mma_issue(int variant, int rounds, double* cycles_per_mma_host, gw_stream_t stream) {
+  if (variant < 0 || variant > 5) return set_error(GW_EINVAL, "variant=%d not in 0..5", variant);
+  if (rounds < 2 || rounds > 100000) return set_error(GW_EINVAL, "rounds=%d not in 2..100000", rounds);
+  if (!cycles_per_mma_host) return set_error(GW_EINVAL, "NULL cycles_per_mma_host");
+  DeviceCtx ctx;
+  int rc = device_ctx(&ctx);
+  if (rc) return rc;
+  return probe_mma_issue(variant, rounds, cycles_per_mma_host, stream, ctx);
+}
+
 }  // extern "C"
 
 extern "C" {

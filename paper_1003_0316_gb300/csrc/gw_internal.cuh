@@ -164,6 +164,8 @@ int qp_solve(int n, int npole, const double* params, const double* eps, const do
 
 // diagnostic of the bounded waits
 int selftest_bounded_wait(double limit_ms, cudaStream_t s, const DeviceCtx& ctx);
+int probe_mma_issue(int variant, int rounds, double* cycles_per_mma, cudaStream_t s,
+                    const DeviceCtx& ctx);
 
 // memory waves
 int plan_waves(int nq, const int64_t* K, const int* nb, int nw, int precision, size_t budget,

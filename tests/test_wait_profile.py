@@ -1,6 +1,8 @@
 """The HERK wait counters (gw_herk_wait_profile): the normal library refuses them without a GPU
 call, the counter list of the binding is the header's, and on a GPU the profiling build counts
-every role of a small split-precision polarization while still computing it correctly."""
+every role of a small split-precision polarization while still computing it correctly. The MMA
+issue probe (gw_probe_mma_issue) checks its arguments before any device call and, on a GPU,
+reports rates no faster than the tensor pipe."""
 import ctypes
 import json
 import os
@@ -40,6 +42,26 @@ def test_normal_build_refuses_without_device_call():
     c = (ctypes.c_ulonglong * 18)()
     assert lib.gw_herk_wait_profile(c, 18, 1) == 8          # GW_EUNSUPPORTED
     assert b"GW_HERK_WAIT_PROFILE" in lib.gw_last_error()
+
+
+def test_mma_probe_rejects_bad_arguments_without_gpu():
+    lib = ctypes.CDLL(_builder().build())
+    lib.gw_probe_mma_issue.restype = ctypes.c_int
+    out = ctypes.c_double(0.0)
+    assert lib.gw_probe_mma_issue(6, 100, ctypes.byref(out), None) == 1
+    assert lib.gw_probe_mma_issue(0, 1, ctypes.byref(out), None) == 1
+    assert lib.gw_probe_mma_issue(0, 100, None, None) == 1
+
+
+@pytest.mark.gpu
+def test_mma_probe_rates():
+    import paper_1003_0316_gb300 as gw
+    alone = gw.probe_mma_issue(0, 200)
+    rates = [gw.probe_mma_issue(v, 200) for v in range(len(gw.MMA_ISSUE_VARIANTS))]
+    gw.check()
+    # 64 cycles per MMA is the pipe's rate (8192 flop per cycle and SM); nothing runs faster
+    assert 58.0 <= alone <= 80.0, alone
+    assert all(58.0 <= r < 5000.0 for r in rates), rates
 
 
 _CHILD = r"""
