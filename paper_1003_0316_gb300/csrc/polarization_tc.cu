@@ -128,16 +128,30 @@ struct TcLaunch {
   int64_t kpad[TQ];
   int nb[TQ];
   int nbi[TQ];
-  int nbj[TQ];
+  int nbj[TQ];              // B column blocks (three-product layout: N_b blocks nbb)
   int ntile[TQ];
+  int prod3[TQ];            // complex polarization in three real products (see k_prep_tc3)
+  double* g3[TQ];           // their tiles: [nw][C, S][col][row], 128 nbj rows and columns
   int64_t item0[TQ + 1];
   int nq;
   int nw;
 };
 
+// Work item -> q, frequency j, A block bi and B block bj (data blocks of the chunk-major copy
+// and of the pre-split tiles) and the tile kind: 0 an upper tile of the real Gram matrix of
+// the interleaved projections (or of the real ones), 1 a tile of C = Mr^T diag(s) Mi, 2 an
+// upper tile of S = (Mr + Mi)^T diag(s) (Mr + Mi) (three-product layout), 3 a tile of the
+// quadratic form.
+// the q of a work item only
+__device__ __forceinline__ int item_q(const TcLaunch& L, int64_t item) {
+  int q = 0;
+  while (q + 1 < L.nq && item >= L.item0[q + 1]) ++q;
+  return q;
+}
+
 template <bool QF>
 __device__ __forceinline__ void decode_item(const TcLaunch& L, int64_t item, int& q, int& j,
-                                            int& bi, int& bj) {
+                                            int& bi, int& bj, int& kind) {
   q = 0;
   while (q + 1 < L.nq && item >= L.item0[q + 1]) ++q;
   int64_t loc = item - L.item0[q];
@@ -146,14 +160,30 @@ __device__ __forceinline__ void decode_item(const TcLaunch& L, int64_t item, int
   if (QF) {             // full rectangular grid; consecutive items share the B column block
     bi = u % L.nbi[q];
     bj = u / L.nbi[q];
+    kind = 3;
     return;
+  }
+  int off = 0;
+  kind = 0;
+  if (L.prod3[q]) {
+    const int nbb = L.nbj[q];
+    if (u < nbb * nbb) {  // C: every tile; consecutive items share the B column block
+      bi = u % nbb;
+      bj = u / nbb;
+      kind = 1;
+      return;
+    }
+    u -= nbb * nbb;
+    off = nbb;
+    kind = 2;
   }
   bj = 0;
   while (u > bj) {      // upper tiles bi <= bj, column by column
     u -= bj + 1;
     ++bj;
   }
-  bi = u;
+  bi = u + off;
+  bj += off;
 }
 
 // byte offset of (row n, 16-byte chunk kc) in a K-major, 64-byte-swizzled tile
@@ -290,8 +320,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint64_t hp0 = hp_now();
     uint64_t hp_ww = 0, hp_ws = 0, hp_n = 0;
     for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
-      int q, j, bi, bj;
-      decode_item<QF>(L, item, q, j, bi, bj);
+      int q, j, bi, bj, kind;
+      decode_item<QF>(L, item, q, j, bi, bj, kind);
       const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
       const float4* __restrict__ xc = reinterpret_cast<const float4*>(L.xT[q]) +
                                       size_t(bi) * size_t(L.kpad[q] / CH) * CH4 * TM + m;
@@ -411,8 +441,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint64_t hp0 = hp_now();
         uint64_t hp_w = 0;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-          int q, j, bi, bj;
-          decode_item<QF>(L, item, q, j, bi, bj);
+          int q, j, bi, bj, kind;
+          decode_item<QF>(L, item, q, j, bi, bj, kind);
           const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
           const char* src =
               L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * size_t(nr * SUB) * CHUNK_BYTES;
@@ -455,8 +485,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint64_t hp0 = hp_now();
         uint64_t hp_w = 0;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-          int q, j, bi, bj;
-          decode_item<QF>(L, item, q, j, bi, bj);
+          int q, j, bi, bj, kind;
+          decode_item<QF>(L, item, q, j, bi, bj, kind);
           const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
           const float* wsrc = L.s[q] + size_t(j) * L.kpad[q];
           const char* xsrc = reinterpret_cast<const char*>(L.xT[q]) +
@@ -507,8 +537,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint64_t hp0 = hp_now();
         uint64_t hp_wb = 0, hp_wa = 0, hp_wc = 0, hp_n = 0;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-          int q, j, bi, bj;
-          decode_item<QF>(L, item, q, j, bi, bj);
+          const int q = item_q(L, item);
           const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
           const int64_t first = int64_t((mpar + 2 - uint32_t(g & 1)) & 1);
           const int64_t nown = nr > first ? (nr - first + 1) / 2 : 0;   // own rounds of the item
@@ -615,8 +644,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     };
     for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
-      int q, j, bi, bj;
-      decode_item<QF>(L, item, q, j, bi, bj);
+      int q, j, bi, bj, kind;
+      decode_item<QF>(L, item, q, j, bi, bj, kind);
       const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
       const int nb = L.nb[q];
 #pragma unroll 8
@@ -697,6 +726,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (I != J) P[size_t(J) * nb + I] = make_double2(g, 0.0);
           }
         }
+      } else if (kind != 0) {
+        // three-product layout: the tile of C or S, transposed ([col][row], rows coalesced),
+        // into the q's scratch; k_prod3_combine forms P after the launch
+        const size_t nbp = size_t(L.nbj[q]) * TM;
+        const int a = (kind == 2 ? bi - L.nbj[q] : bi) * TM + r;
+        const int b0 = (kind == 2 ? bj - L.nbj[q] : bj) * TN;
+        double* gt = L.g3[q] + (size_t(j) * 2 + (kind == 2 ? 1 : 0)) * nbp * nbp + size_t(b0) * nbp + a;
+#pragma unroll 8
+        for (int i = 0; i < TN; ++i) gt[size_t(i) * nbp] = acc[size_t(i) * TM];
       } else {
         // complex combination of rows (2I, 2I+1) held by lanes (2l, 2l+1)
         const int R = bi * TM + r;
@@ -790,6 +828,93 @@ __global__ void __launch_bounds__(128) k_prep_tc(const float* __restrict__ x, in
     const uint32_t off = sw64_off(n, kc);
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     *reinterpret_cast<uint4*>(hi + B_TILE + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+// The same per-q preparation for the complex polarization in three real products. With
+// M = Mr + i Mi and s_tj = |w_tj|, P_IJ = -sum_t s_tj conj(M_tI) M_tJ splits as
+//   P_IJ = -S_IJ + (1 + i) C_IJ + (1 - i) C_JI,
+//   C = Mr^T diag(s) Mi,   S = (Mr + Mi)^T diag(s) (Mr + Mi)
+// (the real part -(Mr^T D Mr + Mi^T D Mi) = -S + C + C^T, the imaginary part C - C^T): S is
+// symmetric, so the HERK computes its upper tiles and all tiles of C, N_b^2 (3/2) instead of
+// (2 N_b)^2 / 2 tile elements, 3/4 of the multiply-adds of the real Gram matrix of the
+// interleaved projections. A side (scaled later by the weights): column blocks [0, nbb) hold
+// Mr, [nbb, 2 nbb) Mr + Mi; B side: [0, nbb) Mi, [nbb, 2 nbb) Mr + Mi (nbb = ceil(N_b / 128),
+// zero padded). One CTA per (128 basis functions, chunk).
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_prep_tc3(const float* __restrict__ x, int64_t K, int nb,
+                                                  int nbb, int64_t kpad, int64_t nch,
+                                                  float* __restrict__ xT, char* __restrict__ bsp) {
+  constexpr int CH = BF16 ? 32 : 16;
+  constexpr int EPC = CH / 4;
+  __shared__ __align__(16) float tile[CH][2 * TM + 4];
+  const int cb = blockIdx.y;
+  const int64_t c = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < CH * TM; idx += 128) {     // (re, im) of 128 basis functions
+    const int t = idx / TM, n2 = idx % TM;
+    const int64_t row = c * CH + t;
+    const int a = cb * TM + n2;
+    float2 v = make_float2(0.f, 0.f);
+    if (row < K && a < nb) v = __ldg(reinterpret_cast<const float2*>(x + row * (2 * int64_t(nb)) + 2 * a));
+    *reinterpret_cast<float2*>(&tile[t][2 * n2]) = v;
+  }
+  __syncthreads();
+  const int n = tid;
+  float vr[CH], vi[CH], vs[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t) {
+    const float2 v = *reinterpret_cast<const float2*>(&tile[t][2 * n]);
+    vr[t] = v.x;
+    vi[t] = v.y;
+    vs[t] = v.x + v.y;
+  }
+  const int blk[2] = {cb, nbb + cb};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float* va = h ? vs : vr;                 // A side: Mr, Mr + Mi
+    const float* vb = h ? vs : vi;                 // B side: Mi, Mr + Mi
+    float4* dst = reinterpret_cast<float4*>(xT) + (size_t(blk[h]) * (kpad / CH) + c) * (CH / 4) * TM + n;
+#pragma unroll
+    for (int t = 0; t < CH / 4; ++t)
+      dst[size_t(t) * TM] = make_float4(va[4 * t], va[4 * t + 1], va[4 * t + 2], va[4 * t + 3]);
+    char* hi = bsp + (size_t(blk[h]) * nch + c) * CHUNK_BYTES;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      uint32_t hw[4], lw[4];
+      split_words<BF16>(vb + kc * EPC, hw, lw, 4);
+      const uint32_t off = sw64_off(n, kc);
+      *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>(hi + B_TILE + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  }
+}
+
+// P (or P += with accumulate) from the three-product tiles: P_ab = -S_ab + C_ab + C_ba
+// + i (C_ab - C_ba) for every a, b (Hermitian, since S is symmetric); the tiles are stored
+// transposed (G[a][b] at [b][a]) with nbp rows and columns, S only in its upper tiles.
+__global__ void k_prod3_combine(double2* __restrict__ P, const double* __restrict__ g3, int nb,
+                                int nbp, int nw, int accumulate) {
+  const int64_t n2 = int64_t(nb) * nb;
+  const int64_t total = n2 * nw;
+  const size_t p2 = size_t(nbp) * nbp;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t j = e / n2, rem = e % n2;
+    const int a = int(rem / nb), b = int(rem % nb);
+    const double* C = g3 + size_t(j) * 2 * p2;
+    const double* S = C + p2;
+    const double cab = C[size_t(b) * nbp + a], cba = C[size_t(a) * nbp + b];
+    // S_ab from its upper element (row <= column), and (C_ab + C_ba) summed in an order-free
+    // way, so that P_ba is exactly conj(P_ab)
+    const double sab = (a <= b) ? S[size_t(b) * nbp + a] : S[size_t(a) * nbp + b];
+    double re = (cab + cba) - sab, im = cab - cba;
+    if (accumulate) {
+      const double2 old = P[e];
+      re += old.x;
+      im += old.y;
+    }
+    P[e] = make_double2(re, im);
   }
 }
 
@@ -917,15 +1042,33 @@ int tile_count(int ncol, int* nbi_out) {
   return nbi * (nbi + 1) / 2;
 }
 
+// Tiles of the complex polarization of one q: the three-product layout (C and the upper half
+// of S over nbb = ceil(N_b / 128) blocks) where it has fewer tiles than the upper half of the
+// real Gram matrix of the interleaved projections (N_b = 600: 40 against 55; N_b <= 64 and a
+// few sizes such as 150 keep the interleaved layout). nbi: data blocks of each side.
+struct CplxLayout {
+  bool prod3;
+  int nbb;
+  int nbi;
+  int ntile;
+};
+CplxLayout cplx_layout(int nb) {
+  int nbi4;
+  const int t4 = tile_count(2 * nb, &nbi4);
+  const int nbb = (nb + TM - 1) / TM;
+  const int t3 = nbb * nbb + nbb * (nbb + 1) / 2;
+  if (t3 < t4) return CplxLayout{true, nbb, 2 * nbb, t3};
+  return CplxLayout{false, nbb, nbi4, t4};
+}
+
 }  // namespace
 
 static int64_t chunk_rows(int precision) { return precision == GW_BF16X3 ? 32 : 16; }
 
-static void q_sizes(int64_t K, int ncol, int precision, int64_t* nch, int64_t* kpad, int* nbi) {
+static void q_sizes(int64_t K, int precision, int64_t* nch, int64_t* kpad) {
   const int64_t ch = chunk_rows(precision);
   *nch = ((K + ch - 1) / ch + SUB - 1) / SUB * SUB;   // whole rounds (padding chunks are zero)
   *kpad = *nch * ch;
-  *nbi = (ncol + TM - 1) / TM;
 }
 
 // q points are processed in groups: preparation of the group's q, then one HERK launch over
@@ -934,10 +1077,16 @@ static void q_sizes(int64_t K, int ncol, int precision, int64_t* nch, int64_t* k
 // share a launch; the workspace holds one group at a time. The grouping uses the complex tile
 // count for real and complex projections alike, so the workspace query and the call agree.
 
-static size_t q_bytes(int64_t K, int ncol, int nw, int precision) {
+// the tiles of C and S of the three-product layout, [nw][2][nbp][nbp] doubles
+static size_t g3_bytes(const CplxLayout& lay, int nw) {
+  const size_t nbp = size_t(lay.nbb) * TM;
+  return lay.prod3 ? ws_round(size_t(nw) * 2 * nbp * nbp * sizeof(double)) : 0;
+}
+
+// nbi: data blocks of each side (the complex layout's, which is at least the real one's)
+static size_t q_bytes(int64_t K, int nbi, int nw, int precision) {
   int64_t nch, kpad;
-  int nbi;
-  q_sizes(K, ncol, precision, &nch, &kpad, &nbi);
+  q_sizes(K, precision, &nch, &kpad);
   return ws_round(size_t(nw) * size_t(kpad) * sizeof(float))          // weights
          + ws_round(size_t(nbi) * TM * size_t(kpad) * sizeof(float))  // chunk-major copy
          + ws_round(size_t(nbi) * size_t(nch) * CHUNK_BYTES);         // pre-split B tiles
@@ -955,7 +1104,7 @@ static void tc_groups(int nq, const int64_t* K, const int* nb, int nw, int sm,
       items = 0;
       n = 0;
     }
-    items += K[q] > 0 ? int64_t(tile_count(2 * nb[q], nullptr)) * nw : 0;
+    items += K[q] > 0 ? int64_t(cplx_layout(nb[q]).ntile) * nw : 0;
     ++n;
   }
   start.push_back(nq);
@@ -971,7 +1120,10 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
   size_t group_max = 0;
   for (size_t g = 0; g + 1 < start.size(); ++g) {
     size_t b = 0;
-    for (int q = start[g]; q < start[g + 1]; ++q) b += q_bytes(K[q], 2 * nb[q], nw, precision);
+    for (int q = start[g]; q < start[g + 1]; ++q) {
+      const CplxLayout lay = cplx_layout(nb[q]);
+      b += q_bytes(K[q], lay.nbi, nw, precision) + (K[q] > 0 ? g3_bytes(lay, nw) : 0);
+    }
     group_max = std::max(group_max, b);
   }
   return ws_round(size_t(sm) * TN * TM * sizeof(double)) + group_max;
@@ -1030,11 +1182,20 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     for (int i = 0; i < n; ++i) {
       const PolQ& Q = qs[q0 + i];
       int64_t nch, kpad;
+      q_sizes(Q.K, precision, &nch, &kpad);
+      const CplxLayout lay = cplx_layout(Q.nb);
+      const bool p3 = !real && lay.prod3 && Q.K > 0;     // K = 0: the zero P of the plain tiles
       int nbi;
-      q_sizes(Q.K, cpb * Q.nb, precision, &nch, &kpad, &nbi);
+      const int ntile = real ? tile_count(Q.nb, &nbi)
+                        : p3 ? (nbi = lay.nbi, lay.ntile) : tile_count(2 * Q.nb, &nbi);
       float* sw = static_cast<float*>(cur.take(size_t(nw) * size_t(kpad) * sizeof(float)));
       float* xT = static_cast<float*>(cur.take(size_t(nbi) * TM * size_t(kpad) * sizeof(float)));
       char* bsp = static_cast<char*>(cur.take(size_t(nbi) * size_t(nch) * CHUNK_BYTES));
+      double* g3 = nullptr;
+      if (p3) {
+        g3 = static_cast<double*>(cur.take(g3_bytes(lay, nw)));
+        if (!g3) return set_error(GW_EWORKSPACE, "internal: three-product tile buffers");
+      }
       if (kpad > 0) {
         if (!sw || !xT || !bsp) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
         int64_t blocks = std::min<int64_t>((kpad + 255) / 256, int64_t(ctx.sm_count) * 8);
@@ -1043,13 +1204,24 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
         GW_LAUNCH_CHECK("k_abs_weights_f32");
         const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbi));
         if (nch > 2147483647LL) return set_error(GW_EINVAL, "too many transitions for one q");
-        if (bf)
-          k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
-                                             kpad, nch, xT, bsp);
-        else
-          k_prep_tc<false><<<pg, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
-                                              kpad, nch, xT, bsp);
-        GW_LAUNCH_CHECK("k_prep_tc");
+        if (p3) {
+          const dim3 pg3(static_cast<unsigned>(nch), static_cast<unsigned>(lay.nbb));
+          if (bf)
+            k_prep_tc3<true><<<pg3, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, Q.nb,
+                                                 lay.nbb, kpad, nch, xT, bsp);
+          else
+            k_prep_tc3<false><<<pg3, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, Q.nb,
+                                                  lay.nbb, kpad, nch, xT, bsp);
+          GW_LAUNCH_CHECK("k_prep_tc3");
+        } else {
+          if (bf)
+            k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
+                                               kpad, nch, xT, bsp);
+          else
+            k_prep_tc<false><<<pg, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
+                                                kpad, nch, xT, bsp);
+          GW_LAUNCH_CHECK("k_prep_tc");
+        }
       }
       L.xT[i] = xT;
       L.bsp[i] = bsp;
@@ -1058,8 +1230,11 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
       L.K[i] = Q.K;
       L.kpad[i] = kpad;
       L.nb[i] = Q.nb;
-      L.ntile[i] = tile_count(cpb * Q.nb, &L.nbi[i]);
-      L.nbj[i] = L.nbi[i];
+      L.ntile[i] = ntile;
+      L.nbi[i] = nbi;
+      L.nbj[i] = p3 ? lay.nbb : nbi;
+      L.prod3[i] = p3 ? 1 : 0;
+      L.g3[i] = g3;
       L.item0[i] = item;
       item += int64_t(L.ntile[i]) * nw;
     }
@@ -1073,6 +1248,14 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
     if (rc) return rc;
     if ((rc = record_herk_event(o, o.launches, true, s))) return rc;
     ++o.launches;
+    for (int i = 0; i < n; ++i) {
+      const int64_t tot = int64_t(nw) * L.nb[i] * L.nb[i];
+      if (!L.prod3[i] || tot == 0) continue;
+      const unsigned blocks = unsigned(std::min<int64_t>((tot + 255) / 256, int64_t(ctx.sm_count) * 8));
+      k_prod3_combine<<<blocks, 256, 0, s>>>(L.P[i], L.g3[i], L.nb[i], L.nbj[i] * TM, nw,
+                                             L.accumulate);
+      GW_LAUNCH_CHECK("k_prod3_combine");
+    }
   }
   return GW_OK;
 }

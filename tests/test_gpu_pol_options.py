@@ -49,6 +49,36 @@ def test_k_slices_accumulate_into_one_p(gw, prec):
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("nb", [100, 200, 333])
+def test_three_product_layout_against_oracle(gw, prec, nb):
+    """N_b = 100, 200, 333 take the three-product layout (C = Mr^T D Mi in every tile, S =
+    (Mr + Mi)^T D (Mr + Mi) in the upper tiles, combined after the launch), 333 with ragged
+    blocks; one call over all three q and, for N_b = 200, K slices accumulated into one P."""
+    wl = S.tiny(nb=nb, nocc=4, nunocc=50, mesh=(2, 2, 1), nw=6, seed=300 + nb)
+    om = wl.omega()
+    M = wl.m_full(0).astype(np.complex64)
+    d = wl.delta(0)
+    P = gw.polarization([T(M)], [T(d)], om, wl.prefactor, prec)[0]
+    gw.check()
+    ref = OP.polarization(M.astype(np.complex128), d, om, wl.prefactor)
+    Pn = P.cpu().numpy()
+    assert rel_fro(Pn, ref) <= 1e-5
+    assert np.array_equal(Pn, np.conj(np.transpose(Pn, (0, 2, 1))))
+    # the diagonal is real
+    assert np.all(np.diagonal(Pn, axis1=1, axis2=2).imag == 0.0)
+    if nb == 200:
+        Pa = torch.zeros_like(P)
+        cuts = [0, 201, 555, len(d)]
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            gw.polarization([T(M[a:b])], [T(d[a:b])], om, wl.prefactor, prec, out=[Pa],
+                            options={"accumulate": True})
+        gw.check()
+        Pan = Pa.cpu().numpy()
+        assert rel_fro(Pan, ref) <= 1e-5
+        assert np.array_equal(Pan, np.conj(np.transpose(Pan, (0, 2, 1))))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 def test_tuning_knobs_do_not_change_the_result(gw, prec):
     """b_stages and the q grouping change neither the per-tile order of the sums nor the
     roundings: the results are bit-identical; the HERK events bracket every HERK launch."""
