@@ -43,7 +43,18 @@ METRIC = "P(iω)+Σ^c GFLOP/s and % of roofline, mixed vs FP64 on GB300 at ≤1e
 # (one q of K = 409,600), from the ncu capture summarised in profiles/ (one q cut to
 # K = 102,400, scaled by K: the tile grid is the same and the traffic grows in proportion with
 # K). Valid for the kernel as profiled; None where no capture of the current kernel exists.
-HERK_TRAFFIC_BYTES = {"bf16x3": (7.060e9 + 0.849e9) * 4, "tf32x3": (22.615e9 + 1.646e9) * 4}
+HERK_TRAFFIC_BYTES = {"bf16x3": (5.753e9 + 0.653e9) * 4, "tf32x3": (10.718e9 + 1.184e9) * 4}
+
+
+def cplx_tiles(nb):
+    """HERK tiles of one frequency of a complex q and whether they are the three-product layout
+    (the library's choice: C and the upper half of S over ceil(N_b / 128) blocks where that is
+    fewer than the upper half of the interleaved 2 N_b x 2 N_b Gram matrix)."""
+    nbi4 = (2 * nb + 127) // 128
+    t4 = nbi4 * (nbi4 + 1) // 2
+    nbb = (nb + 127) // 128
+    t3 = nbb * nbb + nbb * (nbb + 1) // 2
+    return (t3, True) if t3 < t4 else (t4, False)
 
 
 def workload_flops(wl):
@@ -270,15 +281,17 @@ class Pipeline:
             p = 2                                   # FP64 HERK + fixed-order reduction
         else:
             # weights + prep per q; one HERK launch per group of q (a group closes at 4 work
-            # items per SM; items = upper 128-tiles of the real 2 N_b x 2 N_b Gram x frequencies)
+            # items per SM; items = 128-tiles x frequencies); the combination of the
+            # three-product tiles per such q
             sm = torch.cuda.get_device_properties(self.dev).multi_processor_count
-            groups, items = 0, None
+            groups, items, n3 = 0, None, 0
             for nb in self.wl.nb:
-                t = (2 * nb + 127) // 128
+                t, p3 = cplx_tiles(nb)
                 if items is None or items >= 4 * sm:
                     groups, items = groups + 1, 0
-                items += t * (t + 1) // 2 * nw
-            p = 2 * nq + groups
+                items += t * nw
+                n3 += 1 if p3 else 0
+            p = 2 * nq + groups + n3
         # dielectric, per batch of <= 256 systems: eps, per 32-wide panel the diagonal block
         # (+ panel and trailing update but the last), diagonal inverses, inverse by block
         # columns, W^c
