@@ -97,6 +97,88 @@ __device__ __forceinline__ void tile_mac(T acc[4], const T* SA, const T* SB, int
   }
 }
 
+// ---- float-float tile products on the FP32 pipe ----------------------------------------------
+// GB300 executes FP64 fused multiply-adds at 1/64 of its FP32 rate, so the tile products of the
+// factorisation's trailing update, of the inverse by block columns and of Z^H Z run in
+// float-float arithmetic: every FP64 operand becomes an unevaluated sum h + l of two FP32
+// values (48 significant bits), each product h_x h_y is split exactly into its rounded value
+// and error with one FMA (Dekker's product), the cross terms h_x l_y + l_x h_y are added in
+// FP32 (l_x l_y and the rounding of the cross terms lie below 2^-48 of the product), and the
+// running sum keeps its exact rounding errors by Knuth's two-sum in a compensation term; the
+// result returns to FP64 as s + c. About 2^-48 relative per operation against 2^-53 for FP64.
+// Intrinsics (__fmul_rn, __fadd_rn) keep the compiler from fusing the error-free steps.
+struct FF {                // h + l, |l| <= ulp(h) / 2
+  float h, l;
+};
+struct FFC {
+  FF re, im;
+};
+struct FAcc {              // running sum s and compensation c: the value s + c
+  float s, c;
+};
+struct FAccC {
+  FAcc re, im;
+};
+template <typename T> struct FFOf;
+template <> struct FFOf<double> { using tile = FF; using acc = FAcc; };
+template <> struct FFOf<double2> { using tile = FFC; using acc = FAccC; };
+
+__device__ __forceinline__ FF to_ff(double x) {
+  const float h = __double2float_rn(x);
+  return FF{h, __double2float_rn(x - double(h))};
+}
+__device__ __forceinline__ FF to_ff_t(double x) { return to_ff(x); }
+__device__ __forceinline__ FFC to_ff_t(double2 x) { return FFC{to_ff(x.x), to_ff(x.y)}; }
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.h, -x.l}; }
+__device__ __forceinline__ FFC ff_conj(FFC x) { return FFC{x.re, ff_neg(x.im)}; }
+__device__ __forceinline__ FF ff_conj(FF x) { return x; }
+
+// a += x y
+__device__ __forceinline__ void ff_mac(FAcc& a, FF x, FF y) {
+  const float p = __fmul_rn(x.h, y.h);
+  const float e = __fmaf_rn(x.h, y.h, -p);                       // x.h y.h = p + e exactly
+  const float t = __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.h));      // cross terms
+  const float sum = __fadd_rn(a.s, p);                           // two-sum: a.s + p = sum + err
+  const float bp = __fadd_rn(sum, -a.s);
+  const float err = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(sum, -bp)), __fadd_rn(p, -bp));
+  a.s = sum;
+  a.c = __fadd_rn(a.c, __fadd_rn(err, __fadd_rn(e, t)));
+}
+__device__ __forceinline__ void ff_cmac(FAcc& a, FF x, FF y) { ff_mac(a, x, y); }
+__device__ __forceinline__ void ff_cmac(FAccC& a, FFC x, FFC y) {   // a += x y, complex
+  ff_mac(a.re, x.re, y.re);
+  ff_mac(a.re, ff_neg(x.im), y.im);
+  ff_mac(a.im, x.re, y.im);
+  ff_mac(a.im, x.im, y.re);
+}
+__device__ __forceinline__ double ff_value(FAcc a) { return double(a.s) + double(a.c); }
+__device__ __forceinline__ double ff_value_t(FAcc a) { return ff_value(a); }
+__device__ __forceinline__ double2 ff_value_t(FAccC a) { return make_double2(ff_value(a.re), ff_value(a.im)); }
+
+// load_tile into float-float shared memory
+template <typename T>
+__device__ __forceinline__ void load_tile_ff(typename FFOf<T>::tile* S, const T* A, int ld,
+                                             int n_rows, int n_cols, int r0, int c0, int mode) {
+  for (int e = threadIdx.x; e < DB * DB; e += DTHREADS) {
+    int r = e / DB, c = e % DB;
+    int R = r0 + r, C = c0 + c;
+    T v = T{};
+    if (R < n_rows && C < n_cols && (mode == 0 || C <= R)) v = A[size_t(R) * ld + C];
+    S[r * DLD + c] = to_ff_t(v);
+  }
+}
+
+// acc[b] += sum_k opA(tr, k) * SB[k][tc + 8 b] in float-float; opA = SA[tr][k] or conj(SA[k][tr])
+template <bool A_CONJ_T, typename FT, typename FA>
+__device__ __forceinline__ void tile_mac_ff(FA acc[4], const FT* SA, const FT* SB, int tr, int tc) {
+#pragma unroll 4
+  for (int k = 0; k < DB; ++k) {
+    const FT a = A_CONJ_T ? ff_conj(SA[k * DLD + tr]) : SA[tr * DLD + k];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) ff_cmac(acc[b], a, SB[k * DLD + tc + 8 * b]);
+  }
+}
+
 constexpr int DMAXSYS = 256;   // systems per launch (descriptors passed by value)
 template <typename T>
 struct DieBatchT {
@@ -303,10 +385,11 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatchT<T> batc
 // (the lower tiles ct <= rt of the block row and their Hermitian mirror)
 template <typename T>
 __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> batch) {
+  using FT = typename FFOf<T>::tile;
+  using FA = typename FFOf<T>::acc;
   extern __shared__ __align__(16) unsigned char dsm_raw[];
-  T* smem = reinterpret_cast<T*>(dsm_raw);
-  T* SA = smem;
-  T* SB = smem + DB * DLD;
+  FT* SA = reinterpret_cast<FT*>(dsm_raw);      // float-float tiles (the size of T)
+  FT* SB = SA + DB * DLD;
   const DieSysT<T> sys = batch.s[blockIdx.x];
   const int n = sys.n;
   const int nt = (n + DB - 1) / DB;
@@ -316,12 +399,12 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> ba
   const int tid = threadIdx.x;
   const int tr = tid >> 3, tc = tid & 7;
   for (int ct = 0; ct <= rt; ++ct) {
-    T acc[4] = {T{}, T{}, T{}, T{}};
+    FA acc[4] = {};
     for (int kt2 = rt; kt2 < nt; ++kt2) {
-      load_tile(SA, E, n, n, n, kt2 * DB, rt * DB, 1);   // Z[K][R] (lower part)
-      load_tile(SB, E, n, n, n, kt2 * DB, ct * DB, 1);   // Z[K][S]
+      load_tile_ff<T>(SA, E, n, n, n, kt2 * DB, rt * DB, 1);   // Z[K][R] (lower part)
+      load_tile_ff<T>(SB, E, n, n, n, kt2 * DB, ct * DB, 1);   // Z[K][S]
       __syncthreads();
-      tile_mac<true>(acc, SA, SB, tr, tc);
+      tile_mac_ff<true>(acc, SA, SB, tr, tc);
       __syncthreads();
     }
     int R = rt * DB + tr;
@@ -331,7 +414,7 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> ba
       for (int b = 0; b < 4; ++b) {
         int C = ct * DB + tc + 8 * b;
         if (C < n && C <= R) {
-          T x = acc[b];
+          T x = ff_value_t(acc[b]);
           if (C == R) x = real_of<T>(re_(x) - 1.0);
           x = scal(x, sqrt(vr * sys.v[C]));
           sys.Wc[size_t(R) * n + C] = to_c(x);
@@ -384,10 +467,11 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_dinv(const DieBatchT<T>
 // with the earlier blocks Z[k][c] of the same column read back from global memory.
 template <typename T>
 __global__ void __launch_bounds__(DTHREADS) k_dielectric_zcol(const DieBatchT<T> batch) {
+  using FT = typename FFOf<T>::tile;
+  using FA = typename FFOf<T>::acc;
   extern __shared__ __align__(16) unsigned char dsm_raw[];
-  T* smem = reinterpret_cast<T*>(dsm_raw);
-  T* SA = smem;
-  T* SB = smem + DB * DLD;
+  FT* SA = reinterpret_cast<FT*>(dsm_raw);      // float-float tiles (the size of T)
+  FT* SB = SA + DB * DLD;
   const DieSysT<T> sys = batch.s[blockIdx.x];
   const int n = sys.n;
   const int nt = (n + DB - 1) / DB;
@@ -403,24 +487,25 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_zcol(const DieBatchT<T>
 #pragma unroll
       for (int b = 0; b < 4; ++b) out[b] = Dr[tr * DB + tc + 8 * b];
     } else {
-      T acc[4] = {T{}, T{}, T{}, T{}};
+      FA acc[4] = {};
       for (int k = c; k < r; ++k) {
-        load_tile(SA, sys.E, n, n, n, r * DB, k * DB, 0);              // L[r][k]
-        load_tile(SB, Z, n, n, n, k * DB, c * DB, k == c ? 1 : 0);   // Z[k][c]
+        load_tile_ff<T>(SA, sys.E, n, n, n, r * DB, k * DB, 0);              // L[r][k]
+        load_tile_ff<T>(SB, Z, n, n, n, k * DB, c * DB, k == c ? 1 : 0);   // Z[k][c]
         __syncthreads();
-        tile_mac<false>(acc, SA, SB, tr, tc);
+        tile_mac_ff<false>(acc, SA, SB, tr, tc);
         __syncthreads();
       }
       // out = -D_r acc: the product tile in SB, D_r in SA
 #pragma unroll
-      for (int b = 0; b < 4; ++b) SB[tr * DLD + tc + 8 * b] = acc[b];
+      for (int b = 0; b < 4; ++b) SB[tr * DLD + tc + 8 * b] = to_ff_t(ff_value_t(acc[b]));
       const T* Dr = sys.D + size_t(r) * DB * DB;
-      for (int e = tid; e < DB * DB; e += DTHREADS) SA[(e / DB) * DLD + e % DB] = Dr[e];
+      for (int e = tid; e < DB * DB; e += DTHREADS) SA[(e / DB) * DLD + e % DB] = to_ff_t(Dr[e]);
       __syncthreads();
-      tile_mac<false>(out, SA, SB, tr, tc);
+      FA o[4] = {};
+      tile_mac_ff<false>(o, SA, SB, tr, tc);
       __syncthreads();
 #pragma unroll
-      for (int b = 0; b < 4; ++b) out[b] = scal(out[b], -1.0);
+      for (int b = 0; b < 4; ++b) out[b] = scal(ff_value_t(o[b]), -1.0);
     }
     const int R = r * DB + tr;
     if (R < n) {
@@ -543,9 +628,11 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_panel(const DieBatchT<T> batc
 // tiles keep their lower triangle); grid (tiles of the largest system, system)
 template <typename T>
 __global__ void __launch_bounds__(DTHREADS) k_chol_update(const DieBatchT<T> batch, int kt) {
+  using FT = typename FFOf<T>::tile;
+  using FA = typename FFOf<T>::acc;
   extern __shared__ __align__(16) unsigned char dsm_raw[];
-  T* SA = reinterpret_cast<T*>(dsm_raw);
-  T* SB = SA + DB * DLD;
+  FT* SA = reinterpret_cast<FT*>(dsm_raw);      // float-float tiles (the size of T)
+  FT* SB = SA + DB * DLD;
   const DieSysT<T>& sys = batch.s[blockIdx.y];
   const int n = sys.n, nt = (n + DB - 1) / DB;
   const int m = nt - kt - 1;                 // trailing block rows
@@ -560,21 +647,21 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_update(const DieBatchT<T> bat
   const int k0 = kt * DB;
   const int tid = threadIdx.x, tr = tid >> 3, tc = tid & 7;
   const T* E = sys.E;
-  load_tile(SA, E, n, n, n, it * DB, k0, 0);                  // L_ik
+  load_tile_ff<T>(SA, E, n, n, n, it * DB, k0, 0);            // L_ik
   for (int e = tid; e < DB * DB; e += DTHREADS) {             // SB[k][c] = conj(L_jk[c][k])
     const int k = e / DB, c = e % DB;
     const int R = jt * DB + c;
-    SB[k * DLD + c] = R < n ? cconj(E[size_t(R) * n + k0 + k]) : T{};
+    SB[k * DLD + c] = to_ff_t(R < n ? cconj(E[size_t(R) * n + k0 + k]) : T{});
   }
   __syncthreads();
-  T acc[4] = {T{}, T{}, T{}, T{}};
-  tile_mac<false>(acc, SA, SB, tr, tc);
+  FA acc[4] = {};
+  tile_mac_ff<false>(acc, SA, SB, tr, tc);
   const int R = it * DB + tr;
   if (R < n) {
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int C = jt * DB + tc + 8 * b;
-      if (C < n && C <= R) sys.E[size_t(R) * n + C] = csub(E[size_t(R) * n + C], acc[b]);
+      if (C < n && C <= R) sys.E[size_t(R) * n + C] = csub(E[size_t(R) * n + C], ff_value_t(acc[b]));
     }
   }
 }
