@@ -155,6 +155,37 @@ __device__ __forceinline__ double ff_value(FAcc a) { return double(a.s) + double
 __device__ __forceinline__ double ff_value_t(FAcc a) { return ff_value(a); }
 __device__ __forceinline__ double2 ff_value_t(FAccC a) { return make_double2(ff_value(a.re), ff_value(a.im)); }
 
+// the float-float value h + l of an accumulator (two-sum of s and c)
+__device__ __forceinline__ FF ff_renorm(FAcc a) {
+  const float h = __fadd_rn(a.s, a.c);
+  const float bp = __fadd_rn(h, -a.s);
+  return FF{h, __fadd_rn(__fadd_rn(a.s, -__fadd_rn(h, -bp)), __fadd_rn(a.c, -bp))};
+}
+__device__ __forceinline__ FF ff_renorm_t(FAcc a) { return ff_renorm(a); }
+__device__ __forceinline__ FFC ff_renorm_t(FAccC a) { return FFC{ff_renorm(a.re), ff_renorm(a.im)}; }
+__device__ __forceinline__ FAcc ff_acc(FF x) { return FAcc{x.h, x.l}; }
+__device__ __forceinline__ FAccC ff_acc(FFC x) { return FAccC{ff_acc(x.re), ff_acc(x.im)}; }
+// x y rounded to float-float (the correction is below ulp(p), so a fast two-sum renormalises)
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.h, y.h);
+  const float q = __fadd_rn(__fmaf_rn(x.h, y.h, -p), __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.h)));
+  const float h = __fadd_rn(p, q);
+  return FF{h, __fadd_rn(q, -__fadd_rn(h, -p))};
+}
+__device__ __forceinline__ FF ff_scale(FF x, FF r) { return ff_mul(x, r); }
+__device__ __forceinline__ FFC ff_scale(FFC x, FF r) { return FFC{ff_mul(x.re, r), ff_mul(x.im, r)}; }
+// acc -= x conj(l)
+__device__ __forceinline__ void ff_csubmul_conj(FAcc& a, FF x, FF l) { ff_mac(a, ff_neg(x), l); }
+__device__ __forceinline__ void ff_csubmul_conj(FAccC& a, FFC x, FFC l) {
+  ff_mac(a.re, ff_neg(x.re), l.re);
+  ff_mac(a.re, ff_neg(x.im), l.im);
+  ff_mac(a.im, ff_neg(x.im), l.re);
+  ff_mac(a.im, x.re, l.im);
+}
+__device__ __forceinline__ double ff_to_d(FF x) { return double(x.h) + double(x.l); }
+__device__ __forceinline__ double ff_to_t(FF x) { return ff_to_d(x); }
+__device__ __forceinline__ double2 ff_to_t(FFC x) { return make_double2(ff_to_d(x.re), ff_to_d(x.im)); }
+
 // load_tile into float-float shared memory
 template <typename T>
 __device__ __forceinline__ void load_tile_ff(typename FFOf<T>::tile* S, const T* A, int ld,
@@ -398,7 +429,11 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> ba
   const T* E = sys.Z;
   const int tid = threadIdx.x;
   const int tr = tid >> 3, tc = tid & 7;
+  __shared__ double svr[DB], svc[DB];        // square roots of v of the tile's rows and columns
+  if (tid < DB) svr[tid] = rt * DB + tid < n ? sqrt(sys.v[rt * DB + tid]) : 0.0;
   for (int ct = 0; ct <= rt; ++ct) {
+    __syncthreads();                          // the previous tile's epilogue has read svc
+    if (tid < DB) svc[tid] = ct * DB + tid < n ? sqrt(sys.v[ct * DB + tid]) : 0.0;
     FA acc[4] = {};
     for (int kt2 = rt; kt2 < nt; ++kt2) {
       load_tile_ff<T>(SA, E, n, n, n, kt2 * DB, rt * DB, 1);   // Z[K][R] (lower part)
@@ -409,14 +444,13 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> ba
     }
     int R = rt * DB + tr;
     if (R < n) {
-      double vr = sys.v[R];
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         int C = ct * DB + tc + 8 * b;
         if (C < n && C <= R) {
           T x = ff_value_t(acc[b]);
           if (C == R) x = real_of<T>(re_(x) - 1.0);
-          x = scal(x, sqrt(vr * sys.v[C]));
+          x = scal(x, svr[tr] * svc[tc + 8 * b]);
           sys.Wc[size_t(R) * n + C] = to_c(x);
           if (C != R) sys.Wc[size_t(C) * n + R] = to_c(cconj(x));
         }
@@ -526,18 +560,32 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_zcol(const DieBatchT<T>
 // SM takes part however few systems there are (20 systems of N_b = 4096 would leave 132 of
 // 152 SMs idle with one CTA per system).
 
-// eps = 1 - v^1/2 P v^1/2 over the full matrix: grid (element blocks, system)
+// eps = 1 - v^1/2 P v^1/2 over the full matrix: grid (32-row blocks, system); the square roots
+// of v are taken once per row and column block (FP64 square roots are costly on GB300's FP64
+// pipe) and kept in shared memory
 template <typename T>
 __global__ void __launch_bounds__(DTHREADS) k_eps_fill(const DieBatchT<T> batch, unsigned* status) {
+  __shared__ double svr[DB], svc[DTHREADS];
   const DieSysT<T>& sys = batch.s[blockIdx.y];
-  const size_t n = size_t(sys.n), nn = n * n;
+  const int n = sys.n;
+  const int r0 = blockIdx.x * DB;
+  if (r0 >= n) return;                       // whole CTA, before any barrier
+  const int tid = threadIdx.x;
+  if (tid < DB) svr[tid] = r0 + tid < n ? sqrt(sys.v[r0 + tid]) : 0.0;
   bool bad = false;
-  for (size_t e = blockIdx.x * size_t(DTHREADS) + threadIdx.x; e < nn; e += size_t(gridDim.x) * DTHREADS) {
-    const size_t r = e / n, c = e % n;
-    T x = scal(from_c<T>(sys.P[e]), -sqrt(sys.v[r] * sys.v[c]));
-    if (r == c) x = add_re(x, 1.0);
-    if (!fin(x)) bad = true;
-    sys.E[e] = x;
+  for (int c0 = 0; c0 < n; c0 += DTHREADS) {
+    __syncthreads();                          // the previous chunk's svc is read
+    svc[tid] = c0 + tid < n ? sqrt(sys.v[c0 + tid]) : 0.0;
+    __syncthreads();
+    const int c = c0 + tid;
+    if (c >= n) continue;
+    for (int rr = 0; rr < DB && r0 + rr < n; ++rr) {
+      const size_t e = size_t(r0 + rr) * n + c;
+      T x = scal(from_c<T>(sys.P[e]), -(svr[rr] * svc[tid]));
+      if (r0 + rr == c) x = add_re(x, 1.0);
+      if (!fin(x)) bad = true;
+      sys.E[e] = x;
+    }
   }
   if (bad) raise_status(status, ST_ENONFINITE);
 }
@@ -593,34 +641,40 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_diag(const DieBatchT<T> batch
   if (threadIdx.x == 0 && s_fail) raise_status(status, ST_ENOTHPD);
 }
 
-// step 2: the panel X L_kk^H = A_ik below the diagonal block, one row per thread;
-// grid (256-row blocks of the trailing rows, system)
+// step 2: the panel X L_kk^H = A_ik below the diagonal block, one row per thread, in
+// float-float (the reciprocals of the diagonal in FP64); grid (256-row blocks of the trailing
+// rows, system)
 template <typename T>
 __global__ void __launch_bounds__(DTHREADS) k_chol_panel(const DieBatchT<T> batch, int kt) {
-  __shared__ T SD[DB * DLD];
+  using FT = typename FFOf<T>::tile;
+  using FA = typename FFOf<T>::acc;
+  __shared__ FT SD[DB * DLD];
+  __shared__ FF rinv[DB];
   const DieSysT<T>& sys = batch.s[blockIdx.y];
   const int n = sys.n, nt = (n + DB - 1) / DB;
   if (kt >= nt - 1) return;                  // no rows below the last block
   const int k0 = kt * DB;                    // a full block: kt < nt - 1
   const int r0 = k0 + DB + blockIdx.x * DTHREADS;
   if (r0 >= n) return;                       // whole CTA, before any barrier
-  load_tile(SD, sys.E, n, n, n, k0, k0, 1);
+  load_tile_ff<T>(SD, sys.E, n, n, n, k0, k0, 1);
+  if (threadIdx.x < DB)
+    rinv[threadIdx.x] = to_ff(1.0 / re_(sys.E[size_t(k0 + threadIdx.x) * n + k0 + threadIdx.x]));
   __syncthreads();
   const int r = r0 + threadIdx.x;
   if (r < n) {
-    T x[DB];
+    FT x[DB];
     T* row = sys.E + size_t(r) * n + k0;
 #pragma unroll
-    for (int c = 0; c < DB; ++c) x[c] = row[c];
+    for (int c = 0; c < DB; ++c) x[c] = to_ff_t(row[c]);
 #pragma unroll
     for (int c = 0; c < DB; ++c) {
-      T acc = x[c];
+      FA acc = ff_acc(x[c]);
 #pragma unroll
-      for (int k = 0; k < c; ++k) csubmul(acc, x[k], cconj(SD[c * DLD + k]));
-      x[c] = scal(acc, 1.0 / re_(SD[c * DLD + c]));
+      for (int k = 0; k < c; ++k) ff_csubmul_conj(acc, x[k], SD[c * DLD + k]);
+      x[c] = ff_scale(ff_renorm_t(acc), rinv[c]);
     }
 #pragma unroll
-    for (int c = 0; c < DB; ++c) row[c] = x[c];
+    for (int c = 0; c < DB; ++c) row[c] = ff_to_t(x[c]);
   }
 }
 
@@ -674,9 +728,8 @@ static int launch_cholesky_grid(const DieBatchT<T>& batch, int nsys, int ntmax, 
   if (rc) return rc;
   int nmax = 0;
   for (int i = 0; i < nsys; ++i) nmax = std::max(nmax, batch.s[i].n);
-  const int64_t nn = int64_t(nmax) * nmax;
-  const unsigned fb = unsigned(std::min<int64_t>((nn + DTHREADS - 1) / DTHREADS, 4096));
-  k_eps_fill<T><<<dim3(fb, unsigned(nsys)), DTHREADS, 0, s>>>(batch, ctx.status);
+  k_eps_fill<T><<<dim3(unsigned((nmax + DB - 1) / DB), unsigned(nsys)), DTHREADS, 0, s>>>(batch,
+                                                                                        ctx.status);
   GW_LAUNCH_CHECK("k_eps_fill");
   for (int kt = 0; kt < ntmax; ++kt) {
     k_chol_diag<T><<<unsigned(nsys), DTHREADS, 0, s>>>(batch, kt, ctx.status);
