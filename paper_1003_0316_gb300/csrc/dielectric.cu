@@ -5,13 +5,17 @@
 //   Z   = L^{-1}                  blocked triangular inversion
 //   W^c = v^1/2 (Z^H Z - 1) v^1/2
 //
-// One CTA per (q, frequency) system factorises a workspace copy of eps in place, with 32x32
-// tiles staged in shared memory; each thread owns one row and four columns of a tile. The
-// inverse factor follows by block columns (the diagonal blocks inverted first, then one CTA
-// per (system, block column) for the forward substitution of that column), and W^c from the
-// inverse factor with one CTA per (system, 32-row block), so both use every SM. The
-// no-allocation entry point keeps the inverse inside the system's CTA (in place). The phases are FP64-pipe bound:
-// about 4 N^3 real flops per system (N^3/6 complex multiply-adds each).
+// The caller-workspace entry points factorise a workspace copy of eps right-looking over many
+// CTAs (per 32-wide panel: the diagonal block, the panel below it, the trailing update of the
+// lower 32x32 tiles), invert the factor by block columns (the diagonal blocks first, then one
+// CTA per (system, block column) for the forward substitution of that column) and form W^c
+// with one CTA per (system, 32-row block), so every phase uses every SM; each thread owns one
+// row and four columns of a 32x32 tile staged in shared memory. About 4 N^3 real flops per
+// system (N^3/6 complex multiply-adds per phase). Storage and the small steps (diagonal
+// blocks, their inverses) are FP64; the tile products and the panel solve run in float-float
+// arithmetic on the FP32 pipe, which GB300 executes 64 times faster than FP64 (see FF below):
+// about 2^-48 relative per operation. The no-allocation entry point keeps the factorisation
+// and the inverse inside one CTA per system, in FP64.
 #include <vector>
 #include <algorithm>
 #include <mutex>
