@@ -190,6 +190,58 @@ __device__ __forceinline__ double ff_to_d(FF x) { return double(x.h) + double(x.
 __device__ __forceinline__ double ff_to_t(FF x) { return ff_to_d(x); }
 __device__ __forceinline__ double2 ff_to_t(FFC x) { return make_double2(ff_to_d(x.re), ff_to_d(x.im)); }
 
+// e - a rounded to float-float (e a float-float value, a an accumulator)
+__device__ __forceinline__ FF ff_sub_acc(FF e, FAcc a) {
+  const float sh = __fadd_rn(e.h, -a.s);                          // two-sum of e.h and -a.s
+  const float bp = __fadd_rn(sh, -e.h);
+  const float err = __fadd_rn(__fadd_rn(e.h, -__fadd_rn(sh, -bp)), __fadd_rn(-a.s, -bp));
+  return ff_renorm(FAcc{sh, __fadd_rn(err, __fadd_rn(e.l, -a.c))});
+}
+__device__ __forceinline__ FF ff_sub_acc_t(FF e, FAcc a) { return ff_sub_acc(e, a); }
+__device__ __forceinline__ FFC ff_sub_acc_t(FFC e, FAccC a) {
+  return FFC{ff_sub_acc(e.re, a.re), ff_sub_acc(e.im, a.im)};
+}
+__device__ __forceinline__ FF ff_negate(FF x) { return ff_neg(x); }
+__device__ __forceinline__ FFC ff_negate(FFC x) { return FFC{ff_neg(x.re), ff_neg(x.im)}; }
+
+// The caller-workspace path keeps eps, its factor, the inverse factor and the inverted
+// diagonal blocks in float-float form (the bytes of the FP64 element: complex FFC, real FF),
+// so the tile products load them without FP64 conversions; the diagonal blocks are factorised
+// and inverted in FP64 and the output W^c is FP64.
+template <typename T>
+using StorOf = typename FFOf<T>::tile;
+template <typename T>
+__device__ __forceinline__ StorOf<T>* stor(T* p) { return reinterpret_cast<StorOf<T>*>(p); }
+template <typename T>
+__device__ __forceinline__ const StorOf<T>* stor(const T* p) {
+  return reinterpret_cast<const StorOf<T>*>(p);
+}
+
+// a DB x DB tile of float-float storage into shared memory (mode 1: lower triangle only)
+template <typename FT>
+__device__ __forceinline__ void load_tile_s(FT* S, const FT* A, int ld, int n_rows, int n_cols,
+                                            int r0, int c0, int mode) {
+  for (int e = threadIdx.x; e < DB * DB; e += DTHREADS) {
+    int r = e / DB, c = e % DB;
+    int R = r0 + r, C = c0 + c;
+    FT v = FT{};
+    if (R < n_rows && C < n_cols && (mode == 0 || C <= R)) v = A[size_t(R) * ld + C];
+    S[r * DLD + c] = v;
+  }
+}
+// the same into FP64 shared memory
+template <typename T>
+__device__ __forceinline__ void load_tile_s2d(T* S, const StorOf<T>* A, int ld, int n_rows,
+                                              int n_cols, int r0, int c0, int mode) {
+  for (int e = threadIdx.x; e < DB * DB; e += DTHREADS) {
+    int r = e / DB, c = e % DB;
+    int R = r0 + r, C = c0 + c;
+    T v = T{};
+    if (R < n_rows && C < n_cols && (mode == 0 || C <= R)) v = ff_to_t(A[size_t(R) * ld + C]);
+    S[r * DLD + c] = v;
+  }
+}
+
 // load_tile into float-float shared memory
 template <typename T>
 __device__ __forceinline__ void load_tile_ff(typename FFOf<T>::tile* S, const T* A, int ld,
@@ -418,7 +470,7 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric(const DieBatchT<T> batc
 
 // ---- phase 3: W^c = v^1/2 (Z^H Z - 1) v^1/2, one CTA per (system, 32-row block rt) ---------
 // (the lower tiles ct <= rt of the block row and their Hermitian mirror)
-template <typename T>
+template <typename T, bool FS>
 __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> batch) {
   using FT = typename FFOf<T>::tile;
   using FA = typename FFOf<T>::acc;
@@ -440,8 +492,13 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_w(const DieBatchT<T> ba
     if (tid < DB) svc[tid] = ct * DB + tid < n ? sqrt(sys.v[ct * DB + tid]) : 0.0;
     FA acc[4] = {};
     for (int kt2 = rt; kt2 < nt; ++kt2) {
-      load_tile_ff<T>(SA, E, n, n, n, kt2 * DB, rt * DB, 1);   // Z[K][R] (lower part)
-      load_tile_ff<T>(SB, E, n, n, n, kt2 * DB, ct * DB, 1);   // Z[K][S]
+      if (FS) {                              // Z in float-float storage
+        load_tile_s(SA, stor(E), n, n, n, kt2 * DB, rt * DB, 1);   // Z[K][R] (lower part)
+        load_tile_s(SB, stor(E), n, n, n, kt2 * DB, ct * DB, 1);   // Z[K][S]
+      } else {                               // Z in FP64 (the no-allocation entry)
+        load_tile_ff<T>(SA, E, n, n, n, kt2 * DB, rt * DB, 1);
+        load_tile_ff<T>(SB, E, n, n, n, kt2 * DB, ct * DB, 1);
+      }
       __syncthreads();
       tile_mac_ff<true>(acc, SA, SB, tr, tc);
       __syncthreads();
@@ -476,7 +533,7 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_dinv(const DieBatchT<T>
   if (r >= nt) return;
   const int k0 = r * DB;
   const int kb = min(DB, n - k0);
-  load_tile(SD, sys.E, n, n, n, k0, k0, 1);
+  load_tile_s2d(SD, stor(sys.E), n, n, n, k0, k0, 1);
   __syncthreads();
   if (threadIdx.x < DB) {
     const int c = threadIdx.x;
@@ -494,9 +551,9 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_dinv(const DieBatchT<T>
         }
       }
     }
-    T* Dr = sys.D + size_t(r) * DB * DB;
+    StorOf<T>* Dr = stor(sys.D) + size_t(r) * DB * DB;
 #pragma unroll
-    for (int i = 0; i < DB; ++i) Dr[i * DB + c] = z[i];
+    for (int i = 0; i < DB; ++i) Dr[i * DB + c] = to_ff_t(z[i]);
   }
 }
 
@@ -517,33 +574,34 @@ __global__ void __launch_bounds__(DTHREADS) k_dielectric_zcol(const DieBatchT<T>
   if (c >= nt) return;                       // whole CTA, before any barrier
   const int tid = threadIdx.x;
   const int tr = tid >> 3, tc = tid & 7;
-  T* Z = sys.Z;
+  StorOf<T>* Z = stor(sys.Z);
+  const StorOf<T>* L = stor(sys.E);
   for (int r = c; r < nt; ++r) {
-    T out[4] = {T{}, T{}, T{}, T{}};
+    FT out[4] = {FT{}, FT{}, FT{}, FT{}};
     if (r == c) {
-      const T* Dr = sys.D + size_t(r) * DB * DB;
+      const FT* Dr = stor(sys.D) + size_t(r) * DB * DB;
 #pragma unroll
       for (int b = 0; b < 4; ++b) out[b] = Dr[tr * DB + tc + 8 * b];
     } else {
       FA acc[4] = {};
       for (int k = c; k < r; ++k) {
-        load_tile_ff<T>(SA, sys.E, n, n, n, r * DB, k * DB, 0);              // L[r][k]
-        load_tile_ff<T>(SB, Z, n, n, n, k * DB, c * DB, k == c ? 1 : 0);   // Z[k][c]
+        load_tile_s(SA, L, n, n, n, r * DB, k * DB, 0);              // L[r][k]
+        load_tile_s(SB, Z, n, n, n, k * DB, c * DB, k == c ? 1 : 0); // Z[k][c]
         __syncthreads();
         tile_mac_ff<false>(acc, SA, SB, tr, tc);
         __syncthreads();
       }
       // out = -D_r acc: the product tile in SB, D_r in SA
 #pragma unroll
-      for (int b = 0; b < 4; ++b) SB[tr * DLD + tc + 8 * b] = to_ff_t(ff_value_t(acc[b]));
-      const T* Dr = sys.D + size_t(r) * DB * DB;
-      for (int e = tid; e < DB * DB; e += DTHREADS) SA[(e / DB) * DLD + e % DB] = to_ff_t(Dr[e]);
+      for (int b = 0; b < 4; ++b) SB[tr * DLD + tc + 8 * b] = ff_renorm_t(acc[b]);
+      const FT* Dr = stor(sys.D) + size_t(r) * DB * DB;
+      for (int e = tid; e < DB * DB; e += DTHREADS) SA[(e / DB) * DLD + e % DB] = Dr[e];
       __syncthreads();
       FA o[4] = {};
       tile_mac_ff<false>(o, SA, SB, tr, tc);
       __syncthreads();
 #pragma unroll
-      for (int b = 0; b < 4; ++b) out[b] = scal(ff_value_t(o[b]), -1.0);
+      for (int b = 0; b < 4; ++b) out[b] = ff_negate(ff_renorm_t(o[b]));
     }
     const int R = r * DB + tr;
     if (R < n) {
@@ -588,7 +646,7 @@ __global__ void __launch_bounds__(DTHREADS) k_eps_fill(const DieBatchT<T> batch,
       T x = scal(from_c<T>(sys.P[e]), -(svr[rr] * svc[tid]));
       if (r0 + rr == c) x = add_re(x, 1.0);
       if (!fin(x)) bad = true;
-      sys.E[e] = x;
+      stor(sys.E)[e] = to_ff_t(x);
     }
   }
   if (bad) raise_status(status, ST_ENONFINITE);
@@ -635,12 +693,12 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_diag(const DieBatchT<T> batch
   if (kt >= nt) return;                      // whole CTA, before any barrier
   const int k0 = kt * DB, kb = min(DB, n - k0);
   if (threadIdx.x == 0) s_fail = 0;
-  load_tile(SD, sys.E, n, n, n, k0, k0, 1);
+  load_tile_s2d(SD, stor(sys.E), n, n, n, k0, k0, 1);
   __syncthreads();
   chol_block_smem(SD, kb, &s_fail);
   for (int e = threadIdx.x; e < DB * DB; e += DTHREADS) {
     const int r = e / DB, c = e % DB;
-    if (r < kb && c <= r) sys.E[size_t(k0 + r) * n + k0 + c] = SD[r * DLD + c];
+    if (r < kb && c <= r) stor(sys.E)[size_t(k0 + r) * n + k0 + c] = to_ff_t(SD[r * DLD + c]);
   }
   if (threadIdx.x == 0 && s_fail) raise_status(status, ST_ENOTHPD);
 }
@@ -660,16 +718,16 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_panel(const DieBatchT<T> batc
   const int k0 = kt * DB;                    // a full block: kt < nt - 1
   const int r0 = k0 + DB + blockIdx.x * DTHREADS;
   if (r0 >= n) return;                       // whole CTA, before any barrier
-  load_tile_ff<T>(SD, sys.E, n, n, n, k0, k0, 1);
+  load_tile_s(SD, stor(sys.E), n, n, n, k0, k0, 1);
   if (threadIdx.x < DB)
-    rinv[threadIdx.x] = to_ff(1.0 / re_(sys.E[size_t(k0 + threadIdx.x) * n + k0 + threadIdx.x]));
+    rinv[threadIdx.x] = to_ff(1.0 / re_(ff_to_t(stor(sys.E)[size_t(k0 + threadIdx.x) * n + k0 + threadIdx.x])));
   __syncthreads();
   const int r = r0 + threadIdx.x;
   if (r < n) {
     FT x[DB];
-    T* row = sys.E + size_t(r) * n + k0;
+    FT* row = stor(sys.E) + size_t(r) * n + k0;
 #pragma unroll
-    for (int c = 0; c < DB; ++c) x[c] = to_ff_t(row[c]);
+    for (int c = 0; c < DB; ++c) x[c] = row[c];
 #pragma unroll
     for (int c = 0; c < DB; ++c) {
       FA acc = ff_acc(x[c]);
@@ -678,7 +736,7 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_panel(const DieBatchT<T> batc
       x[c] = ff_scale(ff_renorm_t(acc), rinv[c]);
     }
 #pragma unroll
-    for (int c = 0; c < DB; ++c) row[c] = ff_to_t(x[c]);
+    for (int c = 0; c < DB; ++c) row[c] = x[c];
   }
 }
 
@@ -704,12 +762,12 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_update(const DieBatchT<T> bat
   const int it = kt + 1 + ii, jt = kt + 1 + jj;
   const int k0 = kt * DB;
   const int tid = threadIdx.x, tr = tid >> 3, tc = tid & 7;
-  const T* E = sys.E;
-  load_tile_ff<T>(SA, E, n, n, n, it * DB, k0, 0);            // L_ik
+  FT* E = stor(sys.E);
+  load_tile_s(SA, E, n, n, n, it * DB, k0, 0);                // L_ik
   for (int e = tid; e < DB * DB; e += DTHREADS) {             // SB[k][c] = conj(L_jk[c][k])
     const int k = e / DB, c = e % DB;
     const int R = jt * DB + c;
-    SB[k * DLD + c] = to_ff_t(R < n ? cconj(E[size_t(R) * n + k0 + k]) : T{});
+    SB[k * DLD + c] = R < n ? ff_conj(E[size_t(R) * n + k0 + k]) : FT{};
   }
   __syncthreads();
   FA acc[4] = {};
@@ -719,7 +777,7 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_update(const DieBatchT<T> bat
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int C = jt * DB + tc + 8 * b;
-      if (C < n && C <= R) sys.E[size_t(R) * n + C] = csub(E[size_t(R) * n + C], ff_value_t(acc[b]));
+      if (C < n && C <= R) E[size_t(R) * n + C] = ff_sub_acc_t(E[size_t(R) * n + C], acc[b]);
     }
   }
 }
@@ -756,7 +814,8 @@ static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const
   const size_t smem_w = 2 * DB * DLD * sizeof(T);
   {
     int rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_dielectric<T>), smem, ctx.device);
-    if (!rc) rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_dielectric_w<T>), smem_w, ctx.device);
+    if (!rc) rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_dielectric_w<T, true>), smem_w, ctx.device);
+    if (!rc) rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_dielectric_w<T, false>), smem_w, ctx.device);
     if (!rc) rc = set_max_dyn_smem(reinterpret_cast<const void*>(k_dielectric_zcol<T>), smem_w, ctx.device);
     if (rc) return rc;
   }
@@ -785,7 +844,10 @@ static int launch_dielectric(std::vector<DieSysT<T>>& sys, cudaStream_t s, const
       k_dielectric_zcol<T><<<g2, DTHREADS, smem_w, s>>>(batch);
       GW_LAUNCH_CHECK("k_dielectric_zcol");
     }
-    k_dielectric_w<T><<<dim3(unsigned(nb_), unsigned(ntmax)), DTHREADS, smem_w, s>>>(batch);
+    if (by_columns)
+      k_dielectric_w<T, true><<<dim3(unsigned(nb_), unsigned(ntmax)), DTHREADS, smem_w, s>>>(batch);
+    else
+      k_dielectric_w<T, false><<<dim3(unsigned(nb_), unsigned(ntmax)), DTHREADS, smem_w, s>>>(batch);
     GW_LAUNCH_CHECK("k_dielectric_w");
   }
   return GW_OK;
