@@ -186,6 +186,17 @@ __device__ __forceinline__ void decode_item(const TcLaunch& L, int64_t item, int
   bj += off;
 }
 
+// Rounds of a work item: the q's whole K range, except for the quadratic form, whose B operand
+// is the upper triangle of the form (k <= c): column block bj needs the K blocks 0 .. bj only.
+// nr_all: the rounds of the whole K range (the stride of the pre-split B tiles).
+template <bool QF, int CH>
+__device__ __forceinline__ int64_t item_rounds(const TcLaunch& L, int q, int bj, int64_t& nr_all) {
+  nr_all = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+  if (!QF) return nr_all;
+  const int64_t k = L.K[q] < int64_t(bj + 1) * TN ? L.K[q] : int64_t(bj + 1) * TN;
+  return ((k + CH - 1) / CH + SUB - 1) / SUB;
+}
+
 // byte offset of (row n, 16-byte chunk kc) in a K-major, 64-byte-swizzled tile
 __device__ __forceinline__ uint32_t sw64_off(int n, int kc) {
   return uint32_t((n >> 3) * 512 + (n & 7) * 64 + ((kc ^ ((n & 7) >> 1)) << 4));
@@ -322,7 +333,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       int q, j, bi, bj, kind;
       decode_item<QF>(L, item, q, j, bi, bj, kind);
-      const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+      int64_t nr_all;
+      const int64_t nr = item_rounds<QF, CH>(L, q, bj, nr_all);
       const float4* __restrict__ xc = reinterpret_cast<const float4*>(L.xT[q]) +
                                       size_t(bi) * size_t(L.kpad[q] / CH) * CH4 * TM + m;
       const int64_t r_first = int64_t((par + 2 - int(g0 & 1)) & 1);
@@ -443,9 +455,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
           int q, j, bi, bj, kind;
           decode_item<QF>(L, item, q, j, bi, bj, kind);
-          const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
-          const char* src =
-              L.bsp[q] + size_t(j) * L.bsp_jstride[q] + size_t(bj) * size_t(nr * SUB) * CHUNK_BYTES;
+          int64_t nr_all;
+          const int64_t nr = item_rounds<QF, CH>(L, q, bj, nr_all);
+          const char* src = L.bsp[q] + size_t(j) * L.bsp_jstride[q] +
+                            size_t(bj) * size_t(nr_all * SUB) * CHUNK_BYTES;
           for (int64_t r = 0; r < nr; ++r, ++g) {
             const int st = int(g % NSB);
             const uint64_t t = hp_now();
@@ -487,7 +500,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
           int q, j, bi, bj, kind;
           decode_item<QF>(L, item, q, j, bi, bj, kind);
-          const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+          int64_t nr_all;
+          const int64_t nr = item_rounds<QF, CH>(L, q, bj, nr_all);
           const float* wsrc = L.s[q] + size_t(j) * L.kpad[q];
           const char* xsrc = reinterpret_cast<const char*>(L.xT[q]) +
                              size_t(bi) * size_t(L.kpad[q] / CH) * CH4 * TM * 16;
@@ -537,8 +551,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint64_t hp0 = hp_now();
         uint64_t hp_wb = 0, hp_wa = 0, hp_wc = 0, hp_n = 0;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-          const int q = item_q(L, item);
-          const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+          int q, bj = 0;
+          if (QF) {
+            int j, bi, kind;
+            decode_item<QF>(L, item, q, j, bi, bj, kind);
+          } else {
+            q = item_q(L, item);
+          }
+          int64_t nr_all;
+          const int64_t nr = item_rounds<QF, CH>(L, q, bj, nr_all);
           const int64_t first = int64_t((mpar + 2 - uint32_t(g & 1)) & 1);
           const int64_t nown = nr > first ? (nr - first + 1) / 2 : 0;   // own rounds of the item
           for (int64_t i = 0; i < nown; ++i) {
@@ -634,22 +655,70 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float rs[TN];
     // the conversions go through volatile asm so that they stay next to their reductions
     // (converted all at once, 128 doubles would not fit beside the running sums)
+    // quadratic form: this row's c_p part of the item, x_p . (sums), compensated in FP32
+    // (the exact FP32 product as p + e by FMA, added by two-sum); qx: the item's x_p columns
+    float qs = 0.0f, qc = 0.0f;
+    const float4* qx = nullptr;
     auto fold = [&]() {
+      if constexpr (QF) {
+        // columns bj TN + i of row p in the chunk-major copy: float4 group i / 4 of the block
+        // sits at ((i / CH) (CH / 4) + (i % CH) / 4) TM float4 from the block's first one;
+        // eight loads in flight, then their 32 terms (the volatile adds keep the groups apart)
 #pragma unroll
-      for (int i = 0; i < TN; ++i) {
-        double d;
-        asm volatile("cvt.f64.f32 %0, %1;" : "=d"(d) : "f"(rs[i]));
-        atomicAdd(acc + size_t(i) * TM, d);
-        rs[i] = 0.0f;
+        for (int g8 = 0; g8 < TN / 32; ++g8) {
+          float4 xv[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int i = g8 * 32 + e * 4;
+            const float4* ptr = qx + size_t((i / CH) * (CH / 4) + (i % CH) / 4) * TM;
+            asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(xv[e].x), "=f"(xv[e].y), "=f"(xv[e].z), "=f"(xv[e].w)
+                         : "l"(ptr));
+          }
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float xs[4] = {xv[e].x, xv[e].y, xv[e].z, xv[e].w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const float a = rs[g8 * 32 + e * 4 + t], b = xs[t];
+              const float pr = __fmul_rn(a, b);
+              const float er = __fmaf_rn(a, b, -pr);
+              float sn;
+              asm volatile("add.rn.f32 %0, %1, %2;" : "=f"(sn) : "f"(qs), "f"(pr));
+              const float bp = __fsub_rn(sn, qs);
+              const float ds = __fadd_rn(__fsub_rn(qs, __fsub_rn(sn, bp)), __fsub_rn(pr, bp));
+              qc = __fadd_rn(qc, __fadd_rn(ds, er));
+              qs = sn;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < TN; ++i) rs[i] = 0.0f;
+      } else {
+#pragma unroll
+        for (int i = 0; i < TN; ++i) {
+          double d;
+          asm volatile("cvt.f64.f32 %0, %1;" : "=d"(d) : "f"(rs[i]));
+          atomicAdd(acc + size_t(i) * TM, d);
+          rs[i] = 0.0f;
+        }
       }
     };
     for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       int q, j, bi, bj, kind;
       decode_item<QF>(L, item, q, j, bi, bj, kind);
-      const int64_t nr = ((L.K[q] + CH - 1) / CH + SUB - 1) / SUB;
+      int64_t nr_all;
+      const int64_t nr = item_rounds<QF, CH>(L, q, bj, nr_all);
       const int nb = L.nb[q];
+      if (QF) {
+        qs = 0.0f;
+        qc = 0.0f;
+        qx = reinterpret_cast<const float4*>(L.xT[q] + size_t(bi) * size_t(L.kpad[q] / CH) * CH * TM) +
+             size_t(bj) * (TN / 4) * TM + r;
+      } else {
 #pragma unroll 8
-      for (int i = 0; i < TN; ++i) acc[size_t(i) * TM] = 0.0;
+        for (int i = 0; i < TN; ++i) acc[size_t(i) * TM] = 0.0;
+      }
 #pragma unroll
       for (int i = 0; i < TN; ++i) rs[i] = 0.0f;
       bool sum_empty = true;
@@ -698,21 +767,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (stop) break;
       g0 += uint64_t(nr);
       if (!sum_empty) fold();
-      __threadfence();
       if (QF) {
-        // c_p += sum_c X[p][c] Y[p][c] over this tile's columns (X = the A rows themselves)
+        // c_p += sum_c x_pc (x U)_pc over this tile's columns c (U: the upper triangle of the
+        // form, so that x U x^T is the whole form)
         const int64_t p = int64_t(bi) * TM + r;
-        // X[p][k] for k = bj * TN + i, read from the chunk-major copy
-        const float* xb = L.xT[q] + size_t(bi) * size_t(L.kpad[q] / CH) * CH * TM + size_t(r) * 4;
-        double part = 0.0;
-#pragma unroll 8
-        for (int i = 0; i < TN; ++i) {
-          const int64_t k = int64_t(bj) * TN + i;
-          const float xv = __ldg(xb + size_t((k / CH) * (CH / 4) + (k % CH) / 4) * TM * 4 + (k & 3));
-          part = fma(double(xv), acc[size_t(i) * TM], part);
-        }
-        if (p < L.nrow[q]) atomicAdd(L.cq[q] + size_t(j) * L.nrow[q] + p, part);
-      } else if (MODE == 2) {
+        if (p < L.nrow[q]) atomicAdd(L.cq[q] + size_t(j) * L.nrow[q] + p, double(qs) + double(qc));
+        continue;
+      }
+      __threadfence();
+      if (MODE == 2) {
         // real projections: P_IJ = -G_IJ (real symmetric)
         const int I = bi * TM + r;
         double2* P = L.P[q] + size_t(j) * nb * nb;
@@ -960,10 +1023,12 @@ __global__ void k_prep_xpad(const float* __restrict__ x, int64_t nrow, int ncol,
   }
 }
 
-// B operand of the quadratic form for one frequency: the real symmetric form R of the
-// Hermitian W^c (R[2I+a][2J+b] = Re W_IJ for a = b, -Im W_IJ for (a,b) = (0,1), Im W_IJ for
-// (1,0)), or R = Re W^c for real projections (REAL), split and swizzled like the
-// polarization's B tiles, [c block][k chunk].
+// B operand of the quadratic form for one frequency: the upper triangle U of the real form R
+// of W^c (R[2I+a][2J+b] = Re W_IJ for a = b, -Im W_IJ for (a,b) = (0,1), Im W_IJ for (1,0)), or
+// of R = Re W^c for real projections (REAL): U_kk = R_kk, U_kc = R_kc + R_ck for k < c, 0 below
+// the diagonal, so that x U x^T = x R x^T for every real row x (the form sees only the
+// symmetric part of R) with about half the products. Split and swizzled like the
+// polarization's B tiles, [c block][k chunk]; chunks below the diagonal block are zero.
 template <bool BF16, bool REAL>
 __global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W0, int nb,
                                                    int64_t nch, char* __restrict__ bsp0,
@@ -987,13 +1052,20 @@ __global__ void __launch_bounds__(128) k_prep_quad(const double2* __restrict__ W
     for (int e = 0; e < EPC; ++e) {
       const int64_t k = ch * CH + kc * EPC + e;
       float r = 0.0f;
-      if (c < ncol && k < ncol) {
+      if (c < ncol && k <= c) {
         if (REAL) {
-          r = float(W[size_t(k) * nb + J].x);
+          double u = W[size_t(k) * nb + J].x;
+          if (k < c) u += W[size_t(J) * nb + k].x;
+          r = float(u);
         } else {
           const int I = int(k >> 1), a = int(k & 1);
           const double2 w = W[size_t(I) * nb + J];
-          r = float(a == b ? w.x : (a == 0 ? -w.y : w.y));
+          double u = a == b ? w.x : (a == 0 ? -w.y : w.y);
+          if (k < c) {                                  // R_ck = R[2J+b][2I+a]
+            const double2 wt = W[size_t(J) * nb + I];
+            u += a == b ? wt.x : (b == 0 ? -wt.y : wt.y);
+          }
+          r = float(u);
         }
       }
       v[e] = r;
@@ -1147,9 +1219,11 @@ static int launch_tc_k(const TcLaunch& L, unsigned grid, double* acc64, cudaStre
 template <int MODE>
 static int launch_tc(const TcLaunch& L, bool bf, int nsb, unsigned grid, double* acc64,
                      cudaStream_t s, const DeviceCtx& ctx) {
-  if (MODE != 1 && nsb == 6)
-    return bf ? launch_tc_k<true, MODE, 6>(L, grid, acc64, s, ctx)
-              : launch_tc_k<false, MODE, 6>(L, grid, acc64, s, ctx);
+  if constexpr (MODE != 1) {
+    if (nsb == 6)
+      return bf ? launch_tc_k<true, MODE, 6>(L, grid, acc64, s, ctx)
+                : launch_tc_k<false, MODE, 6>(L, grid, acc64, s, ctx);
+  }
   return bf ? launch_tc_k<true, MODE, 4>(L, grid, acc64, s, ctx)
             : launch_tc_k<false, MODE, 4>(L, grid, acc64, s, ctx);
 }

@@ -170,6 +170,31 @@ def test_tc_pair_coefficients(gw, prec, nb):
     assert err <= PAIR_BOUND[prec], err
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("real", [False, True])
+def test_tc_pair_coefficients_any_w(gw, prec, real):
+    """The tensor-core form runs on the upper triangle of the symmetric part of the real form
+    of W^c; c_p = Re m_p^H W m_p sees only that part, so a W that is neither Hermitian nor
+    symmetric (random entries, N_b = 150: three column blocks of the complex form, the last
+    one ragged) gives the same c as the oracle's full double sum."""
+    rng = np.random.default_rng(150)
+    nb, npair, nw = 150, 333, 3
+    W = rng.standard_normal((nw, nb, nb)) + 1j * rng.standard_normal((nw, nb, nb))
+    if real:
+        Ms = rng.standard_normal((npair, nb)).astype(np.float32)
+        Mo = Ms.astype(np.float64).astype(np.complex128)
+        Wo = W.real.astype(np.complex128)
+    else:
+        Ms = (rng.standard_normal((npair, nb)) + 1j * rng.standard_normal((npair, nb))).astype(np.complex64)
+        Mo = Ms.astype(np.complex128)
+        Wo = W
+    c = gw.sigma_pair_coeffs([T(Ms)], [T(Wo)], precision=prec)[0]
+    gw.check()
+    ref = OE.pair_coefficients(Mo, Wo)
+    err = float(np.abs(c.cpu().numpy() - ref).max() / np.abs(ref).max())
+    assert err <= PAIR_BOUND[prec], err
+
+
 @pytest.mark.parametrize("prec", ["tf32x3"])
 def test_tc_sigma_end_to_end_small(gw, prec):
     """Sigma^c through the split-precision P and pair coefficients against the all-FP64
