@@ -33,6 +33,7 @@ struct LmWarpSmem {
   double Ld[LM_NPACK];
   double g[LM_MAXP];
   double b[LM_MAXP];
+  double dinv[LM_MAXP];     // reciprocals of the factor's diagonal
   double th[LM_MAXP];
   int flag;
 };
@@ -70,9 +71,12 @@ __device__ __forceinline__ double warp_cost(const double* om, const double2* yl,
   return 0.5 * warp_sum(c);
 }
 
+// NPOLE: poles of the model (a template parameter, so that the parameter vectors and the
+// loops over them stay in registers)
+template <int NPOLE>
 __global__ void __launch_bounds__(32) k_lm_warp(int ncurve, int nw, OmegaArr om,
                                                 const double2* __restrict__ sigma,
-                                                const double* __restrict__ sign, int npole,
+                                                const double* __restrict__ sign,
                                                 const double* __restrict__ theta_init,
                                                 double* __restrict__ params,
                                                 double* __restrict__ cost_out,
@@ -83,8 +87,9 @@ __global__ void __launch_bounds__(32) k_lm_warp(int ncurve, int nw, OmegaArr om,
   const int lane = threadIdx.x;
   if (cidx >= ncurve) return;
   const double2* y = sigma + size_t(cidx) * nw;
-  const int P = 4 * npole;
-  const int NP = P * (P + 1) / 2;
+  constexpr int npole = NPOLE;
+  constexpr int P = 4 * npole;
+  constexpr int NP = P * (P + 1) / 2;
   double2 yl[2];
   for (int h = 0; h < 2; ++h) {
     const int j = lane + 32 * h;
@@ -99,11 +104,22 @@ __global__ void __launch_bounds__(32) k_lm_warp(int ncurve, int nw, OmegaArr om,
     }
   }
   __syncwarp();
-  double th[LM_MAXP], thn[LM_MAXP];
+  double th[P], thn[P];
   for (int k = 0; k < P; ++k) th[k] = S.th[k];
   const double cscale = 0.5 * warp_sum(yl[0].x * yl[0].x + yl[0].y * yl[0].y +
                                        yl[1].x * yl[1].x + yl[1].y * yl[1].y);
   double C = warp_cost(om.v, yl, nw, npole, th);
+  // the packed entries e = lane + 32 h of A this lane sums: row ea[h], column eb[h]
+  constexpr int EPL = (NP + 31) / 32;
+  int ea[EPL], eb[EPL];
+#pragma unroll
+  for (int h = 0; h < EPL; ++h) {
+    const int e = lane + 32 * h;
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= e) ++a;
+    ea[h] = a;
+    eb[h] = e - a * (a + 1) / 2;
+  }
   double mu = -1.0;
   int it = 0, st = 1;
   for (; it < LM_MAXIT; ++it) {
@@ -140,11 +156,11 @@ __global__ void __launch_bounds__(32) k_lm_warp(int ncurve, int nw, OmegaArr om,
     }
     __syncwarp();
     // A (packed lower) and g, summed over points
-    for (int e = lane; e < NP; e += 32) {
-      int a = int((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-      while ((a + 1) * (a + 2) / 2 <= e) ++a;
-      while (a * (a + 1) / 2 > e) --a;
-      const int bcol = e - a * (a + 1) / 2;
+#pragma unroll
+    for (int h = 0; h < EPL; ++h) {
+      const int e = lane + 32 * h;
+      if (e >= NP) break;
+      const int a = ea[h], bcol = eb[h];
       double v = 0.0;
       for (int j = 0; j < nw; ++j) v += S.rowR[j][a] * S.rowR[j][bcol] + S.rowI[j][a] * S.rowI[j][bcol];
       S.A[e] = v;
@@ -184,14 +200,16 @@ __global__ void __launch_bounds__(32) k_lm_warp(int ncurve, int nw, OmegaArr om,
           double d = S.Ld[jc * (jc + 1) / 2 + jc];
           for (int k = 0; k < jc; ++k) d -= S.Ld[jc * (jc + 1) / 2 + k] * S.Ld[jc * (jc + 1) / 2 + k];
           if (!(d > 0.0)) S.flag = 0;
-          S.Ld[jc * (jc + 1) / 2 + jc] = d > 0.0 ? sqrt(d) : 1.0;
+          const double r = d > 0.0 ? sqrt(d) : 1.0;
+          S.Ld[jc * (jc + 1) / 2 + jc] = r;
+          S.dinv[jc] = 1.0 / r;
         }
         __syncwarp();
         const int i = jc + 1 + lane;
         if (i < P) {
           double v = S.Ld[i * (i + 1) / 2 + jc];
           for (int k = 0; k < jc; ++k) v -= S.Ld[i * (i + 1) / 2 + k] * S.Ld[jc * (jc + 1) / 2 + k];
-          S.Ld[i * (i + 1) / 2 + jc] = v / S.Ld[jc * (jc + 1) / 2 + jc];
+          S.Ld[i * (i + 1) / 2 + jc] = v * S.dinv[jc];
         }
         __syncwarp();
       }
@@ -199,7 +217,7 @@ __global__ void __launch_bounds__(32) k_lm_warp(int ncurve, int nw, OmegaArr om,
       if (ok) {
         // L z = b by column sweeps, then L^T x = z
         for (int k = 0; k < P; ++k) {
-          const double zk = S.b[k] / S.Ld[k * (k + 1) / 2 + k];
+          const double zk = S.b[k] * S.dinv[k];
           __syncwarp();
           const int i = k + 1 + lane;
           if (i < P) S.b[i] -= S.Ld[i * (i + 1) / 2 + k] * zk;
@@ -207,7 +225,7 @@ __global__ void __launch_bounds__(32) k_lm_warp(int ncurve, int nw, OmegaArr om,
           __syncwarp();
         }
         for (int k = P - 1; k >= 0; --k) {
-          const double xk = S.b[k] / S.Ld[k * (k + 1) / 2 + k];
+          const double xk = S.b[k] * S.dinv[k];
           __syncwarp();
           if (lane < k) S.b[lane] -= S.Ld[k * (k + 1) / 2 + lane] * xk;
           if (lane == 0) S.b[k] = xk;
@@ -255,8 +273,18 @@ int launch_lm(int ncurve, int nw, const OmegaArr& om, const double* sigma, const
               int* status, int keep_better, cudaStream_t s) {
   if (ncurve == 0) return GW_OK;
   if (nw > LM_WMAXNW) return set_error(GW_EINVAL, "the fit takes at most %d frequencies", LM_WMAXNW);
-  k_lm_warp<<<ncurve, 32, 0, s>>>(ncurve, nw, om, reinterpret_cast<const double2*>(sigma), sign,
-                                  npole, theta_init, params, cost, iters, status, keep_better);
+  const double2* y = reinterpret_cast<const double2*>(sigma);
+  auto go = [&](auto kern) {
+    kern<<<ncurve, 32, 0, s>>>(ncurve, nw, om, y, sign, theta_init, params, cost, iters, status,
+                               keep_better);
+  };
+  switch (npole) {
+    case 1: go(k_lm_warp<1>); break;
+    case 2: go(k_lm_warp<2>); break;
+    case 3: go(k_lm_warp<3>); break;
+    case 4: go(k_lm_warp<4>); break;
+    default: go(k_lm_warp<5>); break;
+  }
   GW_LAUNCH_CHECK("k_lm_warp");
   return GW_OK;
 }
