@@ -143,10 +143,18 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host,
  *   fp64_waves          GW_FP64: the K splits fill at least this many waves of CTAs; 0 means 4.
  *   herk_events         NULL, or n_herk_events pairs of cudaEvent_t (created by the caller,
  *                       layout [start, end] per pair): the call records the pair around each
- *                       of its first n_herk_events HERK launches on `stream` (the dominant
- *                       kernel alone, without the per-q preparation);
+ *                       of its first n_herk_events HERK launches, on the stream the HERK runs
+ *                       on (the dominant kernel alone, without the per-q preparation);
  *   n_herk_events       the number of pairs in herk_events;
- *   herk_launches_out   NULL, or (host) the number of HERK launches of the call.
+ *   herk_launches_out   NULL, or (host) the number of HERK launches of the call;
+ *   serial_prep         split-precision paths with more than one group: nonzero runs each
+ *                       group's preparation (weights, operand copies) on `stream` before its
+ *                       HERK launch; 0 (default) prepares group g + 1 on a low-priority stream
+ *                       of the library while the HERK of group g runs on a high-priority one
+ *                       (the HERK's last, partial wave leaves SMs idle), with two workspace
+ *                       slots. Both streams are forked from `stream` at entry and joined to it
+ *                       before the call returns: the call is ordered on `stream` either way,
+ *                       and a capture of `stream` into a CUDA graph takes both in.
  * gw_polarization_workspace_ex gives the workspace for the same options (group_items_per_sm
  * and fp64_waves change it). Errors: GW_EINVAL for b_stages other than 0, 4 or 6, negative
  * counts. */
@@ -158,6 +166,7 @@ typedef struct gw_pol_options {
   void* const* herk_events;
   int n_herk_events;
   int* herk_launches_out;
+  int serial_prep;
 } gw_pol_options;
 size_t gw_polarization_workspace_ex(int nq, const int64_t* K_host, const int* nb_host, int nw,
                                     int precision, const gw_pol_options* options);

@@ -62,7 +62,7 @@ class PolOptions(ctypes.Structure):
     """gw_pol_options (include/gw.h)."""
     _fields_ = [("accumulate", _i32), ("group_items_per_sm", _i32), ("b_stages", _i32),
                 ("fp64_waves", _i32), ("herk_events", _P(_vp)), ("n_herk_events", _i32),
-                ("herk_launches_out", _P(_i32))]
+                ("herk_launches_out", _P(_i32)), ("serial_prep", _i32)]
 
 
 _sig("gw_polarization_workspace_ex", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32, _P(PolOptions))
@@ -263,6 +263,7 @@ def _pol_options(options):
     o.group_items_per_sm = int(options.get("group_items_per_sm", 0))
     o.b_stages = int(options.get("b_stages", 0))
     o.fp64_waves = int(options.get("fp64_waves", 0))
+    o.serial_prep = int(bool(options.get("serial_prep", False)))
     keep = []
     evs = options.get("herk_events")
     if evs:
@@ -293,7 +294,8 @@ def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=No
                  options=None):
     """P[q] = sum_t w_tj M_tI conj(M_tJ) for each q (complex128 [nw][N_b][N_b]).
     options: None or a dict of gw_pol_options fields (accumulate, group_items_per_sm,
-    b_stages, fp64_waves, herk_events = [(start, end), ...] torch.cuda.Event pairs); after the
+    b_stages, fp64_waves, serial_prep, herk_events = [(start, end), ...] torch.cuda.Event
+    pairs); after the
     call options["herk_launches"] holds the number of HERK launches."""
     prec = PRECISIONS.get(precision, precision)
     om, nw = _om(omega)

@@ -109,6 +109,7 @@ int resolve_pol_options(const gw_pol_options* o, PolOpts* out) {
   if (o->group_items_per_sm) out->group_items_per_sm = o->group_items_per_sm;
   if (o->b_stages) out->b_stages = o->b_stages;
   if (o->fp64_waves) out->fp64_waves = o->fp64_waves;
+  out->serial_prep = o->serial_prep != 0;
   out->events = o->herk_events;
   out->n_events = o->n_herk_events;
   return GW_OK;

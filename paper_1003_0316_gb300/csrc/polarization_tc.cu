@@ -51,6 +51,7 @@
 #include <vector>
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 #include <cuda_bf16.h>
 
 #include "gw_internal.cuh"
@@ -1182,13 +1183,10 @@ static void tc_groups(int nq, const int64_t* K, const int* nb, int nw, int sm,
   start.push_back(nq);
 }
 
-size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision,
-                        const PolOpts& o) {
-  int sm = 152, dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
-  cudaGetLastError();
-  std::vector<int> start;
-  tc_groups(nq, K, nb, nw, sm, o.group_items_per_sm, start);
+// the workspace of the largest group (the order of pol_tc's slices: per q the weights, the
+// chunk-major copy, the pre-split tiles and the three-product tiles)
+static size_t group_max_bytes(const std::vector<int>& start, const int64_t* K, const int* nb,
+                              int nw, int precision) {
   size_t group_max = 0;
   for (size_t g = 0; g + 1 < start.size(); ++g) {
     size_t b = 0;
@@ -1198,7 +1196,59 @@ size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int pre
     }
     group_max = std::max(group_max, b);
   }
-  return ws_round(size_t(sm) * TN * TM * sizeof(double)) + group_max;
+  return group_max;
+}
+
+// the preparation of the next group overlaps the HERK of the current one (two slots)
+static bool overlapped(const std::vector<int>& start, const PolOpts& o) {
+  return start.size() > 2 && !o.serial_prep;
+}
+
+size_t pol_tc_workspace(int nq, const int64_t* K, const int* nb, int nw, int precision,
+                        const PolOpts& o) {
+  int sm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  std::vector<int> start;
+  tc_groups(nq, K, nb, nw, sm, o.group_items_per_sm, start);
+  const size_t group_max = group_max_bytes(start, K, nb, nw, precision);
+  return ws_round(size_t(sm) * TN * TM * sizeof(double)) + (overlapped(start, o) ? 2 : 1) * group_max;
+}
+
+// Streams of the overlapped preparation. A q of the mesh workload is one group of 640 work
+// items, 4.2 waves on 152 SMs: during the HERK's last, partial wave most SMs are idle. With
+// more than one group, the weights and operand copies of group g + 1 (bound by HBM) therefore
+// run on a low-priority stream while the HERK of group g runs on a high-priority one; the
+// priorities make the HERK's CTAs (one per SM, each holding the whole register file) take the
+// SMs first whenever both are ready, and the copies fill the SMs the HERK has left. Two
+// workspace slots alternate between groups; the preparation of group g waits for the HERK of
+// group g - 2, the last reader of its slot. The call's stream is forked to the two streams at
+// entry and joined again at exit, so the call keeps the ordering of one stream.
+struct PolStreams {
+  cudaStream_t herk = nullptr, prep = nullptr;
+  cudaEvent_t entry = nullptr, exit_h = nullptr, exit_p = nullptr;
+  cudaEvent_t prep_done[2] = {nullptr, nullptr}, herk_done[2] = {nullptr, nullptr};
+};
+static std::mutex g_ps_mu;           // held while a call enqueues its work on the streams
+static PolStreams g_ps[64];
+static bool g_ps_ok[64];
+
+static int pol_streams(int dev, PolStreams** out) {   // with g_ps_mu held
+  if (dev < 0 || dev >= 64) return set_error(GW_EINVAL, "device id %d out of range", dev);
+  if (!g_ps_ok[dev]) {
+    PolStreams p;
+    int least = 0, greatest = 0;
+    GW_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    GW_CUDA_TRY(cudaStreamCreateWithPriority(&p.herk, cudaStreamNonBlocking, greatest));
+    GW_CUDA_TRY(cudaStreamCreateWithPriority(&p.prep, cudaStreamNonBlocking, least));
+    cudaEvent_t* evs[] = {&p.entry,        &p.exit_h,       &p.exit_p,      &p.prep_done[0],
+                          &p.prep_done[1], &p.herk_done[0], &p.herk_done[1]};
+    for (cudaEvent_t* e : evs) GW_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    g_ps[dev] = p;
+    g_ps_ok[dev] = true;
+  }
+  *out = &g_ps[dev];
+  return GW_OK;
 }
 
 static size_t herk_smem(int nsb) { return size_t(nsb) * STAGE_BYTES + NWS * WSLOT_BYTES + 1024; }
@@ -1228,26 +1278,20 @@ static int launch_tc(const TcLaunch& L, bool bf, int nsb, unsigned grid, double*
             : launch_tc_k<false, MODE, 4>(L, grid, acc64, s, ctx);
 }
 
-int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
-           bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx,
-           PolOpts& o) {
+// the groups of pol_tc: preparation on sp, HERK and combination on sh (the same stream unless
+// ps is given: then slot g mod 2 of the workspace and the events of ps order the two)
+static int pol_tc_groups(const std::vector<int>& start, const PolQ* qs, double pref, int nw,
+                         const OmegaArr& om, int precision, bool real, WsCursor& cur,
+                         size_t group_base, size_t group_max, double* acc64, PolStreams* ps,
+                         cudaStream_t sp, cudaStream_t sh, const DeviceCtx& ctx, PolOpts& o) {
   const bool bf = precision == GW_BF16X3;
   const int cpb = real ? 1 : 2;          // real operand columns per basis function
-  WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
-  double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
-  if (!acc64) return set_error(GW_EWORKSPACE, "internal: tensor-core workspace too small");
-  const size_t group_base = cur.used;
-  std::vector<int64_t> Ks(nq);
-  std::vector<int> nbs(nq);
-  for (int q = 0; q < nq; ++q) {
-    Ks[q] = qs[q].K;
-    nbs[q] = qs[q].nb;
-  }
-  std::vector<int> start;
-  tc_groups(nq, Ks.data(), nbs.data(), nw, ctx.sm_count, o.group_items_per_sm, start);
   for (size_t g = 0; g + 1 < start.size(); ++g) {
     const int q0 = start[g], n = start[g + 1] - start[g];
-    cur.used = group_base;               // the previous group's launch is ordered before this one
+    const int slot = ps ? int(g % 2) : 0;
+    // one slot: the previous group's launch is ordered before this group's preparation
+    cur.used = group_base + size_t(slot) * group_max;
+    if (ps && g >= 2) GW_CUDA_TRY(cudaStreamWaitEvent(sp, ps->herk_done[slot], 0));
     TcLaunch L{};
     L.nq = n;
     L.nw = nw;
@@ -1273,7 +1317,7 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
       if (kpad > 0) {
         if (!sw || !xT || !bsp) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
         int64_t blocks = std::min<int64_t>((kpad + 255) / 256, int64_t(ctx.sm_count) * 8);
-        k_abs_weights_f32<<<unsigned(blocks), 256, 0, s>>>(Q.K, kpad, Q.delta, Q.dbar, Q.f, pref,
+        k_abs_weights_f32<<<unsigned(blocks), 256, 0, sp>>>(Q.K, kpad, Q.delta, Q.dbar, Q.f, pref,
                                                            nw, om, sw, ctx.status);
         GW_LAUNCH_CHECK("k_abs_weights_f32");
         const dim3 pg(static_cast<unsigned>(nch), static_cast<unsigned>(nbi));
@@ -1281,18 +1325,18 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
         if (p3) {
           const dim3 pg3(static_cast<unsigned>(nch), static_cast<unsigned>(lay.nbb));
           if (bf)
-            k_prep_tc3<true><<<pg3, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, Q.nb,
+            k_prep_tc3<true><<<pg3, 128, 0, sp>>>(static_cast<const float*>(Q.M), Q.K, Q.nb,
                                                  lay.nbb, kpad, nch, xT, bsp);
           else
-            k_prep_tc3<false><<<pg3, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, Q.nb,
+            k_prep_tc3<false><<<pg3, 128, 0, sp>>>(static_cast<const float*>(Q.M), Q.K, Q.nb,
                                                   lay.nbb, kpad, nch, xT, bsp);
           GW_LAUNCH_CHECK("k_prep_tc3");
         } else {
           if (bf)
-            k_prep_tc<true><<<pg, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
+            k_prep_tc<true><<<pg, 128, 0, sp>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
                                                kpad, nch, xT, bsp);
           else
-            k_prep_tc<false><<<pg, 128, 0, s>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
+            k_prep_tc<false><<<pg, 128, 0, sp>>>(static_cast<const float*>(Q.M), Q.K, cpb * Q.nb,
                                                 kpad, nch, xT, bsp);
           GW_LAUNCH_CHECK("k_prep_tc");
         }
@@ -1313,25 +1357,74 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
       item += int64_t(L.ntile[i]) * nw;
     }
     L.item0[n] = item;
-    if (item == 0) continue;
-    unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
-    int rc = record_herk_event(o, o.launches, false, s);
-    if (rc) return rc;
-    rc = real ? launch_tc<2>(L, bf, o.b_stages, grid, acc64, s, ctx)
-              : launch_tc<0>(L, bf, o.b_stages, grid, acc64, s, ctx);
-    if (rc) return rc;
-    if ((rc = record_herk_event(o, o.launches, true, s))) return rc;
-    ++o.launches;
+    if (ps) {                            // the HERK of this group after its preparation
+      GW_CUDA_TRY(cudaEventRecord(ps->prep_done[slot], sp));
+      GW_CUDA_TRY(cudaStreamWaitEvent(sh, ps->prep_done[slot], 0));
+    }
+    if (item > 0) {
+      unsigned grid = unsigned(std::min<int64_t>(item, ctx.sm_count));
+      int rc = record_herk_event(o, o.launches, false, sh);
+      if (rc) return rc;
+      rc = real ? launch_tc<2>(L, bf, o.b_stages, grid, acc64, sh, ctx)
+                : launch_tc<0>(L, bf, o.b_stages, grid, acc64, sh, ctx);
+      if (rc) return rc;
+      if ((rc = record_herk_event(o, o.launches, true, sh))) return rc;
+      ++o.launches;
+    }
     for (int i = 0; i < n; ++i) {
       const int64_t tot = int64_t(nw) * L.nb[i] * L.nb[i];
       if (!L.prod3[i] || tot == 0) continue;
       const unsigned blocks = unsigned(std::min<int64_t>((tot + 255) / 256, int64_t(ctx.sm_count) * 8));
-      k_prod3_combine<<<blocks, 256, 0, s>>>(L.P[i], L.g3[i], L.nb[i], L.nbj[i] * TM, nw,
+      k_prod3_combine<<<blocks, 256, 0, sh>>>(L.P[i], L.g3[i], L.nb[i], L.nbj[i] * TM, nw,
                                              L.accumulate);
       GW_LAUNCH_CHECK("k_prod3_combine");
     }
+    if (ps) GW_CUDA_TRY(cudaEventRecord(ps->herk_done[slot], sh));   // the slot is free again
   }
   return GW_OK;
+}
+
+
+int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int precision,
+           bool real, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceCtx& ctx,
+           PolOpts& o) {
+  WsCursor cur{static_cast<char*>(ws), ws_bytes, 0};
+  double* acc64 = static_cast<double*>(cur.take(size_t(ctx.sm_count) * TN * TM * sizeof(double)));
+  if (!acc64) return set_error(GW_EWORKSPACE, "internal: tensor-core workspace too small");
+  const size_t group_base = cur.used;
+  std::vector<int64_t> Ks(nq);
+  std::vector<int> nbs(nq);
+  for (int q = 0; q < nq; ++q) {
+    Ks[q] = qs[q].K;
+    nbs[q] = qs[q].nb;
+  }
+  std::vector<int> start;
+  tc_groups(nq, Ks.data(), nbs.data(), nw, ctx.sm_count, o.group_items_per_sm, start);
+  const size_t group_max = group_max_bytes(start, Ks.data(), nbs.data(), nw, precision);
+  const bool ovl = overlapped(start, o);
+  cudaStream_t sp = s, sh = s;         // preparation and HERK streams
+  std::unique_lock<std::mutex> lk(g_ps_mu, std::defer_lock);
+  PolStreams* ps = nullptr;
+  if (ovl) {
+    lk.lock();
+    int rc = pol_streams(ctx.device, &ps);
+    if (rc) return rc;
+    GW_CUDA_TRY(cudaEventRecord(ps->entry, s));
+    GW_CUDA_TRY(cudaStreamWaitEvent(ps->herk, ps->entry, 0));
+    GW_CUDA_TRY(cudaStreamWaitEvent(ps->prep, ps->entry, 0));
+    sp = ps->prep;
+    sh = ps->herk;
+  }
+  int rc = pol_tc_groups(start, qs, pref, nw, om, precision, real, cur, group_base, group_max,
+                         acc64, ovl ? ps : nullptr, sp, sh, ctx, o);
+  if (ovl) {                           // join both streams into the call's stream (errors too)
+    cudaError_t e = cudaEventRecord(ps->exit_h, sh);
+    if (e == cudaSuccess) e = cudaEventRecord(ps->exit_p, sp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ps->exit_h, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ps->exit_p, 0);
+    if (e != cudaSuccess && rc == GW_OK) rc = cuda_error(e, "joining the polarization streams");
+  }
+  return rc;
 }
 
 // ------------------------------------------------------------ pair coefficients

@@ -2,7 +2,9 @@
 // device memory together (the 64-q uneven mesh workload holds ~470 GB of projections): every q
 // goes to one wave, and per wave the projections, the polarization workspace and the outputs
 // must fit in a byte budget. First-fit decreasing: q points in order of decreasing footprint,
-// each into the first wave with room (a new wave when none has). Host code only.
+// each into the first wave with room (a new wave when none has); a wave's bytes are evaluated
+// for its whole q list, since the workspace of one call is not a sum over its q. Host code
+// only.
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -19,31 +21,49 @@ static size_t pol_ws(int nq, const int64_t* K, const int* nb, int nw, int precis
 int plan_waves(int nq, const int64_t* K, const int* nb, int nw, int precision, size_t budget,
                int* wave_of_q, int* nwaves) {
   const size_t elem = precision == GW_FP64 ? 16 : 8;
-  const int64_t K0 = 0;
-  const int nb0 = 1;
-  // workspace that a launch needs once, whatever its q points (per-SM scratch)
-  const size_t shared = pol_ws(1, &K0, &nb0, nw, precision);
+  // projections and outputs of one q (plus the alignment of their allocations)
+  std::vector<size_t> data(nq);
+  for (int q = 0; q < nq; ++q)
+    data[q] = size_t(K[q]) * size_t(nb[q]) * elem + size_t(nw) * size_t(nb[q]) * size_t(nb[q]) * 16 +
+              3 * 256;
+  // the bytes of a wave: its data and the workspace of one call over its q in increasing order
+  // (the workspace is not additive over q: groups, and two slots when there are several)
+  auto cost = [&](const std::vector<int>& qs) {
+    std::vector<int64_t> Kw;
+    std::vector<int> nbw;
+    size_t b = 0;
+    for (int q : qs) {
+      Kw.push_back(K[q]);
+      nbw.push_back(nb[q]);
+      b += data[q];
+    }
+    return b + pol_ws(int(qs.size()), Kw.data(), nbw.data(), nw, precision);
+  };
   std::vector<size_t> foot(nq);
   for (int q = 0; q < nq; ++q) {
-    const size_t ws = pol_ws(1, &K[q], &nb[q], nw, precision);
-    foot[q] = size_t(K[q]) * size_t(nb[q]) * elem + (ws > shared ? ws - shared : 0) +
-              size_t(nw) * size_t(nb[q]) * size_t(nb[q]) * 16 + 3 * 256;
-    if (foot[q] + shared > budget)
+    foot[q] = cost({q});
+    if (foot[q] > budget)
       return set_error(GW_EINVAL, "q=%d alone needs %zu bytes, above the budget of %zu", q,
-                       foot[q] + shared, budget);
+                       foot[q], budget);
   }
   std::vector<int> order(nq);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return foot[a] > foot[b]; });
-  std::vector<size_t> used;
+  std::vector<std::vector<int>> waves;
   for (int q : order) {
-    int w = 0;
-    while (w < int(used.size()) && used[w] + foot[q] > budget) ++w;
-    if (w == int(used.size())) used.push_back(shared);
-    used[w] += foot[q];
-    wave_of_q[q] = w;
+    size_t w = 0;
+    for (; w < waves.size(); ++w) {
+      std::vector<int> t = waves[w];
+      t.insert(std::upper_bound(t.begin(), t.end(), q), q);
+      if (cost(t) <= budget) {
+        waves[w] = t;
+        break;
+      }
+    }
+    if (w == waves.size()) waves.push_back({q});
+    wave_of_q[q] = int(w);
   }
-  *nwaves = int(used.size());
+  *nwaves = int(waves.size());
   return GW_OK;
 }
 

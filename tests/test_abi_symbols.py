@@ -81,18 +81,32 @@ def test_extrapolar_and_real_entry_points_reject_bad_arguments_without_gpu():
     assert rc == 1                       # fewer than 4 frequency nodes
 
 
+class _PolOpt(ctypes.Structure):
+    _fields_ = [("accumulate", ctypes.c_int), ("group_items_per_sm", ctypes.c_int),
+                ("b_stages", ctypes.c_int), ("fp64_waves", ctypes.c_int),
+                ("herk_events", ctypes.c_void_p), ("n_herk_events", ctypes.c_int),
+                ("herk_launches_out", ctypes.c_void_p), ("serial_prep", ctypes.c_int)]
+
+
 def test_polarization_workspace_holds_one_group_of_large_q():
     """The tensor-core polarization prepares and launches q points group by group: eight q
-    that each fill the GPU need the workspace of one, while small q share a group."""
+    that each fill the GPU need two groups' slots of workspace (the next group is prepared
+    while the HERK of the current one runs), one with serial_prep; small q share a group."""
     lib = _lib()
     lib.gw_polarization_workspace.restype = ctypes.c_size_t
+    lib.gw_polarization_workspace_ex.restype = ctypes.c_size_t
     GW_BF16X3 = 2
     big = lambda n: ((ctypes.c_int64 * n)(*([409600] * n)), (ctypes.c_int * n)(*([600] * n)))
+    K0, nb0 = (ctypes.c_int64 * 1)(0), (ctypes.c_int * 1)(1)
     K1, nb1 = big(1)
     K8, nb8 = big(8)
+    w0 = lib.gw_polarization_workspace(1, K0, nb0, 16, GW_BF16X3)     # the per-SM scratch
     w1 = lib.gw_polarization_workspace(1, K1, nb1, 16, GW_BF16X3)
     w8 = lib.gw_polarization_workspace(8, K8, nb8, 16, GW_BF16X3)
-    assert w1 > 0 and w8 == w1
+    assert w1 > w0 > 0 and w8 == w0 + 2 * (w1 - w0)
+    serial = _PolOpt(serial_prep=1)
+    assert lib.gw_polarization_workspace_ex(8, K8, nb8, 16, GW_BF16X3, ctypes.byref(serial)) == w1
+    assert lib.gw_polarization_workspace_ex(1, K1, nb1, 16, GW_BF16X3, ctypes.byref(_PolOpt())) == w1
     # small q: 2 x 2 upper tiles x 16 frequencies = 48 items each, so many share a group
     Ks = (ctypes.c_int64 * 8)(*([1000] * 8))
     nbs = (ctypes.c_int * 8)(*([100] * 8))
@@ -109,11 +123,7 @@ def test_polarization_options_rejected_without_gpu():
     lib = _lib()
     lib.gw_last_error.restype = ctypes.c_char_p
 
-    class Opt(ctypes.Structure):
-        _fields_ = [("accumulate", ctypes.c_int), ("group_items_per_sm", ctypes.c_int),
-                    ("b_stages", ctypes.c_int), ("fp64_waves", ctypes.c_int),
-                    ("herk_events", ctypes.c_void_p), ("n_herk_events", ctypes.c_int),
-                    ("herk_launches_out", ctypes.c_void_p)]
+    Opt = _PolOpt
 
     K = (ctypes.c_int64 * 1)(64)
     nb = (ctypes.c_int * 1)(8)

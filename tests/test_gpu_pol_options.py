@@ -80,15 +80,19 @@ def test_three_product_layout_against_oracle(gw, prec, nb):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 def test_tuning_knobs_do_not_change_the_result(gw, prec):
-    """b_stages and the q grouping change neither the per-tile order of the sums nor the
-    roundings: the results are bit-identical; the HERK events bracket every HERK launch."""
+    """b_stages, the q grouping and the overlapped preparation (one group prepared while the
+    HERK of the one before runs, or serial_prep) change neither the per-tile order of the sums
+    nor the roundings: the results are bit-identical; the HERK events bracket every HERK
+    launch."""
     wls = [S.tiny(nb=nb, nocc=3, nunocc=nu, mesh=(2, 2, 1), nw=4, seed=90 + nb)
            for nb, nu in ((96, 30), (40, 7), (130, 55))]
     om = wls[0].omega()
     Ms = [T(w.m_full(0).astype(np.complex64)) for w in wls]
     ds = [T(w.delta(0)) for w in wls]
     ref = gw.polarization(Ms, ds, om, 0.5, prec)
-    for opts in ({"b_stages": 6}, {"group_items_per_sm": 1}, {"group_items_per_sm": 64, "b_stages": 6}):
+    for opts in ({"b_stages": 6}, {"group_items_per_sm": 1},
+                 {"group_items_per_sm": 1, "serial_prep": True},
+                 {"group_items_per_sm": 64, "b_stages": 6}):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(4)]
         o = dict(opts, herk_events=evs)

@@ -90,9 +90,12 @@ def test_tc_odd_basis(gw, prec, nb):
     assert rel_fro(P.cpu().numpy(), ref) <= BOUND[prec]
 
 
-def test_tc_polarization_cuda_graph_replay(gw):
+@pytest.mark.parametrize("options", [None, {"group_items_per_sm": 1}])
+def test_tc_polarization_cuda_graph_replay(gw, options):
     """The split-precision polarization captured in a CUDA graph and replayed on new
-    inputs gives the direct call's result bit for bit (every launch only enqueues)."""
+    inputs gives the direct call's result bit for bit (every launch only enqueues); with one
+    group per q the capture takes in the library's two streams (the preparation of the
+    second q overlapping the HERK of the first)."""
     wls = [S.tiny(nb=nb, nocc=3, nunocc=nu, mesh=(2, 2, 1), nw=5, seed=30 + nb)
            for nb, nu in ((64, 20), (50, 11))]
     om = wls[0].omega()
@@ -100,16 +103,16 @@ def test_tc_polarization_cuda_graph_replay(gw):
     ds = [T(w.delta(0)) for w in wls]
     Ks = [m.shape[0] for m in Ms]
     nbs = [m.shape[1] for m in Ms]
-    ws = torch.empty(gw.polarization_workspace(Ks, nbs, len(om), "tf32x3"), dtype=torch.uint8,
-                     device="cuda:0")
+    ws = torch.empty(gw.polarization_workspace_ex(Ks, nbs, len(om), "tf32x3", options),
+                     dtype=torch.uint8, device="cuda:0")
     out = [torch.empty((len(om), nb, nb), dtype=torch.complex128, device="cuda:0") for nb in nbs]
-    gw.polarization(Ms, ds, om, 0.5, "tf32x3", out=out, ws=ws)      # warm-up outside capture
+    gw.polarization(Ms, ds, om, 0.5, "tf32x3", out=out, ws=ws, options=options)   # warm-up
     torch.cuda.synchronize()
     s = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
         with torch.cuda.graph(g, stream=s):
-            gw.polarization(Ms, ds, om, 0.5, "tf32x3", out=out, ws=ws)
+            gw.polarization(Ms, ds, om, 0.5, "tf32x3", out=out, ws=ws, options=options)
     for trial in range(2):
         scale = 1.0 + trial
         for m, w in zip(Ms, wls):
