@@ -12,7 +12,9 @@
  *     no pointer after a call returns and never frees caller memory.
  *   - Complex data is interleaved (re, im): complex128 = two doubles, complex64 = two
  *     floats. Matrices are row-major and dense (leading dimension = row length).
- *   - Every compute call only enqueues work on `stream` (no host synchronisation).
+ *   - Every compute call only enqueues work ordered on `stream` (no host
+ *     synchronisation; gw_polarization* fork to two streams of the library and join them
+ *     back to `stream` before returning).
  *     Argument errors are returned at once (GW_EINVAL, message in gw_last_error()).
  *     Errors found on the device (a non-positive-definite dielectric matrix, a
  *     non-finite value, an expired bounded wait) are recorded in a library-owned
