@@ -1401,14 +1401,20 @@ int pol_tc(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, int 
   std::vector<int> start;
   tc_groups(nq, Ks.data(), nbs.data(), nw, ctx.sm_count, o.group_items_per_sm, start);
   const size_t group_max = group_max_bytes(start, Ks.data(), nbs.data(), nw, precision);
-  const bool ovl = overlapped(start, o);
   cudaStream_t sp = s, sh = s;         // preparation and HERK streams
-  std::unique_lock<std::mutex> lk(g_ps_mu, std::defer_lock);
+  std::unique_lock<std::mutex> lk(g_ps_mu);
   PolStreams* ps = nullptr;
-  if (ovl) {
-    lk.lock();
+  // The streams and events are created by the first call that runs outside a stream capture
+  // (single group or not); a call captured before that runs on the caller's stream alone.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  GW_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+  const bool known = ctx.device >= 0 && ctx.device < 64 && g_ps_ok[ctx.device];
+  if (known || cs == cudaStreamCaptureStatusNone) {
     int rc = pol_streams(ctx.device, &ps);
     if (rc) return rc;
+  }
+  const bool ovl = overlapped(start, o) && ps != nullptr;
+  if (ovl) {
     GW_CUDA_TRY(cudaEventRecord(ps->entry, s));
     GW_CUDA_TRY(cudaStreamWaitEvent(ps->herk, ps->entry, 0));
     GW_CUDA_TRY(cudaStreamWaitEvent(ps->prep, ps->entry, 0));
