@@ -875,9 +875,9 @@ def run_case_batched(args):
         qbig = max(w, key=lambda q: Ks[q] * nbs[q] ** 2)
         if args.autotune and prec != "fp64":
             t0 = time.perf_counter()
+            # the cache file: GW_AUTOTUNE_CACHE, else the autotuner's default under ~/.cache
             e = autotune.tune(nbs[qbig], Ks[qbig], wl.nw, precisions=(prec,), bound=1e-6,
-                              cache_path=os.path.join(ROOT, "gpurun_out", "autotune.json")
-                              if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+                              cache_path=os.environ.get("GW_AUTOTUNE_CACHE") or None)
             tune_s += time.perf_counter() - t0
             tuned.append(e)
         else:
