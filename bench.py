@@ -255,8 +255,9 @@ class Pipeline:
 
     def step_from_host(self, host_M, host_d, host_Ms, copy_stream):
         """One step whose inputs start in pinned host memory: the projections stream in q by q on
-        the copy stream while the polarization of the q before runs (gw.polarization_streamed);
-        the Sigma projections follow on the same copy stream."""
+        the copy stream, and one polarization call over all q prepares each q once its copy has
+        arrived (gw.polarization_streamed), so later copies overlap the HERK of earlier q; the
+        Sigma projections follow on the same copy stream."""
         gw, torch = self.gw, self.torch
         gw.polarization_streamed(host_M, host_d, self.om, self.wl.prefactor, self.prec,
                                  dev_Ms=self.M, dev_deltas=self.delta, out=self.P, ws=self.ws_p,
@@ -453,8 +454,9 @@ def e2e_measure(pipe, args, world):
     return {"value": (fp + fs) * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms,
             "h2d_gbs_measured": h2d_gbs,
-            "how": "projections streamed q by q from pinned host memory on a copy stream while "
-                   "the polarization of the q before runs; Sigma projections and energies too; "
+            "how": "projections streamed q by q from pinned host memory on a copy stream, one "
+                   "polarization call over all q preparing each q once its copy has arrived; "
+                   "Sigma projections and energies too; "
                    "fitted parameters and Sigma^c read back"}
 
 

@@ -156,7 +156,11 @@ int gw_polarization(int nq, const int64_t* K_host, const int* nb_host,
  *                       (the HERK's last, partial wave leaves SMs idle), with two workspace
  *                       slots. Both streams are forked from `stream` at entry and joined to it
  *                       before the call returns: the call is ordered on `stream` either way,
- *                       and a capture of `stream` into a CUDA graph takes both in.
+ *                       and a capture of `stream` into a CUDA graph takes both in;
+ *   input_events        NULL, or per q (host array) a cudaEvent_t or NULL: the call reads the
+ *                       projections and energies of q only after that event (e.g. recorded
+ *                       after their host-to-device copy on another stream), so the copies of
+ *                       later q overlap the work on earlier ones within one call.
  * gw_polarization_workspace_ex gives the workspace for the same options (group_items_per_sm
  * and fp64_waves change it). Errors: GW_EINVAL for b_stages other than 0, 4 or 6, negative
  * counts. */
@@ -169,6 +173,7 @@ typedef struct gw_pol_options {
   int n_herk_events;
   int* herk_launches_out;
   int serial_prep;
+  void* const* input_events;
 } gw_pol_options;
 size_t gw_polarization_workspace_ex(int nq, const int64_t* K_host, const int* nb_host, int nw,
                                     int precision, const gw_pol_options* options);

@@ -62,7 +62,8 @@ class PolOptions(ctypes.Structure):
     """gw_pol_options (include/gw.h)."""
     _fields_ = [("accumulate", _i32), ("group_items_per_sm", _i32), ("b_stages", _i32),
                 ("fp64_waves", _i32), ("herk_events", _P(_vp)), ("n_herk_events", _i32),
-                ("herk_launches_out", _P(_i32)), ("serial_prep", _i32)]
+                ("herk_launches_out", _P(_i32)), ("serial_prep", _i32),
+                ("input_events", _P(_vp))]
 
 
 _sig("gw_polarization_workspace_ex", _sz, _i32, _P(_i64), _P(_i32), _i32, _i32, _P(PolOptions))
@@ -265,6 +266,11 @@ def _pol_options(options):
     o.fp64_waves = int(options.get("fp64_waves", 0))
     o.serial_prep = int(bool(options.get("serial_prep", False)))
     keep = []
+    ins = options.get("input_events")
+    if ins:
+        arr = (_vp * len(ins))(*[(e.cuda_event if e is not None else None) for e in ins])
+        keep.append(arr)
+        o.input_events = ctypes.cast(arr, _P(_vp))
     evs = options.get("herk_events")
     if evs:
         handles = []
@@ -294,8 +300,8 @@ def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=No
                  options=None):
     """P[q] = sum_t w_tj M_tI conj(M_tJ) for each q (complex128 [nw][N_b][N_b]).
     options: None or a dict of gw_pol_options fields (accumulate, group_items_per_sm,
-    b_stages, fp64_waves, serial_prep, herk_events = [(start, end), ...] torch.cuda.Event
-    pairs); after the
+    b_stages, fp64_waves, serial_prep, input_events = [torch.cuda.Event per q, recorded],
+    herk_events = [(start, end), ...] torch.cuda.Event pairs); after the
     call options["herk_launches"] holds the number of HERK launches."""
     prec = PRECISIONS.get(precision, precision)
     om, nw = _om(omega)
@@ -328,10 +334,11 @@ def polarization(Ms, deltas, omega, prefactor, precision="fp64", fs=None, out=No
 def polarization_streamed(host_Ms, host_deltas, omega, prefactor, precision="bf16x3",
                           dev_Ms=None, dev_deltas=None, out=None, ws=None, copy_stream=None):
     """P[q] for projections that live in (pinned) host memory: the host-to-device copies run on a
-    copy stream, one q after the other, and the polarization of each q starts on the current
-    stream as soon as its inputs have arrived, so the transfer of q + 1 overlaps the tensor-core
-    work of q. dev_Ms / dev_deltas: device buffers (allocated if None); ws: a workspace for the
-    largest single q. Returns the list of P (complex128 [nw][N_b][N_b])."""
+    copy stream, one q after the other, each followed by an event; one polarization call over all
+    q waits for each q's event before reading that q's inputs (gw_pol_options.input_events), so
+    the transfer of later q overlaps the tensor-core work on earlier ones. dev_Ms / dev_deltas:
+    device buffers (allocated if None); ws: a workspace of polarization_workspace over all q.
+    Returns the list of P (complex128 [nw][N_b][N_b])."""
     om, nw = _om(omega)
     nq = len(host_Ms)
     cur = torch.cuda.current_stream()
@@ -344,10 +351,6 @@ def polarization_streamed(host_Ms, host_deltas, omega, prefactor, precision="bf1
     if out is None:
         out = [torch.empty((nw, m.shape[1], m.shape[1]), dtype=torch.complex128, device=dev)
                for m in host_Ms]
-    if ws is None:
-        prec = PRECISIONS.get(precision, precision)
-        need = max(polarization_workspace([m.shape[0]], [m.shape[1]], nw, prec) for m in host_Ms)
-        ws = torch.empty(max(int(need), 1), dtype=torch.uint8, device=dev)
     cs.wait_stream(cur)               # earlier work on the current stream is done with the buffers
     ready = []
     with torch.cuda.stream(cs):
@@ -357,9 +360,8 @@ def polarization_streamed(host_Ms, host_deltas, omega, prefactor, precision="bf1
             ev = torch.cuda.Event()
             ev.record(cs)
             ready.append(ev)
-    for q in range(nq):
-        cur.wait_event(ready[q])
-        polarization([dev_Ms[q]], [dev_deltas[q]], omega, prefactor, precision, out=[out[q]], ws=ws)
+    polarization(dev_Ms, dev_deltas, omega, prefactor, precision, out=out, ws=ws,
+                 options={"input_events": ready})
     for t in list(dev_Ms) + list(dev_deltas):
         t.record_stream(cs)
     return out

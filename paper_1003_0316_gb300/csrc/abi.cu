@@ -110,6 +110,7 @@ int resolve_pol_options(const gw_pol_options* o, PolOpts* out) {
   if (o->b_stages) out->b_stages = o->b_stages;
   if (o->fp64_waves) out->fp64_waves = o->fp64_waves;
   out->serial_prep = o->serial_prep != 0;
+  out->input_events = o->input_events;
   out->events = o->herk_events;
   out->n_events = o->n_herk_events;
   return GW_OK;

@@ -94,6 +94,7 @@ struct PolOpts {
   int b_stages = 4;
   int fp64_waves = 4;
   bool serial_prep = false;        // no overlap of a group's preparation with the HERK before
+  void* const* input_events = nullptr;   // per q: cudaEvent_t to wait for before reading its inputs
   void* const* events = nullptr;   // cudaEvent_t pairs around the HERK launches
   int n_events = 0;
   int launches = 0;                // out: HERK launches of the call

@@ -310,6 +310,10 @@ int pol_fp64(int nq, const PolQ* qs, double pref, int nw, const OmegaArr& om, vo
   std::vector<int> splits;
   std::vector<int64_t> tiles;
   plan_fp64(nq, K.data(), nb.data(), nw, ctx.sm_count, o.fp64_waves, splits, tiles);
+  if (o.input_events)                  // every q's inputs before the first launch
+    for (int q = 0; q < nq; ++q)
+      if (o.input_events[q])
+        GW_CUDA_TRY(cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(o.input_events[q]), 0));
   for (int q0 = 0; q0 < nq; q0 += MAXQ) {
     int n = std::min(MAXQ, nq - q0);
     PolLaunch L{};

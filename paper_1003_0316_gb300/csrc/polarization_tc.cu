@@ -1316,6 +1316,9 @@ static int pol_tc_groups(const std::vector<int>& start, const PolQ* qs, double p
       }
       if (kpad > 0) {
         if (!sw || !xT || !bsp) return set_error(GW_EWORKSPACE, "internal: tensor-core buffers");
+        // the q's inputs (projections, energies) are read only by its weights and copies
+        if (o.input_events && o.input_events[q0 + i])
+          GW_CUDA_TRY(cudaStreamWaitEvent(sp, static_cast<cudaEvent_t>(o.input_events[q0 + i]), 0));
         int64_t blocks = std::min<int64_t>((kpad + 255) / 256, int64_t(ctx.sm_count) * 8);
         k_abs_weights_f32<<<unsigned(blocks), 256, 0, sp>>>(Q.K, kpad, Q.delta, Q.dbar, Q.f, pref,
                                                            nw, om, sw, ctx.status);

@@ -309,6 +309,24 @@ def test_polarization_streamed_from_host(gw):
     gw.check()
     for a, b in zip(got, ref):
         assert torch.equal(a, b)
+    # the same waits with one group per q (each q's preparation on the library's second
+    # stream, after its copy's event)
+    cs = torch.cuda.Stream()
+    dM = [torch.empty(m.shape, dtype=m.dtype, device="cuda:0") for m in host_M]
+    dd = [torch.empty(d.shape, dtype=d.dtype, device="cuda:0") for d in host_d]
+    cs.wait_stream(torch.cuda.current_stream())
+    evs = []
+    with torch.cuda.stream(cs):
+        for q in range(len(dM)):
+            dM[q].copy_(host_M[q], non_blocking=True)
+            dd[q].copy_(host_d[q], non_blocking=True)
+            evs.append(torch.cuda.Event())
+            evs[-1].record(cs)
+    got = gw.polarization(dM, dd, om, 0.25, "bf16x3",
+                          options={"input_events": evs, "group_items_per_sm": 1})
+    gw.check()
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
